@@ -1,0 +1,332 @@
+"""Pins of the FP64 oracle: checks against facts fixed by the paper and by mathematics,
+not by the oracle's own code.
+
+Each function raises AssertionError when the oracle (whichever build of it is loaded)
+disagrees with the fact it pins.  tests/test_oracle_pins.py runs them against the
+oracle; tests/test_oracle_mutants.py runs them against copies of the oracle with a
+planted mistake and requires that some pin fails for every mistake.
+
+Facts used (paper: arXiv 2412.14775, Sections 2.1, 2.2, Tables 1-2):
+  P1  SK under the null.  If |I_i| are i.i.d. Gamma(shape d), the generalised
+      spectral kurtosis of Nita & Gary (2010; cited in Sec. 2.1) has E[tau] = 1 and
+      Var[tau] = 2 d (d+1) W^2 / ((W-1)(Wd+2)(Wd+3)).  (The Dirichlet moments of
+      |I_i|/S1 give both; d = 1 is the classic 4W^2/((W-1)(W+2)(W+3)).)
+  P2  Cauchy-Schwarz: 1 <= W S2/S1^2 <= W, so 0 <= tau <= Wd+1, with tau = 0 for a
+      constant magnitude and tau = Wd+1 for a single non-zero sample.
+  P3  A fully polarised signal V = c e e^H has (Q, U, V) = c w with a fixed real w,
+      |w| = |e1|^2 + |e2|^2 = I/c, so both directional statistics are 1.
+  P4  Isotropic noise: unit vectors uniform on the sphere, E[r^2] = 1/W exactly;
+      antipodal pairs give r = 0.
+  P5  Hermitian autocorrelations have Im Q = Im U = Im V = 0, so r_Im = 0.
+  P6  Averaging: mean of unflagged samples and weight n/K, checked over every subset
+      of flagged windows of a bin.
+  P7  Exact evaluation on a small integer grid (50-digit arithmetic, Stokes taken as
+      traces against the Pauli matrices instead of the sums of Eq. IQUV).
+  P8  Splitting a stream into blocks at multiples of W changes nothing.
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import mpmath
+import numpy as np
+
+import oracle
+from oracle import OracleStream
+
+EPS32 = 2.0 ** -23
+
+
+def _stream(R, M, K, d=1.0, s_low=-1e300, s_high=1e300, gamma=1e300, eps=EPS32):
+    return OracleStream(R, M, K, d, s_low, s_high, gamma, eps)
+
+
+def _run_windows(vis, M, d=1.0, eps=EPS32, **thr):
+    """vis [nwin, M, 4] complex -> oracle outputs with one window per row."""
+    st = _stream(vis.shape[0], M, M, d=d, eps=eps, **thr)
+    return st.process(vis)
+
+
+def _sk_var(M, d):
+    return 2.0 * d * (d + 1.0) * M * M / ((M - 1.0) * (M * d + 2.0) * (M * d + 3.0))
+
+
+def _check_mean_var(tau, M, d, z=4.0):
+    n = tau.size
+    var_cf = _sk_var(M, d)
+    mean = tau.mean()
+    assert abs(mean - 1.0) < z * math.sqrt(var_cf / n), (M, d, mean)
+    c = tau - mean
+    v = np.mean(c * c)
+    m4 = np.mean(c ** 4)
+    se_v = math.sqrt(max(m4 - v * v, 0.0) / n)
+    assert abs(v - var_cf) < z * se_v, (M, d, v, var_cf)
+
+
+# ---------------------------------------------------------------------------------
+def pin_p1_sk_null_gamma(nwin=100000, seed=1):
+    """P1 with |I| ~ Gamma(d): xx carries the positive real magnitude, all else 0."""
+    for M, d in ((16, 1.0), (16, 2.0), (20, 0.5), (8, 3.66)):
+        rng = np.random.default_rng(seed + M * 7 + int(d * 10))
+        g = rng.gamma(shape=d, scale=1.0, size=(nwin, M))
+        vis = np.zeros((nwin, M, 4), np.complex128)
+        vis[..., 0] = g
+        out = _run_windows(vis, M, d=d, eps=0.0)
+        _check_mean_var(out["tau"].ravel(), M, d)
+
+
+def pin_p1_sk_null_autocorrelation(nwin=100000, seed=2):
+    """P1 with unaveraged autocorrelations of complex Gaussian voltages x, y:
+    I = |x|^2 + |y|^2 is Gamma(2) distributed, so d = 2 centres tau at 1."""
+    M = 16
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal((nwin, M)) + 1j * rng.standard_normal((nwin, M))) / math.sqrt(2)
+    y = (rng.standard_normal((nwin, M)) + 1j * rng.standard_normal((nwin, M))) / math.sqrt(2)
+    vis = np.stack([x * x.conj(), x * y.conj(), y * x.conj(), y * y.conj()], axis=-1)
+    out = _run_windows(vis, M, d=2.0, eps=0.0)
+    _check_mean_var(out["tau"].ravel(), M, 2.0)
+
+
+def pin_p2_sk_bounds(seed=3):
+    """P2: 0 <= tau <= Wd+1 on arbitrary data, and both ends are attained."""
+    rng = np.random.default_rng(seed)
+    for M, d in ((2, 1.0), (5, 0.7), (16, 3.66), (64, 1.0)):
+        lead = (M * d + 1.0) / (M - 1.0)
+        n = 4000
+        mags = np.concatenate([
+            rng.lognormal(0.0, 3.0, size=(n, M)),
+            rng.uniform(0, 1, size=(n, M)) * (rng.uniform(size=(n, M)) < 0.2),
+            rng.exponential(size=(n, M))])
+        keep = mags.sum(axis=1) > 0
+        mags = mags[keep]
+        ph = rng.uniform(0, 2 * np.pi, size=mags.shape)
+        vis = np.zeros(mags.shape + (4,), np.complex128)
+        vis[..., 0] = mags * np.exp(1j * ph) * 0.5
+        vis[..., 3] = mags * np.exp(1j * ph) * 0.5          # I = xx + yy = mags e^{j ph}
+        vis[..., 1] = rng.standard_normal(mags.shape)        # xy, yx do not enter SK
+        tau = _run_windows(vis, M, d=d, eps=0.0)["tau"].ravel()
+        assert np.all(tau >= -1e-12 * (M * d + 1)), (M, d, tau.min())
+        assert np.all(tau <= (M * d + 1) * (1 + 1e-12)), (M, d, tau.max())
+
+        # constant magnitude, random phases -> tau = 0 (I split evenly over xx and yy)
+        const = np.zeros((50, M, 4), np.complex128)
+        const[..., 0] = 1.5 * np.exp(1j * rng.uniform(0, 2 * np.pi, size=(50, M)))
+        const[..., 3] = const[..., 0]
+        tau0 = _run_windows(const, M, d=d, eps=0.0)["tau"]
+        assert np.all(np.abs(tau0) < 1e-12 * lead * M), (M, d, tau0)
+
+        # one non-zero sample -> tau = Wd + 1
+        one = np.zeros((M, M, 4), np.complex128)
+        for k in range(M):
+            one[k, k, 0] = 2.5 - 1.5j
+        tau1 = _run_windows(one, M, d=d, eps=0.0)["tau"]
+        assert np.allclose(tau1, M * d + 1.0, rtol=1e-13, atol=0), (M, d, tau1)
+
+        # all-zero window with eps > 0: tau = lead * (0/eps - 1) = -lead, finite
+        zero = np.zeros((1, M, 4), np.complex128)
+        tz = _run_windows(zero, M, d=d, eps=EPS32)["tau"]
+        assert tz[0, 0] == -lead, (M, d, tz)
+
+
+def _polarised(rng, nwin, M, c_of):
+    th = rng.uniform(0, np.pi, size=(nwin, 1))
+    ph = np.where(rng.uniform(size=(nwin, 1)) < 0.5, 0.0, rng.uniform(0, 2 * np.pi, size=(nwin, 1)))
+    e1 = np.cos(th) * np.ones((1, M))
+    e2 = np.sin(th) * np.exp(1j * ph) * np.ones((1, M))
+    c = c_of(rng, nwin, M)
+    return np.stack([c * e1 * e1.conj(), c * e1 * e2.conj(), c * e2 * e1.conj(), c * e2 * e2.conj()],
+                    axis=-1)
+
+
+def pin_p3_fully_polarised(seed=4):
+    """P3: a fully polarised window has r_Re = r_Im = 1; a real c has r_Im = 0;
+    and per sample |(Re Q, Re U, Re V)| = |Re I| for real c (Stokes identity)."""
+    rng = np.random.default_rng(seed)
+    M = 16
+
+    def const_phase(rng, n, M):       # varying amplitude, constant phase per window
+        amp = rng.uniform(0.5, 20.0, size=(n, M))
+        ph = rng.uniform(0, 2 * np.pi, size=(n, 1))
+        return amp * np.exp(1j * ph)
+
+    vis = _polarised(rng, 2000, M, const_phase)
+    out = _run_windows(vis, M, eps=0.0)
+    assert np.allclose(out["r_re"], 1.0, rtol=0, atol=1e-12), out["r_re"].min()
+    assert np.allclose(out["r_im"], 1.0, rtol=0, atol=1e-12), out["r_im"].min()
+
+    def real_c(rng, n, M):
+        return rng.uniform(0.5, 20.0, size=(n, M)) * np.where(rng.uniform(size=(n, 1)) < 0.5, -1, 1)
+
+    vis = _polarised(rng, 500, M, real_c)
+    # with c real, yx = conj(xy) and xx, yy are real; write them so exactly (the
+    # products above round differently in the last bit)
+    vis[..., 2] = vis[..., 1].conj()
+    vis[..., 0] = vis[..., 0].real
+    vis[..., 3] = vis[..., 3].real
+    out = _run_windows(vis, M, eps=EPS32)
+    assert np.all(out["r_im"] == 0.0)
+    assert np.allclose(out["r_re"], 1.0, rtol=0, atol=1e-6)
+    # c purely imaginary: Re(Q, U, V) = 0 so r_Re = 0, r_Im = 1; only the Im part
+    # can raise the flag (the Re and Im flags are combined with OR, Sec. 2.2)
+    vis_i = 1j * vis
+    out = _run_windows(vis_i, M, eps=EPS32, s_low=-1e300, s_high=1e300, gamma=0.5)
+    assert np.all(out["r_re"] == 0.0)
+    assert np.allclose(out["r_im"], 1.0, rtol=0, atol=1e-6)
+    assert np.all(out["wflag"] == 1)
+    for k in range(50):
+        s = oracle.stokes(np.stack([vis[k, 0].real, vis[k, 0].imag], -1).reshape(8))
+        assert math.isclose(math.hypot(s[2], s[4], s[6]), abs(s[0]), rel_tol=1e-12), s
+
+
+def pin_p4_isotropic_null(nwin=100000, seed=5):
+    """P4: i.i.d. circular Gaussian correlations give E[r^2] = 1/W per part, and a
+    window made of antipodal pairs gives r = 0 exactly."""
+    rng = np.random.default_rng(seed)
+    for M in (8, 16, 20):
+        vis = (rng.standard_normal((nwin, M, 4)) + 1j * rng.standard_normal((nwin, M, 4))) / math.sqrt(2)
+        out = _run_windows(vis, M, eps=0.0)
+        for key in ("r_re", "r_im"):
+            r2 = out[key].ravel() ** 2
+            se = r2.std() / math.sqrt(r2.size)
+            assert abs(r2.mean() - 1.0 / M) < 4 * se, (M, key, r2.mean(), 1.0 / M)
+        half = (rng.standard_normal((200, M // 2, 4)) + 1j * rng.standard_normal((200, M // 2, 4)))
+        anti = np.empty((200, M, 4), np.complex128)
+        anti[:, 0::2] = half
+        anti[:, 1::2] = -half
+        o2 = _run_windows(anti, M, eps=EPS32)
+        assert np.all(o2["r_re"] == 0.0) and np.all(o2["r_im"] == 0.0)
+
+
+def pin_p5_autocorrelation_r_im(seed=6):
+    """P5: Hermitian V (xx, yy real, yx = conj(xy)) gives r_Im = 0 exactly."""
+    rng = np.random.default_rng(seed)
+    M = 16
+    n = 3000
+    xx = rng.exponential(size=(n, M))
+    yy = rng.exponential(size=(n, M))
+    xy = rng.standard_normal((n, M)) + 1j * rng.standard_normal((n, M))
+    vis = np.stack([xx + 0j, xy, xy.conj(), yy + 0j], axis=-1)
+    out = _run_windows(vis, M, eps=EPS32)
+    assert np.all(out["r_im"] == 0.0)
+    assert np.all(out["r_re"] > 0.0)
+
+
+def pin_p6_averaging_bruteforce(seed=7):
+    """P6: for every subset of flagged windows in a bin, the output equals the mean
+    of the unflagged samples (numpy), the weight equals their count / K, and the
+    per-sample flag bits equal the window flags expanded over W samples."""
+    rng = np.random.default_rng(seed)
+    for M, nb in ((4, 8), (16, 4), (3, 5)):
+        K = M * nb
+        d = 1.0
+        lead_max = M * d + 1.0
+        subsets = list(itertools.product((0, 1), repeat=nb))
+        R = len(subsets)
+        vis = np.zeros((R, K, 4), np.complex128)
+        for rr, sub in enumerate(subsets):
+            for w, fl in enumerate(sub):
+                blk = vis[rr, w * M:(w + 1) * M]
+                # xy, yx never enter SK; gamma = 2 keeps DS from flagging (r <= 1)
+                blk[:, 1] = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+                blk[:, 2] = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+                if fl:     # spike window: I non-zero at one sample only -> tau = Wd + 1
+                    blk[rng.integers(M), 0] = 3.0 + 1.0j
+                else:      # flat window: |I| constant -> tau = 0
+                    blk[:, 0] = 2.0 * np.exp(1j * rng.uniform(0, 2 * np.pi, size=M))
+        st = OracleStream(R, M, K, d, -0.5, lead_max / 2, 2.0, EPS32)
+        out = st.process(vis)
+        want_flags = np.array(subsets, dtype=np.uint8)
+        assert np.array_equal(out["wflag"], want_flags), M
+        for rr, sub in enumerate(subsets):
+            keep = np.repeat(1 - np.array(sub), M).astype(bool)
+            n = keep.sum()
+            exp = vis[rr][keep].mean(axis=0) if n else np.zeros(4)
+            got = out["avg"][rr, 0].reshape(4, 2)
+            assert np.allclose(got[:, 0], exp.real, rtol=1e-13, atol=1e-14), (M, sub)
+            assert np.allclose(got[:, 1], exp.imag, rtol=1e-13, atol=1e-14), (M, sub)
+            assert out["weight"][rr, 0] == n / K
+            bits = np.zeros((K + 31) // 32, np.uint64)
+            for t in range(K):
+                if not keep[t]:
+                    bits[t // 32] |= np.uint64(1) << np.uint64(t % 32)
+            assert np.array_equal(out["flagbits"][rr].astype(np.uint64), bits), (M, sub)
+
+
+def _pauli_stokes(v):
+    """Stokes (I, Q, U, V) of one 2x2 correlation matrix as traces tr(V sigma_k) with
+    sigma = (identity, Z, X, Y) -- a second route to Eq. IQUV."""
+    Vm = [[v[0], v[1]], [v[2], v[3]]]
+    sig = {
+        "I": [[1, 0], [0, 1]], "Q": [[1, 0], [0, -1]],
+        "U": [[0, 1], [1, 0]], "V": [[0, -1j], [1j, 0]]}
+    out = []
+    for k in "IQUV":
+        s = sig[k]
+        tr = sum(Vm[a][b] * s[b][a] for a in range(2) for b in range(2))
+        out.append(complex(tr))
+    return out
+
+
+def pin_p7_exact_grid(nwin_per_M=3000, seed=8):
+    """P7: windows of W in {2,3,4} with every correlation on {-1,0,1}+j{-1,0,1};
+    statistics to 1e-12 against 50-digit evaluation, flags identical (ties at a
+    threshold, decided exactly, are counted and must also agree)."""
+    mpmath.mp.dps = 50
+    rng = np.random.default_rng(seed)
+    eps = Fraction(1, 2 ** 23)
+    epsm = mpmath.mpf(1) / 2 ** 23
+    for M, d in ((2, 1.0), (3, 0.5), (4, 2.0)):
+        s_low, s_high, gamma = 0.25, 1.75, 0.6
+        vals = rng.integers(-1, 2, size=(nwin_per_M, M, 4, 2))
+        vis = vals[..., 0] + 1j * vals[..., 1]
+        out = _run_windows(vis, M, d=d, eps=float(eps), s_low=s_low, s_high=s_high, gamma=gamma)
+        dd = Fraction(d)
+        lead = (M * dd + 1) / (M - 1)
+        for w in range(nwin_per_M):
+            st = [_pauli_stokes(vis[w, i]) for i in range(M)]
+            # SK: S2 is an exact rational, S1 a sum of square roots of integers
+            S2 = sum(Fraction(int(round(s[0].real)) ** 2 + int(round(s[0].imag)) ** 2) for s in st)
+            S1 = mpmath.fsum(mpmath.sqrt(int(round(s[0].real)) ** 2 + int(round(s[0].imag)) ** 2)
+                             for s in st)
+            tau = mpmath.mpf(lead.numerator) / lead.denominator * (
+                M * mpmath.mpf(S2.numerator) / S2.denominator / (S1 * S1 + epsm) - 1)
+            rs = []
+            for part in (0, 1):
+                acc = [mpmath.mpf(0)] * 3
+                for s in st:
+                    comp = [int(round((s[k].real, s[k].imag)[part])) for k in (1, 2, 3)]
+                    p = mpmath.sqrt(sum(c * c for c in comp)) + epsm
+                    acc = [acc[k] + comp[k] / p for k in range(3)]
+                rs.append(mpmath.sqrt(sum(a * a for a in acc)) / M)
+            got = (out["tau"][w, 0], out["r_re"][w, 0], out["r_im"][w, 0])
+            for g, e, floor in zip(got, (tau, rs[0], rs[1]), (1.0, M ** -0.5, M ** -0.5)):
+                assert abs(g - float(e)) <= 1e-12 * max(abs(float(e)), floor), (M, w, g, e)
+            f = (tau < s_low) or (tau > s_high) or (rs[0] > gamma) or (rs[1] > gamma)
+            assert bool(out["wflag"][w, 0]) == bool(f), (M, w, got)
+
+
+def pin_p8_block_split(seed=9):
+    """P8: processing a stream as one block or as blocks split at multiples of W
+    gives identical statistics, flags, averages and weights."""
+    rng = np.random.default_rng(seed)
+    R, M, K, T = 7, 4, 24, 240
+    vis = rng.standard_normal((R, T, 4)) + 1j * rng.standard_normal((R, T, 4))
+    vis[:, 50:60] *= 8.0
+    vis[2, 100:130, :] = 5.0 * (1 + 1j)
+    thr = (1.0, 0.3, 2.0, 0.7, EPS32)
+    whole = OracleStream(R, M, K, *thr).process(vis)
+    for cuts in ((8, 120), (4, 28, 96, 100, 236), (24, 48, 72), (12,)):
+        st = OracleStream(R, M, K, *thr)
+        parts = []
+        edges = (0,) + cuts + (T,)
+        for a, b in zip(edges[:-1], edges[1:]):
+            parts.append(st.process(vis[:, a:b]))
+        for key in ("tau", "r_re", "r_im", "wflag"):
+            assert np.array_equal(np.concatenate([p[key] for p in parts], axis=1), whole[key]), key
+        assert np.array_equal(np.concatenate([p["avg"] for p in parts], axis=1), whole["avg"])
+        assert np.array_equal(np.concatenate([p["weight"] for p in parts], axis=1), whole["weight"])
+
+
+ALL_PINS = [pin_p1_sk_null_gamma, pin_p1_sk_null_autocorrelation, pin_p2_sk_bounds,
+            pin_p3_fully_polarised, pin_p4_isotropic_null, pin_p5_autocorrelation_r_im,
+            pin_p6_averaging_bruteforce, pin_p7_exact_grid, pin_p8_block_split]

@@ -1,0 +1,74 @@
+"""The pins must catch plausible mistakes.
+
+Each case copies the oracle's C source, plants one mistake (a dropped term, a wrong
+sign or index, a misread formula), builds it into a separate library on the CPU and
+runs every pin against it.  A mutant that passes every pin would mean the pins do
+not protect that part of the oracle.
+"""
+import os
+
+import pytest
+
+import oracle.build
+import oracle.oracle
+import oracle_pins
+
+MUTANTS = {
+    # Eq. IQUV
+    "U_sign": ("s[4] = xy_re + yx_re;", "s[4] = xy_re - yx_re;"),
+    "Q_uses_xy": ("s[2] = xx_re - yy_re;", "s[2] = xy_re - yy_re;"),
+    "V_re_from_real_parts": ("s[6] = -(xy_im - yx_im);", "s[6] = -(xy_re - yx_re);"),
+    "I_im_dropped_yy": ("s[1] = xx_im + yy_im;", "s[1] = xx_im;"),
+    # Section 2.1 / Table 1
+    "tau_minus_one_outside": ("return lead * (Wd * s2 / (s12 + eps) - 1.0);",
+                              "return lead * (Wd * s2 / (s12 + eps)) - 1.0;"),
+    "tau_lead_W_not_W_minus_1": ("(Wd * d + 1.0) / (Wd - 1.0);", "(Wd * d + 1.0) / (Wd);"),
+    "S1_sums_power": ("acc_add(&S1, z, compensated);", "acc_add(&S1, y, compensated);"),
+    "eps_dropped_from_S1sq": ("/ (s12 + eps) - 1.0", "/ (s12) - 1.0"),
+    # Section 2.2 / Table 2
+    "r_not_divided_by_W": ("return sqrt(qb + ub + vb) / (double)W;", "return sqrt(qb + ub + vb);"),
+    "p_without_sqrt": ("const double p = sqrt(a + b + c) + eps;", "const double p = (a + b + c) + eps;"),
+    "v_from_wrong_part": ("const double v = stokes[8 * i + 6 + part];",
+                          "const double v = stokes[8 * i + 7 - part];"),
+    "eps_dropped_from_p": ("const double p = sqrt(a + b + c) + eps;", "const double p = sqrt(a + b + c);"),
+    # flag rule
+    "sk_and_ds": ("return f_sk | (f_re | f_im);", "return f_sk & (f_re | f_im);"),
+    "im_part_ignored": ("return f_sk | (f_re | f_im);", "return f_sk | f_re;"),
+    "flag_bit_shifted": ("(uint32_t)1u << (ts % 32)", "(uint32_t)1u << ((ts + 1) % 32)"),
+    # averaging and carry
+    "avg_divides_by_K": ("acc_val(&bin[c]) / bin_n", "acc_val(&bin[c]) / (double)K"),
+    "weight_counts_windows": ("weight[(size_t)row * n_out + b] = bin_n / (double)K;",
+                              "weight[(size_t)row * n_out + b] = bin_n / (double)W / (double)K;"),
+    "flagged_samples_averaged": ("if (!f) {\n                for (int i = 0; i < W; ++i)",
+                                 "if (1) {\n                for (int i = 0; i < W; ++i)"),
+    "carry_dropped": ("bin[c].s = carry_sum[(size_t)row * 8 + c]; bin[c].c = 0;",
+                      "bin[c].s = 0; bin[c].c = 0;"),
+}
+
+
+@pytest.fixture(scope="module")
+def src():
+    with open(oracle.build.SRC) as f:
+        return f.read()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, src, tmp_path):
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mutated = tmp_path / "rfi_oracle_mutant.c"
+    mutated.write_text(src.replace(old, new))
+    lib = oracle.build.compile_source(str(mutated), str(tmp_path / "libmutant.so"))
+    oracle.oracle.use_library(lib)
+    try:
+        caught = []
+        for pin in oracle_pins.ALL_PINS:
+            try:
+                pin()
+            except (AssertionError, ValueError, FloatingPointError):
+                caught.append(pin.__name__)
+                break
+        assert caught, f"no pin detects mutant {name}"
+    finally:
+        oracle.oracle.use_library(None)
+    assert os.path.exists(lib)
