@@ -1,0 +1,339 @@
+"""Throughput of the sm_103a online RFI flagging path (arXiv 2412.14775).
+
+One step = one rfi_process_block call on a whole LOFAR-scale block: 62 stations
+(1953 baselines incl. autocorrelations), 64 channels, 256 samples, 4 correlations
+complex64 (1.02 GB), window M = 16, averaging 256 -> 1: Stokes, spectral kurtosis,
+directional statistics (Re, Im), flags, flag packing and flagged averaging, all in
+one kernel launch.  Inputs are 1 GB, far larger than the 126 MB L2, so no L2 flush
+is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("visibility samples/sec and HBM GB/s (% of peak), FP16 vs FP32; "
+          "p99 latency vs real time")
+WORKLOAD = dict(workload="lofar-scale block", stations=62, baselines=1953, channels=64,
+                samples_per_block=256, window_M=16, avg_K=256, correlations=4)
+BLOCK_SECONDS = 256 * 0.5e-3       # 2000 samples ~ 1 s in the paper's simulations
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def algo_bytes(R, T, M, K, n_out, sample_bytes):
+    """Bytes the method must move per launch: input, flag words, stats, averages."""
+    return R * (T * sample_bytes + 4 * math.ceil(T / 32) + 12 * (T // M) + 36 * n_out)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    from paper_2412_14775_b300.thresholds import default_thresholds
+    M, K, T = 16, 256, 256
+    thr = default_thresholds(M)
+    d = synth.lofar_block(seed=2)
+    R = d["vis"].shape[0] * d["vis"].shape[1]
+    rows = d["vis"].reshape(R, T, 4, 2)
+    # size each step's sample so that warm-up plus timed steps take about a minute
+    t0 = time.perf_counter()
+    oracle.OracleStream(512, M, K, **thr).process(rows[:512])
+    per_row = (time.perf_counter() - t0) / 512
+    budget = 60.0 / (args.warmup + args.steps)
+    n_rows = int(min(R, max(16, budget / max(per_row, 1e-9))))
+    if args.ref_rows:
+        n_rows = min(n_rows, args.ref_rows)
+    times = []
+    for step in range(args.warmup + args.steps):
+        sel = rows[(step * n_rows) % R:(step * n_rows) % R + n_rows]
+        st = oracle.OracleStream(len(sel), M, K, **thr)
+        t0 = time.perf_counter()
+        st.process(sel)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append((len(sel) * T, dt))
+    samples = sum(s for s, _ in times)
+    secs = sum(t for _, t in times)
+    v = samples / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, dtype="complex64"),
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n_rows} of {R} rows x {T} samples per step"},
+            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seconds_target=10.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the block."""
+    import oracle
+    import synth
+    from paper_2412_14775_b300.thresholds import default_thresholds
+    M, K, T = 16, 256, 256
+    thr = default_thresholds(M)
+    d = synth.lofar_block(seed=2)
+    R = d["vis"].shape[0] * d["vis"].shape[1]
+    rows = d["vis"].reshape(R, T, 4, 2)
+    t0 = time.perf_counter()
+    oracle.OracleStream(256, M, K, **thr).process(rows[:256])
+    per_row = (time.perf_counter() - t0) / 256
+    n = int(min(R, max(256, seconds_target / max(per_row, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.OracleStream(n, M, K, **thr).process(rows[:n])
+    dt = time.perf_counter() - t0
+    return {"value": n * T / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} of {R} rows x {T} samples of the FP32 block, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler_index=None):
+    """Warm up, then time `steps` launches with per-launch CUDA events on the
+    launching stream (the device time of the flagging kernel)."""
+    for _ in range(warmup):
+        stream_obj.process(vis, out=out, stream=cuda_stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    sampler = ClockSampler(sampler_index) if sampler_index is not None else None
+    if sampler:
+        sampler.__enter__()
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(cuda_stream)
+    for a, b in ev:
+        a.record(cuda_stream)
+        stream_obj.process(vis, out=out, stream=cuda_stream)
+        b.record(cuda_stream)
+    t_all1.record(cuda_stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__()
+    per = [a.elapsed_time(b) * 1e-3 for a, b in ev]
+    total = t_all0.elapsed_time(t_all1) * 1e-3
+    return total, per, (sampler.summary() if sampler else None)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-rows", type=int, default=0, help="cap on oracle rows per step")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile", default="", help="lanes_per_row,warps_per_block override")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2412_14775_b300 import RfiStream, default_thresholds
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peak, peak_kind = _peaks()
+    M, K, T = 16, 256, 256
+    thr = default_thresholds(M)
+    opts = {}
+    if args.tile:
+        p, w = args.tile.split(",")
+        opts = dict(lanes_per_row=int(p), warps_per_block=int(w))
+
+    d = synth.lofar_block(seed=2 + rank)
+    R = d["vis"].shape[0] * d["vis"].shape[1]
+    host32 = torch.from_numpy(d["vis"].reshape(R, T, 4, 2))
+    vis32 = host32.to(dev)
+    st = RfiStream(62, 64, M, K, thr, "f32", **opts)
+    out = st.alloc_outputs(T, device=dev)
+    cs = torch.cuda.current_stream(dev)
+
+    if ws > 1:
+        dist.barrier()
+    total, per, clocks = time_kernel(st, vis32, out, args.steps, args.warmup, torch, cs,
+                                     sampler_index=local)
+    if ws > 1:
+        t = torch.tensor([total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    samples = R * T
+    value = ws * samples * args.steps / total
+    n_out = 1
+    bytes_launch = algo_bytes(R, T, M, K, n_out, 32)
+    kern = statistics.mean(per)
+    achieved = bytes_launch / kern / 1e9
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # FP16 storage (same geometry), window sweep
+        fp16 = {}
+        host16 = host32.half()
+        vis16 = host16.to(dev)
+        del vis32
+        for Mw in (8, 16, 32, 64):
+            s16 = RfiStream(62, 64, Mw, 256, default_thresholds(Mw), "f16", **opts)
+            o16 = s16.alloc_outputs(T, device=dev)
+            tot16, per16, _ = time_kernel(s16, vis16, o16, max(200, args.steps // 4), args.warmup,
+                                          torch, cs)
+            b16 = algo_bytes(R, T, Mw, 256, 1, 16)
+            k16 = statistics.mean(per16)
+            fp16[f"M{Mw}"] = {"samples_per_s": samples * len(per16) / tot16,
+                              "kernel_us": k16 * 1e6, "achieved_gbs": b16 / k16 / 1e9,
+                              "frac": b16 / k16 / 1e9 / peak,
+                              "lanes_per_row": s16.options["lanes_per_row"]}
+            s16.close()
+        extras["fp16"] = fp16
+        del vis16
+        torch.cuda.empty_cache()
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        hst = RfiStream(62, 64, M, K, thr, "f32", host_max_T=T, host_chunks=8, **opts)
+        hin = host32.pin_memory()
+        hout = hst.alloc_outputs(T, device="cpu", pin_memory=True)
+        for _ in range(3):
+            hst.process_host(hin, out=hout)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            hst.process_host(hin, out=hout)
+            _ = float(hout["weight"][0, 0])        # the result is read on the host
+        dt = time.perf_counter() - t0
+        d2h = sum(x.numel() * x.element_size() for x in hout.values())
+        e2e = {"value": samples * args.e2e_steps / dt, "unit": "samples/s",
+               "h2d_bytes_per_step": hin.numel() * hin.element_size(),
+               "d2h_bytes_per_step": d2h}
+        hst.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": dict(WORKLOAD, dtype="complex64", l2="inputs 1.02 GB > 126 MB L2, no flush",
+                           lanes_per_row=st.options["lanes_per_row"],
+                           warps_per_block=st.options["warps_per_block"]),
+            "hbm_gbs": achieved * ws,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind, "kernel_us": kern * 1e6,
+                         "algorithmic_bytes_per_launch": bytes_launch},
+            "frac_of_8tbs": achieved / 8000.0,
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": args.steps,
+            "real_time_factor": BLOCK_SECONDS / kern,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * rfi.h -- C ABI of the B300 (sm_103a) online RFI flagging library.
+ *
+ * The library implements the online interference mitigation of Yatawatta, Boonstra
+ * and Broekema, "Energy and polarization based online interference mitigation in
+ * radio interferometry" (arXiv 2412.14775):
+ *   - complex Stokes I, Q, U, V of every sample (Section 2, Eq. IQUV);
+ *   - over each window of M consecutive samples, the spectral-kurtosis statistic
+ *       tau = (M d + 1)/(M - 1) * (M S2 / (S1^2 + eps) - 1),
+ *       S1 = sum |I|, S2 = sum |I|^2                    (Section 2.1, Table 1);
+ *   - the directional statistic of the normalised polarisation vector, separately
+ *     for the real and the imaginary parts of (Q, U, V):
+ *       p = sqrt(q^2 + u^2 + v^2) + eps, r = |sum (q, u, v)/p| / M
+ *                                                       (Section 2.2, Table 2);
+ *   - window flag = (tau < s_low) OR (tau > s_high) OR (r_Re > gamma) OR
+ *     (r_Im > gamma); a NaN statistic also flags       (Sections 2.1, 2.2);
+ *   - flagged samples are left out of the time average and the weight of each
+ *     averaged output is the unflagged fraction        (end of Section 2.1).
+ *
+ * Terms.  A "stream" is one subband: R = B * C rows, B = N(N+1)/2 baselines of N
+ * stations including autocorrelations (Section 2: each of the N(N+1)/2 correlator
+ * streams is mitigated separately) and C channels.  Each row is one (baseline,
+ * channel) time series; rows are independent.  Blocks of T samples of all rows
+ * arrive one after another; windows and averaging bins are counted from the
+ * stream's first sample and continue across blocks.
+ *
+ * Conventions for every function:
+ *   - Every function returns an rfi_status (int).  No C++ exception crosses the ABI.
+ *   - Buffers passed to rfi_process_* are caller-owned DEVICE pointers (e.g. the
+ *     data pointer of a CUDA tensor) unless the function name ends in _host.  The
+ *     library checks that each is device-accessible and suitably aligned and returns
+ *     RFI_EINVAL otherwise; it never dereferences a host pointer on the device.
+ *   - A context owns its device state (averaging carry, task counter), allocated in
+ *     rfi_create*; rfi_process_block and rfi_process_batch allocate nothing, do not
+ *     synchronise the stream and may be captured in a CUDA graph.
+ *   - One context is used by one host thread at a time; work for one context must
+ *     be issued in stream order (a context's carry is read and written by each call).
+ *   - A CUDA error seen by a context makes it sticky-failed (RFI_ESTATE) until
+ *     rfi_reset.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL = the legacy
+ *     default stream).
+ */
+#ifndef RFI_H
+#define RFI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rfi_ctx rfi_ctx;
+
+/* Input sample formats.  One sample = the 4 correlations xx, xy, yx, yy of one
+ * (baseline, channel, time) point (Section 2, Eq. V), each as (re, im). */
+typedef enum {
+    RFI_C64  = 0,   /* float32 re, im x 4 = 32 bytes per sample                   */
+    RFI_C32H = 1    /* IEEE binary16 re, im x 4 = 16 bytes per sample; arithmetic
+                       after exact widening to float32 (FP16 storage, FP32 math)   */
+} rfi_dtype;
+
+/* Thresholds (Sections 2.1-2.3).  d: SK shape parameter; [s_low, s_high]: SK
+ * acceptance interval; gamma: directional-statistic threshold; eps: the additive
+ * constant of Tables 1 and 2 (added to S1^2 and to p).  Stored on the device as
+ * float32 (the kernels compare in float32). */
+typedef struct {
+    double d, s_low, s_high, gamma, eps;
+} rfi_thresholds;
+
+typedef enum {
+    RFI_OK           = 0,
+    RFI_EINVAL       = 1,   /* bad argument: size, alignment, pointer kind, layout */
+    RFI_ENOMEM       = 2,   /* device or pinned-host allocation failed in create   */
+    RFI_ECUDA        = 3,   /* a CUDA runtime call failed (context becomes sticky) */
+    RFI_ETIMEOUT     = 4,   /* a bounded device wait gave up (reserved)            */
+    RFI_ESTATE       = 5,   /* context is sticky-failed, destroyed or misused      */
+    RFI_EUNSUPPORTED = 6    /* valid request this build has no kernel for          */
+} rfi_status;
+
+/* Launch shape of the flagging kernel.  Zero fields mean "choose automatically".
+ *   lanes_per_row  P: lanes of a warp that share one row; a power of two in
+ *                  {1, 2, 4, 8, 16, 32}; each lane owns every P-th load unit of a
+ *                  window (a load unit is 32 bytes: one C64 sample or two C32H
+ *                  samples; 16 bytes = one sample for C32H when M is odd).
+ *   warps_per_block  1..32.
+ *   host_max_T     > 0: also allocate device staging for rfi_process_block_host
+ *                  with blocks of up to host_max_T samples.
+ *   host_chunks    row chunks pipelined by rfi_process_block_host (copy in,
+ *                  compute and copy out overlap across chunks); 0 = 4.
+ *   compensated    Kahan-compensated S1 and S2 (the SK moments): 1 = on, -1 = off,
+ *                  0 = on for windows of M >= 64 samples.
+ * The reduction order of a window depends only on (M, P, load unit), so two
+ * contexts with the same shape give bit-identical results for the same data,
+ * whether launched alone or inside a batch. */
+typedef struct {
+    int lanes_per_row;
+    int warps_per_block;
+    int host_max_T;
+    int host_chunks;
+    int compensated;
+} rfi_options;
+
+/* Create a context for one stream of `stations` stations (B = N(N+1)/2 baselines)
+ * and `channels` channels, window M = window_M >= 2 samples and output averaging
+ * factor K = avg_K samples (K a multiple of M).  Allocates the device state on the
+ * current CUDA device.  *out is set to NULL on failure. */
+int rfi_create(rfi_ctx **out, int stations, int channels, int window_M, int avg_K,
+               const rfi_thresholds *thr, rfi_dtype dtype);
+int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int avg_K,
+                  const rfi_thresholds *thr, rfi_dtype dtype, const rfi_options *opt);
+
+/* Rows R = B * C of the stream. */
+int rfi_rows(const rfi_ctx *ctx, long long *rows);
+
+/* Number of averaged outputs per row that the next rfi_process_block with T
+ * samples will complete: floor((n_seen + T)/K) - floor(n_seen/K), where n_seen is
+ * the number of samples already processed. */
+int rfi_outputs_for(const rfi_ctx *ctx, int T, int *n_out);
+
+/* The launch shape the context uses (after automatic choice). */
+int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt);
+
+/* Replace the thresholds (takes effect for work issued afterwards). */
+int rfi_set_thresholds(rfi_ctx *ctx, const rfi_thresholds *thr);
+
+/* Process one block of T samples (T a positive multiple of M) of every row.
+ *   vis    [R][T][4 correlations][re, im] in the context's dtype; 32-byte aligned.
+ *   flags  [R][ceil(T/32)] uint32: bit (t mod 32) of word t/32 is 1 when sample t
+ *          of the row lies in a flagged window (the flag applies to all 4
+ *          correlations).  Bits at t >= T are 0.  4-byte aligned.
+ *   avg    [R][n_out][4][re, im] float32: mean of the unflagged samples of every
+ *          averaging bin that completes in this call (n_out = rfi_outputs_for);
+ *          0 where every sample of the bin was flagged.  16-byte aligned.
+ *   weight [R][n_out] float32: unflagged samples of the bin / K.
+ *   stats  [3][R][T/M] float32: tau, r_Re, r_Im of every window (SoA).
+ * avg and weight may be NULL only when n_out == 0.  Asynchronous on `stream`. */
+int rfi_process_block(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags, float *avg,
+                      float *weight, float *stats, void *stream);
+
+/* As rfi_process_block, but every buffer is in HOST memory (page-locked memory
+ * lets the copies overlap).  Copies the block in through the context's device
+ * staging (requires host_max_T >= T at create), runs the kernel per row chunk and
+ * copies the outputs back; returns after the outputs are in host memory. */
+int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags,
+                           float *avg, float *weight, float *stats, void *stream);
+
+/* Process one block for each of n contexts in ONE persistent launch.  All contexts
+ * must share dtype, M and lanes_per_row (else RFI_EINVAL); T[i], sizes and layouts
+ * per context are as for rfi_process_block.  Warps take (context, row group) tasks
+ * from a device counter owned by ctxs[0]; two batches that share ctxs[0] must not
+ * run concurrently.  Results are bit-identical to rfi_process_block on each
+ * context alone. */
+int rfi_process_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *T,
+                      uint32_t *const *flags, float *const *avg, float *const *weight,
+                      float *const *stats, void *stream);
+
+/* A batch captured once in a CUDA graph and replayed.  rfi_batch_graph_create
+ * fixes the contexts and block lengths; each rfi_batch_graph_launch supplies this
+ * step's buffers, updates the captured kernel's parameters (no allocation) and
+ * launches the graph on `stream`. */
+typedef struct rfi_batch_graph rfi_batch_graph;
+int rfi_batch_graph_create(rfi_batch_graph **out, rfi_ctx *const *ctxs, int n, const int *T);
+int rfi_batch_graph_launch(rfi_batch_graph *g, const void *const *vis, uint32_t *const *flags,
+                           float *const *avg, float *const *weight, float *const *stats,
+                           void *stream);
+int rfi_batch_graph_destroy(rfi_batch_graph *g);
+
+/* Drop the averaging carry and the sample count (stream restart); clears a sticky
+ * error.  Synchronises with work already issued for the context. */
+int rfi_reset(rfi_ctx *ctx);
+
+/* Free the context and its device state.  rfi_destroy(NULL) is a no-op. */
+int rfi_destroy(rfi_ctx *ctx);
+
+/* Static description of a status code. */
+const char *rfi_status_str(int status);
+
+/* Text of the last error recorded by the library on the calling thread. */
+const char *rfi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RFI_H */

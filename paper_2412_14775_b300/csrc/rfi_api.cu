@@ -1,0 +1,734 @@
+// rfi_api.cu -- C ABI of the online RFI flagging library (declared in include/rfi.h).
+//
+// Host responsibilities: argument and pointer validation (every device buffer is
+// checked to be device memory of the context's GPU, aligned, and large enough for
+// what the kernel will touch, before any launch), per-context state (thresholds,
+// sample count, carry), launch-shape choice, the host-buffer pipeline and the
+// persistent batch launch, optionally replayed from a CUDA graph.
+#include "rfi.h"
+#include "rfi_device.cuh"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <vector>
+
+using namespace rfi;
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail(int status, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+// ---- kernel instance table ------------------------------------------------------
+typedef void (*BlockFn)(StreamArgs);
+typedef void (*BatchFn)(BatchArgs);
+
+struct Instance {
+    int dt, spu, P, ch, kahan;
+    const void *block_fn;
+    const void *batch_fn;
+};
+
+#define RFI_INST(DT, SPU, P, CH, K)                                                         \
+    {DT, SPU, P, CH, K, (const void *)&k_block<DT, SPU, P, CH, (bool)K>,                   \
+     (const void *)&k_batch<DT, SPU, P, CH, (bool)K>}
+#define RFI_INST_CH(DT, SPU, P, K)                                                           \
+    RFI_INST(DT, SPU, P, 1, K), RFI_INST(DT, SPU, P, 2, K), RFI_INST(DT, SPU, P, 4, K),     \
+        RFI_INST(DT, SPU, P, 5, K), RFI_INST(DT, SPU, P, 8, K)
+#define RFI_INST_P(DT, SPU, K)                                                               \
+    RFI_INST_CH(DT, SPU, 1, K), RFI_INST_CH(DT, SPU, 2, K), RFI_INST_CH(DT, SPU, 4, K),     \
+        RFI_INST_CH(DT, SPU, 8, K), RFI_INST_CH(DT, SPU, 16, K), RFI_INST_CH(DT, SPU, 32, K)
+
+const Instance g_instances[] = {
+    RFI_INST_P(DT_F32, 1, 0),
+    RFI_INST_P(DT_F16, 2, 0),
+    RFI_INST_P(DT_F32, 1, 1),
+    RFI_INST_P(DT_F16, 2, 1),
+    // binary16 input with an odd window: one sample per 16-byte unit, one lane per row
+    RFI_INST_CH(DT_F16, 1, 1, 0),
+    RFI_INST_CH(DT_F16, 1, 1, 1),
+};
+
+const Instance *find_instance(int dt, int spu, int P, int ch, int kahan) {
+    for (const Instance &in : g_instances)
+        if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan)
+            return &in;
+    return nullptr;
+}
+
+int largest_chunk(int S) {
+    static const int opts[] = {8, 5, 4, 2, 1};
+    for (int c : opts)
+        if (S % c == 0) return c;
+    return 1;
+}
+
+constexpr unsigned int CTX_MAGIC = 0x52464931u;  // "RFI1"
+std::mutex g_live_mu;
+std::set<const void *> g_live;                     // live contexts and graphs
+
+bool is_live(const void *p) {
+    std::lock_guard<std::mutex> lk(g_live_mu);
+    return g_live.count(p) != 0;
+}
+
+// cuMemGetAddressRange through the runtime's driver entry point (no libcuda link).
+typedef CUresult (*PFN_range)(CUdeviceptr *, size_t *, CUdeviceptr);
+PFN_range get_range_fn() {
+    static PFN_range fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_range>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+struct rfi_ctx {
+    unsigned int magic;
+    int device;
+    int stations, channels, M, K;
+    long long B, C, R;
+    rfi_dtype dtype;
+    rfi_thresholds thr;
+    int P, spu, S, ch, kahan, wpb;
+    const Instance *inst;
+    long long n_seen;
+    int status;
+    float *carry;                       // [R][P][9]
+    unsigned long long *counter;        // [2]: batch task counter, blocks done
+    // host-buffer path
+    int host_max_T, host_chunks;
+    char *h_vis;
+    uint32_t *h_flags;
+    float *h_avg, *h_weight, *h_stats;
+    cudaStream_t s_in, s_run, s_out;
+    cudaEvent_t ev_start, ev_done;
+    std::vector<cudaEvent_t> ev_in, ev_run;
+};
+
+struct rfi_batch_graph {
+    int n;
+    std::vector<rfi_ctx *> ctxs;
+    std::vector<int> T;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaGraphNode_t node;
+    const Instance *inst;
+    int grid, block;
+};
+
+namespace {
+
+int sample_bytes(rfi_dtype dt) { return dt == RFI_C64 ? 32 : 16; }
+
+int check_ctx(const rfi_ctx *ctx) {
+    if (!ctx) return fail(RFI_EINVAL, "null context");
+    if (!is_live(ctx) || ctx->magic != CTX_MAGIC)
+        return fail(RFI_ESTATE, "context was destroyed or is not a context");
+    if (ctx->status != RFI_OK)
+        return fail(RFI_ESTATE, "context is sticky-failed (%s); call rfi_reset",
+                    rfi_status_str(ctx->status));
+    return RFI_OK;
+}
+
+// A device buffer must be device (or managed) memory of `device`, aligned to
+// `align`, and [p, p + bytes) must lie inside one allocation.
+int check_dev(const void *p, size_t bytes, size_t align, int device, const char *what) {
+    if (bytes == 0) return RFI_OK;
+    if (!p) return fail(RFI_EINVAL, "%s: null pointer", what);
+    if (reinterpret_cast<uintptr_t>(p) % align)
+        return fail(RFI_EINVAL, "%s: pointer not %zu-byte aligned", what, align);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RFI_EINVAL, "%s: not a CUDA pointer (%s)", what, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(RFI_EINVAL, "%s: not device memory", what);
+    if (at.type == cudaMemoryTypeDevice && at.device != device)
+        return fail(RFI_EINVAL, "%s: memory of device %d, context on device %d", what,
+                    at.device, device);
+    PFN_range range = get_range_fn();
+    if (range) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (range(&base, &size, reinterpret_cast<CUdeviceptr>(p)) == CUDA_SUCCESS) {
+            const uintptr_t end = static_cast<uintptr_t>(base) + size;
+            if (reinterpret_cast<uintptr_t>(p) + bytes > end)
+                return fail(RFI_EINVAL, "%s: buffer holds %zu bytes from this pointer, need %zu",
+                            what, (size_t)(end - reinterpret_cast<uintptr_t>(p)), bytes);
+        }
+    }
+    return RFI_OK;
+}
+
+int check_thresholds(const rfi_thresholds *t) {
+    if (!t) return fail(RFI_EINVAL, "null thresholds");
+    if (std::isnan(t->d) || std::isnan(t->s_low) || std::isnan(t->s_high) ||
+        std::isnan(t->gamma) || std::isnan(t->eps))
+        return fail(RFI_EINVAL, "thresholds must not be NaN");
+    if (!std::isfinite(t->d) || !std::isfinite(t->eps) || t->eps < 0)
+        return fail(RFI_EINVAL, "d must be finite and eps finite and >= 0");
+    if (t->s_low > t->s_high) return fail(RFI_EINVAL, "s_low > s_high");
+    return RFI_OK;
+}
+
+int choose_shape(rfi_ctx *c, int P_req) {
+    const int dt = c->dtype == RFI_C64 ? DT_F32 : DT_F16;
+    // samples per 32-byte load unit: binary16 packs two samples when M is even
+    int spu = (dt == DT_F16 && c->M % 2 == 0) ? 2 : 1;
+    int P = P_req;
+    if (P == 0) {
+        P = 2;
+        while (P > 1 && (c->M % (P * spu)) != 0) P >>= 1;
+    }
+    if (P != 1 && P != 2 && P != 4 && P != 8 && P != 16 && P != 32)
+        return fail(RFI_EINVAL, "lanes_per_row must be a power of two <= 32");
+    if (c->M % (P * spu) != 0) {
+        if (dt == DT_F16 && spu == 2 && P_req != 0) {
+            return fail(RFI_EINVAL, "window M=%d is not a multiple of 2*lanes_per_row=%d", c->M,
+                        2 * P);
+        }
+        return fail(RFI_EINVAL, "window M=%d is not a multiple of lanes_per_row=%d", c->M, P);
+    }
+    if (dt == DT_F16 && spu == 1 && P != 1)
+        return fail(RFI_EINVAL, "odd windows of binary16 input need lanes_per_row = 1");
+    c->P = P;
+    c->spu = spu;
+    c->S = c->M / (P * spu);
+    c->ch = largest_chunk(c->S);
+    c->inst = find_instance(dt, spu, P, c->ch, c->kahan);
+    if (!c->inst) return fail(RFI_EUNSUPPORTED, "no kernel for this launch shape");
+    return RFI_OK;
+}
+
+StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, float *avg,
+                     float *weight, float *stats, long long r0, long long nrows) {
+    StreamArgs a;
+    const int nwin = T / c->M;
+    const int Wpr = (T + 31) / 32;
+    const long long n_out = (c->n_seen + T) / c->K - c->n_seen / c->K;
+    a.vis = static_cast<const char *>(vis) + r0 * (long long)T * sample_bytes(c->dtype);
+    a.flags = flags + r0 * Wpr;
+    a.avg = avg ? avg + r0 * n_out * 8 : nullptr;
+    a.weight = weight ? weight + r0 * n_out : nullptr;
+    a.stats = stats + r0 * nwin;
+    a.carry = c->carry + r0 * c->P * 9;
+    a.R = nrows;
+    a.stats_plane = c->R * nwin;
+    a.T = T;
+    a.M = c->M;
+    a.K = c->K;
+    a.Wpr = Wpr;
+    a.nwin = nwin;
+    a.n_out = (int)n_out;
+    a.bin_pos0 = (int)(c->n_seen % c->K);
+    const double Md = c->M;
+    a.c0 = (float)((Md * c->thr.d + 1.0) / (Md - 1.0));
+    a.s_low = (float)c->thr.s_low;
+    a.s_high = (float)c->thr.s_high;
+    a.gamma = (float)c->thr.gamma;
+    a.eps = (float)c->thr.eps;
+    a.fM = (float)c->M;
+    a.fK = (float)c->K;
+    return a;
+}
+
+int check_block_args(const rfi_ctx *c, const void *vis, int T, const uint32_t *flags,
+                     const float *avg, const float *weight, const float *stats, bool device) {
+    if (T <= 0 || T % c->M != 0)
+        return fail(RFI_EINVAL, "T=%d must be a positive multiple of M=%d", T, c->M);
+    if ((long long)T * c->R > (1ll << 40)) return fail(RFI_EINVAL, "block too large");
+    const long long n_out = (c->n_seen + T) / c->K - c->n_seen / c->K;
+    const size_t sb = sample_bytes(c->dtype);
+    const size_t vis_align = (size_t)sb * c->spu;
+    const size_t R = (size_t)c->R;
+    const size_t nw = T / c->M, wpr = (T + 31) / 32;
+    if (!device) {
+        if (!vis || !flags || !stats || (n_out > 0 && (!avg || !weight)))
+            return fail(RFI_EINVAL, "null host buffer");
+        return RFI_OK;
+    }
+    int rc;
+    if ((rc = check_dev(vis, R * T * sb, vis_align, c->device, "vis"))) return rc;
+    if ((rc = check_dev(flags, R * wpr * 4, 4, c->device, "flags"))) return rc;
+    if ((rc = check_dev(stats, 3 * R * nw * 4, 4, c->device, "stats"))) return rc;
+    if (n_out > 0) {
+        if ((rc = check_dev(avg, R * n_out * 32, 16, c->device, "avg"))) return rc;
+        if ((rc = check_dev(weight, R * n_out * 4, 4, c->device, "weight"))) return rc;
+    }
+    return RFI_OK;
+}
+
+int set_cuda_error(rfi_ctx *c, cudaError_t e, const char *where) {
+    c->status = RFI_ECUDA;
+    return fail(RFI_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
+    if (a.R <= 0) return RFI_OK;
+    const int RW = 32 / c->P;
+    const long long groups = (a.R + RW - 1) / RW;
+    const long long blocks = (groups + c->wpb - 1) / c->wpb;
+    void *args[] = {const_cast<StreamArgs *>(&a)};
+    cudaError_t e = cudaLaunchKernel(c->inst->block_fn, dim3((unsigned)blocks),
+                                     dim3(32 * c->wpb), args, 0, st);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "kernel launch");
+    return RFI_OK;
+}
+
+// Resident blocks of a batch kernel on the whole GPU (cached per kernel, block size
+// and device).
+int persistent_grid(const Instance *in, int wpb, int device) {
+    struct Entry { const void *fn; int wpb, device, grid; };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry &e : cache)
+        if (e.fn == in->batch_fn && e.wpb == wpb && e.device == device) return e.grid;
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, in->batch_fn, 32 * wpb, 0) !=
+            cudaSuccess ||
+        per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    cache.push_back({in->batch_fn, wpb, device, std::max(sms, 1) * per});
+    return cache.back().grid;
+}
+
+int build_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *T,
+                uint32_t *const *flags, float *const *avg, float *const *weight,
+                float *const *stats, bool validate_buffers, BatchArgs *b) {
+    if (n < 1 || n > MAX_BATCH) return fail(RFI_EINVAL, "batch size %d not in [1, %d]", n, MAX_BATCH);
+    if (!ctxs || !T) return fail(RFI_EINVAL, "null batch arrays");
+    int rc;
+    for (int i = 0; i < n; ++i) {
+        if ((rc = check_ctx(ctxs[i]))) return rc;
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return fail(RFI_EINVAL, "context %d appears twice", i);
+        if (ctxs[i]->inst != ctxs[0]->inst || ctxs[i]->device != ctxs[0]->device)
+            return fail(RFI_EINVAL, "context %d differs in dtype, M or launch shape", i);
+    }
+    b->n = n;
+    b->counter = ctxs[0]->counter;
+    long long tot = 0;
+    for (int i = 0; i < n; ++i) {
+        const rfi_ctx *c = ctxs[i];
+        if (validate_buffers) {
+            if (!vis || !flags || !avg || !weight || !stats)
+                return fail(RFI_EINVAL, "null batch buffer arrays");
+            if ((rc = check_block_args(c, vis[i], T[i], flags[i], avg[i], weight[i], stats[i],
+                                       true)))
+                return rc;
+            b->s[i] = make_args(c, vis[i], T[i], flags[i], avg[i], weight[i], stats[i], 0, c->R);
+        } else {
+            if (T[i] <= 0 || T[i] % c->M != 0)
+                return fail(RFI_EINVAL, "T[%d]=%d must be a positive multiple of M", i, T[i]);
+            b->s[i] = make_args(c, nullptr, T[i], nullptr, nullptr, nullptr, nullptr, 0, c->R);
+        }
+        b->prefix[i] = tot;
+        tot += (c->R + 32 / c->P - 1) / (32 / c->P);
+    }
+    b->prefix[n] = tot;
+    for (int i = n + 1; i <= MAX_BATCH; ++i) b->prefix[i] = tot;
+    b->total = tot;
+    return RFI_OK;
+}
+
+void free_ctx(rfi_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->carry) cudaFree(c->carry);
+    if (c->counter) cudaFree(c->counter);
+    if (c->h_vis) cudaFree(c->h_vis);
+    if (c->h_flags) cudaFree(c->h_flags);
+    if (c->h_avg) cudaFree(c->h_avg);
+    if (c->h_weight) cudaFree(c->h_weight);
+    if (c->h_stats) cudaFree(c->h_stats);
+    for (cudaEvent_t e : c->ev_in) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_run) cudaEventDestroy(e);
+    if (c->ev_start) cudaEventDestroy(c->ev_start);
+    if (c->ev_done) cudaEventDestroy(c->ev_done);
+    if (c->s_in) cudaStreamDestroy(c->s_in);
+    if (c->s_run) cudaStreamDestroy(c->s_run);
+    if (c->s_out) cudaStreamDestroy(c->s_out);
+    c->magic = 0;
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rfi_status_str(int s) {
+    switch (s) {
+        case RFI_OK: return "RFI_OK";
+        case RFI_EINVAL: return "RFI_EINVAL: invalid argument";
+        case RFI_ENOMEM: return "RFI_ENOMEM: allocation failed";
+        case RFI_ECUDA: return "RFI_ECUDA: CUDA error";
+        case RFI_ETIMEOUT: return "RFI_ETIMEOUT: bounded device wait expired";
+        case RFI_ESTATE: return "RFI_ESTATE: context failed, destroyed or misused";
+        case RFI_EUNSUPPORTED: return "RFI_EUNSUPPORTED: no kernel for this request";
+        default: return "unknown rfi status";
+    }
+}
+
+const char *rfi_last_error(void) { return g_last_error; }
+
+int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int avg_K,
+                  const rfi_thresholds *thr, rfi_dtype dtype, const rfi_options *opt) {
+    if (!out) return fail(RFI_EINVAL, "null output handle");
+    *out = nullptr;
+    if (stations < 1 || channels < 1) return fail(RFI_EINVAL, "stations and channels must be >= 1");
+    if (window_M < 2) return fail(RFI_EINVAL, "window M must be >= 2 (tau divides by M-1)");
+    if (avg_K < window_M || avg_K % window_M != 0)
+        return fail(RFI_EINVAL, "averaging factor K=%d must be a positive multiple of M=%d", avg_K,
+                    window_M);
+    if (dtype != RFI_C64 && dtype != RFI_C32H) return fail(RFI_EINVAL, "unknown dtype");
+    int rc;
+    if ((rc = check_thresholds(thr))) return rc;
+    rfi_options o = {0, 0, 0, 0, 0};
+    if (opt) o = *opt;
+    if (o.warps_per_block < 0 || o.warps_per_block > 16 || o.host_max_T < 0 || o.host_chunks < 0 ||
+        o.compensated < -1 || o.compensated > 1)
+        return fail(RFI_EINVAL, "bad options");
+
+    rfi_ctx *c = new (std::nothrow) rfi_ctx();
+    if (!c) return fail(RFI_ENOMEM, "host allocation failed");
+    c->magic = CTX_MAGIC;
+    cudaError_t de = cudaGetDevice(&c->device);
+    if (de != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(RFI_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(de));
+    }
+    c->stations = stations;
+    c->channels = channels;
+    c->M = window_M;
+    c->K = avg_K;
+    c->B = (long long)stations * (stations + 1) / 2;
+    c->C = channels;
+    c->R = c->B * c->C;
+    c->dtype = dtype;
+    c->thr = *thr;
+    c->kahan = o.compensated == 1 || (o.compensated == 0 && window_M >= 64);
+    c->wpb = o.warps_per_block ? o.warps_per_block : 8;
+    c->status = RFI_OK;
+    if ((rc = choose_shape(c, o.lanes_per_row))) {
+        delete c;
+        return rc;
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->carry, sizeof(float) * 9 * (size_t)c->P * c->R)) != cudaSuccess ||
+        (e = cudaMalloc(&c->counter, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(c->carry, 0, sizeof(float) * 9 * (size_t)c->P * c->R)) != cudaSuccess ||
+        (e = cudaMemset(c->counter, 0, 2 * sizeof(unsigned long long))) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return fail(e == cudaErrorMemoryAllocation ? RFI_ENOMEM : RFI_ECUDA,
+                    "device allocation failed: %s", cudaGetErrorString(e));
+    }
+    c->host_max_T = o.host_max_T;
+    c->host_chunks = o.host_chunks ? o.host_chunks : 4;
+    if (c->host_max_T > 0) {
+        const int T = c->host_max_T - c->host_max_T % c->M;
+        if (T < c->M) {
+            free_ctx(c);
+            return fail(RFI_EINVAL, "host_max_T smaller than M");
+        }
+        c->host_max_T = T;
+        const size_t R = (size_t)c->R;
+        const size_t n_out_max = (size_t)T / c->K + 1;
+        bool ok = cudaMalloc(&c->h_vis, R * T * sample_bytes(dtype)) == cudaSuccess &&
+                  cudaMalloc(&c->h_flags, R * ((T + 31) / 32) * 4) == cudaSuccess &&
+                  cudaMalloc(&c->h_avg, R * n_out_max * 32) == cudaSuccess &&
+                  cudaMalloc(&c->h_weight, R * n_out_max * 4) == cudaSuccess &&
+                  cudaMalloc(&c->h_stats, 3 * R * (T / c->M) * 4) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&c->s_run, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; ok && i < c->host_chunks; ++i) {
+            cudaEvent_t a, b;
+            ok = cudaEventCreateWithFlags(&a, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b, cudaEventDisableTiming) == cudaSuccess;
+            if (ok) {
+                c->ev_in.push_back(a);
+                c->ev_run.push_back(b);
+            }
+        }
+        if (!ok) {
+            cudaGetLastError();
+            free_ctx(c);
+            return fail(RFI_ENOMEM, "device staging allocation failed");
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        g_live.insert(c);
+    }
+    *out = c;
+    return RFI_OK;
+}
+
+int rfi_create(rfi_ctx **out, int stations, int channels, int window_M, int avg_K,
+               const rfi_thresholds *thr, rfi_dtype dtype) {
+    return rfi_create_ex(out, stations, channels, window_M, avg_K, thr, dtype, nullptr);
+}
+
+int rfi_rows(const rfi_ctx *ctx, long long *rows) {
+    if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
+    if (!rows) return fail(RFI_EINVAL, "null output");
+    *rows = ctx->R;
+    return RFI_OK;
+}
+
+int rfi_outputs_for(const rfi_ctx *ctx, int T, int *n_out) {
+    if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
+    if (!n_out) return fail(RFI_EINVAL, "null output");
+    if (T < 0 || T % ctx->M != 0) return fail(RFI_EINVAL, "T must be a multiple of M");
+    *n_out = (int)((ctx->n_seen + T) / ctx->K - ctx->n_seen / ctx->K);
+    return RFI_OK;
+}
+
+int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
+    if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
+    if (!opt) return fail(RFI_EINVAL, "null output");
+    opt->lanes_per_row = ctx->P;
+    opt->warps_per_block = ctx->wpb;
+    opt->host_max_T = ctx->host_max_T;
+    opt->host_chunks = ctx->host_chunks;
+    opt->compensated = ctx->kahan ? 1 : -1;
+    return RFI_OK;
+}
+
+int rfi_set_thresholds(rfi_ctx *ctx, const rfi_thresholds *thr) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if ((rc = check_thresholds(thr))) return rc;
+    ctx->thr = *thr;
+    return RFI_OK;
+}
+
+int rfi_process_block(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags, float *avg,
+                      float *weight, float *stats, void *stream) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if ((rc = check_block_args(ctx, vis, T, flags, avg, weight, stats, true))) return rc;
+    const StreamArgs a = make_args(ctx, vis, T, flags, avg, weight, stats, 0, ctx->R);
+    if ((rc = launch_block(ctx, a, static_cast<cudaStream_t>(stream)))) return rc;
+    ctx->n_seen += T;
+    return RFI_OK;
+}
+
+int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags, float *avg,
+                           float *weight, float *stats, void *stream) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if ((rc = check_block_args(ctx, vis, T, flags, avg, weight, stats, false))) return rc;
+    if (T > ctx->host_max_T)
+        return fail(RFI_EINVAL, "T=%d exceeds the host staging (host_max_T=%d)", T, ctx->host_max_T);
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    const long long R = ctx->R;
+    const int nch = (int)std::min<long long>(ctx->host_chunks, R);
+    const int nwin = T / ctx->M, wpr = (T + 31) / 32;
+    const long long n_out = (ctx->n_seen + T) / ctx->K - ctx->n_seen / ctx->K;
+    const size_t sb = sample_bytes(ctx->dtype);
+    cudaError_t e;
+    if ((e = cudaEventRecord(ctx->ev_start, user)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->s_in, ctx->ev_start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->s_run, ctx->ev_start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_start, 0)) != cudaSuccess)
+        return set_cuda_error(ctx, e, "host path setup");
+    for (int k = 0; k < nch; ++k) {
+        const long long r0 = R * k / nch, r1 = R * (k + 1) / nch, nr = r1 - r0;
+        if (nr <= 0) continue;
+        e = cudaMemcpyAsync(ctx->h_vis + r0 * T * sb, static_cast<const char *>(vis) + r0 * T * sb,
+                            nr * T * sb, cudaMemcpyHostToDevice, ctx->s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in[k], ctx->s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_run, ctx->ev_in[k], 0);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "host path copy-in");
+        StreamArgs a = make_args(ctx, ctx->h_vis, T, ctx->h_flags, ctx->h_avg, ctx->h_weight,
+                                 ctx->h_stats, r0, nr);
+        if ((rc = launch_block(ctx, a, ctx->s_run))) return rc;
+        e = cudaEventRecord(ctx->ev_run[k], ctx->s_run);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_run[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(flags + r0 * wpr, ctx->h_flags + r0 * wpr, nr * wpr * 4,
+                                cudaMemcpyDeviceToHost, ctx->s_out);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(stats + r0 * nwin, (size_t)R * nwin * 4,
+                                  ctx->h_stats + r0 * nwin, (size_t)R * nwin * 4, nr * nwin * 4, 3,
+                                  cudaMemcpyDeviceToHost, ctx->s_out);
+        if (e == cudaSuccess && n_out > 0)
+            e = cudaMemcpyAsync(avg + r0 * n_out * 8, ctx->h_avg + r0 * n_out * 8,
+                                nr * n_out * 32, cudaMemcpyDeviceToHost, ctx->s_out);
+        if (e == cudaSuccess && n_out > 0)
+            e = cudaMemcpyAsync(weight + r0 * n_out, ctx->h_weight + r0 * n_out, nr * n_out * 4,
+                                cudaMemcpyDeviceToHost, ctx->s_out);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "host path copy-out");
+    }
+    if ((e = cudaEventRecord(ctx->ev_done, ctx->s_out)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(user, ctx->ev_done, 0)) != cudaSuccess ||
+        (e = cudaEventSynchronize(ctx->ev_done)) != cudaSuccess)
+        return set_cuda_error(ctx, e, "host path completion");
+    ctx->n_seen += T;
+    return RFI_OK;
+}
+
+int rfi_process_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *T,
+                      uint32_t *const *flags, float *const *avg, float *const *weight,
+                      float *const *stats, void *stream) {
+    static thread_local BatchArgs tb;
+    BatchArgs *b = &tb;
+    int rc = build_batch(ctxs, n, vis, T, flags, avg, weight, stats, true, b);
+    if (rc) return rc;
+    rfi_ctx *c0 = ctxs[0];
+    const int grid = persistent_grid(c0->inst, c0->wpb, c0->device);
+    void *args[] = {b};
+    cudaError_t e = cudaLaunchKernel(c0->inst->batch_fn, dim3(grid), dim3(32 * c0->wpb), args, 0,
+                                     static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        for (int i = 0; i < n; ++i) ctxs[i]->status = RFI_ECUDA;
+        return fail(RFI_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < n; ++i) ctxs[i]->n_seen += T[i];
+    return RFI_OK;
+}
+
+int rfi_batch_graph_create(rfi_batch_graph **out, rfi_ctx *const *ctxs, int n, const int *T) {
+    if (!out) return fail(RFI_EINVAL, "null output handle");
+    *out = nullptr;
+    BatchArgs *b = new (std::nothrow) BatchArgs;
+    if (!b) return fail(RFI_ENOMEM, "host allocation failed");
+    int rc = build_batch(ctxs, n, nullptr, T, nullptr, nullptr, nullptr, nullptr, false, b);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    rfi_batch_graph *g = new (std::nothrow) rfi_batch_graph();
+    if (!g) {
+        delete b;
+        return fail(RFI_ENOMEM, "host allocation failed");
+    }
+    g->n = n;
+    g->ctxs.assign(ctxs, ctxs + n);
+    g->T.assign(T, T + n);
+    g->inst = ctxs[0]->inst;
+    g->block = 32 * ctxs[0]->wpb;
+    g->grid = persistent_grid(g->inst, ctxs[0]->wpb, ctxs[0]->device);
+    cudaKernelNodeParams kp = {};
+    void *args[] = {b};
+    kp.func = const_cast<void *>(g->inst->batch_fn);
+    kp.gridDim = dim3(g->grid);
+    kp.blockDim = dim3(g->block);
+    kp.kernelParams = args;
+    cudaError_t e = cudaGraphCreate(&g->graph, 0);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&g->node, g->graph, nullptr, 0, &kp);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    delete b;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return fail(RFI_ECUDA, "graph build: %s", cudaGetErrorString(e));
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        g_live.insert(g);
+    }
+    *out = g;
+    return RFI_OK;
+}
+
+int rfi_batch_graph_launch(rfi_batch_graph *g, const void *const *vis, uint32_t *const *flags,
+                           float *const *avg, float *const *weight, float *const *stats,
+                           void *stream) {
+    if (!g || !is_live(g)) return fail(RFI_ESTATE, "not a live batch graph");
+    static thread_local BatchArgs tb;
+    BatchArgs *b = &tb;
+    int rc = build_batch(g->ctxs.data(), g->n, vis, g->T.data(), flags, avg, weight, stats, true, b);
+    if (rc) return rc;
+    cudaKernelNodeParams kp = {};
+    void *args[] = {b};
+    kp.func = const_cast<void *>(g->inst->batch_fn);
+    kp.gridDim = dim3(g->grid);
+    kp.blockDim = dim3(g->block);
+    kp.kernelParams = args;
+    cudaError_t e = cudaGraphExecKernelNodeSetParams(g->exec, g->node, &kp);
+    if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        for (rfi_ctx *c : g->ctxs) c->status = RFI_ECUDA;
+        return fail(RFI_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < g->n; ++i) g->ctxs[i]->n_seen += g->T[i];
+    return RFI_OK;
+}
+
+int rfi_batch_graph_destroy(rfi_batch_graph *g) {
+    if (!g) return RFI_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        if (!g_live.erase(g)) return fail(RFI_ESTATE, "not a live batch graph");
+    }
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return RFI_OK;
+}
+
+int rfi_reset(rfi_ctx *ctx) {
+    if (!ctx || !is_live(ctx) || ctx->magic != CTX_MAGIC)
+        return fail(RFI_ESTATE, "not a live context");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemset(ctx->carry, 0, sizeof(float) * 9 * (size_t)ctx->P * ctx->R);
+    if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        ctx->status = RFI_ECUDA;
+        return fail(RFI_ECUDA, "reset: %s", cudaGetErrorString(e));
+    }
+    ctx->n_seen = 0;
+    ctx->status = RFI_OK;
+    return RFI_OK;
+}
+
+int rfi_destroy(rfi_ctx *ctx) {
+    if (!ctx) return RFI_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        if (!g_live.erase(ctx)) return fail(RFI_ESTATE, "not a live context (double destroy?)");
+    }
+    free_ctx(ctx);
+    return RFI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// rfi_device.cuh -- sm_103a device code of the online RFI flagging path
+// (arXiv 2412.14775, Sections 2, 2.1, 2.2; Tables 1 and 2).
+//
+// Work decomposition.  A warp owns RW = 32/P rows ("row group") and walks their
+// windows in time order.  The P lanes of one row split every window of M samples:
+// a window is a run of M*SB contiguous bytes, cut into 16- or 32-byte load units,
+// and lane j of the row loads units j, j+P, j+2P, ... so one warp instruction reads
+// P*UB contiguous bytes from each of RW rows (whole sectors, nothing wasted).
+// Each lane keeps its own partial sums of the window; an xor-butterfly over the P
+// lanes completes S1, S2 and the two resultant vectors, after which every lane of
+// the row holds bit-identical totals (float addition is commutative), evaluates
+// tau and r, and the window flag follows.  Per-row outputs (stats, flag words,
+// averages) are written by lane 0 of the row.
+//
+// Averaging.  Each lane also sums its samples of the window (8 floats); when the
+// window is not flagged that partial joins the lane's running bin sum.  When a bin
+// of K samples closes, the P running sums are reduced and the mean of the unflagged
+// samples and the weight (unflagged / K) are written.  An open bin at the end of a
+// block is kept per lane in the context's carry, so splitting a stream into blocks
+// at multiples of M gives bit-identical results.
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace rfi {
+
+enum { DT_F32 = 0, DT_F16 = 1 };
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int MAX_BATCH = 64;
+
+// One stream's work in one launch (passed by value in kernel parameter space).
+struct StreamArgs {
+    const void *vis;        // [R][T][4][2] of row 0 of this launch
+    uint32_t *flags;        // [R][Wpr]
+    float *avg;             // [R][n_out][8]
+    float *weight;          // [R][n_out]
+    float *stats;           // plane k at stats + k*stats_plane: [R][nwin]
+    float *carry;           // [R][P][9]: per-lane open-bin sums (8) and count
+    long long R;            // rows in this launch
+    long long stats_plane;  // floats between the tau, r_Re and r_Im planes
+    int T, M, K, Wpr, nwin, n_out;
+    int bin_pos0;           // samples of the open bin consumed before this block
+    float c0;               // (M d + 1)/(M - 1), Table 1 group 5
+    float s_low, s_high, gamma, eps, fM, fK;
+};
+
+struct BatchArgs {
+    int n;
+    long long total;                    // total row-group tasks
+    long long prefix[MAX_BATCH + 1];    // first task of each stream
+    unsigned long long *counter;        // [0] task counter, [1] low word: blocks done
+    StreamArgs s[MAX_BATCH];
+};
+
+// ---- hardware approximations (PTX ISA: sqrt.approx / rcp.approx) --------------
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---- streaming loads of one 16- or 32-byte unit (read once: no L1 allocation) ---
+template <int UB> struct Unit;
+template <> struct Unit<32> { uint32_t r[8]; };
+template <> struct Unit<16> { uint32_t r[4]; };
+
+__device__ __forceinline__ void load_unit(const char *p, Unit<32> &u) {
+    asm("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3]),
+          "=r"(u.r[4]), "=r"(u.r[5]), "=r"(u.r[6]), "=r"(u.r[7])
+        : "l"(p));
+}
+__device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
+    asm("ld.global.nc.L1::no_allocate.v4.b32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3])
+        : "l"(p));
+}
+
+// Sample k of a unit as 8 floats: re/im of xx, xy, yx, yy.  Widening a binary16
+// value to float32 is exact.
+template <int DT, int UB>
+__device__ __forceinline__ void decode(const Unit<UB> &u, int k, float x[8]) {
+    if constexpr (DT == DT_F32) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = __uint_as_float(u.r[c]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            __half2 h = *reinterpret_cast<const __half2 *>(&u.r[4 * k + c]);
+            float2 f = __half22float2(h);
+            x[2 * c] = f.x;
+            x[2 * c + 1] = f.y;
+        }
+    }
+}
+
+// ---- per-lane window accumulators ------------------------------------------
+struct WinAcc {
+    float s1, s2;                 // Table 1 groups 3, 4
+    float c1, c2;                 // Kahan compensation of s1, s2 (when enabled)
+    float qr, ur, vr, qi, ui, vi; // Table 2 group 4, Re and Im parts
+    float a[8];                   // sum of the raw correlations (averaging)
+};
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// One sample: Eq. IQUV, then Table 1 groups 1-4 and Table 2 groups 1-4 for the Re
+// and Im parts of (Q, U, V).
+template <bool KAHAN>
+__device__ __forceinline__ void accumulate(WinAcc &A, const float x[8], float eps) {
+    const float Ir = x[0] + x[6], Ii = x[1] + x[7];   // I = xx + yy
+    const float Qr = x[0] - x[6], Qi = x[1] - x[7];   // Q = xx - yy
+    const float Ur = x[2] + x[4], Ui = x[3] + x[5];   // U = xy + yx
+    const float Vr = x[5] - x[3], Vi = x[2] - x[4];   // V = j (xy - yx)
+    const float y = Ir * Ir + Ii * Ii;                // |I|^2
+    const float z = sqrt_approx(y);                   // |I|
+    if constexpr (KAHAN) {
+        kahan_add(A.s1, A.c1, z);
+        kahan_add(A.s2, A.c2, y);
+    } else {
+        A.s1 += z;
+        A.s2 += y;
+    }
+    const float pr = sqrt_approx(Qr * Qr + Ur * Ur + Vr * Vr) + eps;
+    const float ir = rcp_approx(pr);
+    A.qr += Qr * ir; A.ur += Ur * ir; A.vr += Vr * ir;
+    const float pi = sqrt_approx(Qi * Qi + Ui * Ui + Vi * Vi) + eps;
+    const float ii = rcp_approx(pi);
+    A.qi += Qi * ii; A.ui += Ui * ii; A.vi += Vi * ii;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) A.a[c] += x[c];
+}
+
+template <int P>
+__device__ __forceinline__ float allsum(float v) {
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// ---- one row group of one stream ---------------------------------------------
+// DT: input dtype; SPU: samples per load unit (1 or 2); P: lanes per row;
+// CH: load units issued together per lane; KAHAN: compensated S1, S2.
+template <int DT, int SPU, int P, int CH, bool KAHAN>
+__device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
+    constexpr int RW = 32 / P;
+    constexpr int SB = (DT == DT_F32) ? 32 : 16;   // bytes per sample
+    constexpr int UB = SB * SPU;                   // bytes per load unit
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (P - 1);
+    const long long row = group * RW + lane / P;
+    const bool active = row < a.R;
+    const long long rowc = active ? row : a.R - 1;  // inactive lanes re-read a valid row
+    const int S = a.M / (P * SPU);                  // load units per lane per window
+    const char *rp = static_cast<const char *>(a.vis) + rowc * (long long)a.T * SB;
+    const bool lead = active && j == 0;
+
+    float acc[8];
+    float cnt = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = 0.f;
+    if (a.bin_pos0 != 0) {
+        const float *cp = a.carry + (rowc * P + j) * 9;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = cp[c];
+        cnt = cp[8];
+    }
+    int pos = a.bin_pos0;
+    int bin = 0;
+    uint32_t fword = 0;
+
+    for (int w = 0; w < a.nwin; ++w) {
+        WinAcc A;
+        A.s1 = A.s2 = A.c1 = A.c2 = 0.f;
+        A.qr = A.ur = A.vr = A.qi = A.ui = A.vi = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) A.a[c] = 0.f;
+        const char *wp = rp + (long long)w * a.M * SB + j * UB;
+        for (int s0 = 0; s0 < S; s0 += CH) {
+            Unit<UB> u[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) load_unit(wp + (s0 + c) * (P * UB), u[c]);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+#pragma unroll
+                for (int k = 0; k < SPU; ++k) {
+                    float x[8];
+                    decode<DT, UB>(u[c], k, x);
+                    accumulate<KAHAN>(A, x, a.eps);
+                }
+            }
+        }
+        if constexpr (KAHAN) {
+            A.s1 -= A.c1;
+            A.s2 -= A.c2;
+        }
+        // complete the window over the P lanes of the row
+        const float S1 = allsum<P>(A.s1), S2 = allsum<P>(A.s2);
+        const float qr = allsum<P>(A.qr), ur = allsum<P>(A.ur), vr = allsum<P>(A.vr);
+        const float qi = allsum<P>(A.qi), ui = allsum<P>(A.ui), vi = allsum<P>(A.vi);
+        // Table 1 groups 6-7 and Sec. 2.1: tau = c0 * (M S2 / (S1^2 + eps) - 1)
+        const float s12 = S1 * S1;
+        const float tau = a.c0 * (a.fM * S2 / (s12 + a.eps) - 1.0f);
+        // Table 2 groups 5-6: r = sqrt(q^2 + u^2 + v^2) / M, per part
+        const float r_re = sqrtf(qr * qr + ur * ur + vr * vr) / a.fM;
+        const float r_im = sqrtf(qi * qi + ui * ui + vi * vi) / a.fM;
+        // SK flag OR (DS Re OR DS Im); a NaN statistic fails its "inside" test
+        const bool f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
+                       !(r_im <= a.gamma);
+        if (lead) {
+            float *sp = a.stats + row * a.nwin + w;
+            sp[0] = tau;
+            sp[a.stats_plane] = r_re;
+            sp[2 * a.stats_plane] = r_im;
+        }
+        // the flag covers every sample of the window: set bits [w*M, w*M + M)
+        {
+            int lo = w * a.M;
+            const int hi = lo + a.M;
+            while (lo < hi) {
+                const int b0 = lo & 31;
+                const int nb = min(hi - lo, 32 - b0);
+                if (f) fword |= (nb == 32 ? FULL : ((1u << nb) - 1u)) << b0;
+                lo += nb;
+                if ((lo & 31) == 0) {
+                    if (lead) a.flags[row * a.Wpr + ((lo - 1) >> 5)] = fword;
+                    fword = 0;
+                }
+            }
+        }
+        // flagged samples are excluded from the average (end of Sec. 2.1)
+        if (!f) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] += A.a[c];
+            cnt += (float)(S * SPU);
+        }
+        pos += a.M;
+        if (pos == a.K) {
+            float tot[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
+            const float n = allsum<P>(cnt);
+            if (lead) {
+                float4 *ap = reinterpret_cast<float4 *>(a.avg + (row * a.n_out + bin) * 8);
+                float o[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) o[c] = n > 0.f ? tot[c] / n : 0.f;
+                ap[0] = make_float4(o[0], o[1], o[2], o[3]);
+                ap[1] = make_float4(o[4], o[5], o[6], o[7]);
+                a.weight[row * a.n_out + bin] = n / a.fK;
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = 0.f;
+            cnt = 0.f;
+            pos = 0;
+            ++bin;
+        }
+    }
+    if (a.T & 31) {
+        if (lead) a.flags[row * a.Wpr + (a.T >> 5)] = fword;
+    }
+    if (pos != 0 && active) {
+        float *cp = a.carry + (row * P + j) * 9;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) cp[c] = acc[c];
+        cp[8] = cnt;
+    }
+}
+
+// ---- kernels ---------------------------------------------------------------------
+template <int DT, int SPU, int P, int CH, bool KAHAN>
+__global__ void __launch_bounds__(512, 1) k_block(const __grid_constant__ StreamArgs a) {
+    const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (group * (32 / P) >= a.R) return;     // whole warp leaves together
+    process_group<DT, SPU, P, CH, KAHAN>(a, group);
+}
+
+// Persistent batch: every warp takes (stream, row group) tasks from a device counter
+// until none is left; the last block to finish resets the counter for the next
+// launch in stream order.
+template <int DT, int SPU, int P, int CH, bool KAHAN>
+__global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchArgs b) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(b.counter, 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        if ((long long)t >= b.total) break;
+        // stream i = number of streams whose next-stream prefix is <= t
+        int i = 0;
+        for (int base = 0; base < b.n; base += 32) {
+            const int k = base + lane;
+            const bool le = k < b.n && b.prefix[k + 1] <= (long long)t;
+            i += __popc(__ballot_sync(FULL, le));
+        }
+        process_group<DT, SPU, P, CH, KAHAN>(b.s[i], (long long)t - b.prefix[i]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int *done = reinterpret_cast<unsigned int *>(b.counter + 1);
+        const unsigned int prev = atomicAdd(done, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(b.counter, 0ull);
+            atomicExch(done, 0u);
+        }
+    }
+}
+
+}  // namespace rfi

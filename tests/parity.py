@@ -1,0 +1,123 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path and the FP64 oracle on the
+same seeded input and compare them element by element.
+
+Tolerances (FP32 path, written here once and used by every parity test):
+  * statistics: |gpu - oracle| <= 1e-5 * max(|oracle|, floor), floor = 1 for tau (its
+    null mean) and M^-1/2 for r_Re, r_Im (their null RMS);
+  * flags: identical, except windows where some statistic of the oracle lies within
+    1e-4 * max(|threshold|, floor) of its threshold (those may fall either way);
+  * averages: |gpu - oracle| <= 1e-5 * max(|oracle|, 1) per component and weights
+    exactly equal, in every bin none of whose windows is exempt from flag equality.
+The GPU flag words must also equal, bit for bit, the flag rule applied in float32 to
+the GPU's own statistics (self-consistency of the packing).
+"""
+import numpy as np
+import torch
+
+STAT_RTOL = 1e-5
+BAND = 1e-4
+AVG_RTOL = 1e-5
+
+
+def to_device_rows(vis_np, dtype):
+    """[..., T, 4, 2] numpy float32 -> contiguous CUDA tensor [R, T, 4, 2] of `dtype`."""
+    v = vis_np.reshape(-1, *vis_np.shape[-3:])
+    t = torch.from_numpy(np.ascontiguousarray(v))
+    if dtype == "f16":
+        t = t.to(torch.float16)
+    return t.cuda()
+
+
+def run_gpu(stream, vis_dev, out=None):
+    o = stream.process(vis_dev, out=out)
+    torch.cuda.synchronize()
+    return gpu_to_numpy(o)
+
+
+def gpu_to_numpy(o):
+    st = o["stats"].cpu().numpy()
+    return dict(tau=st[0].astype(np.float64), r_re=st[1].astype(np.float64),
+                r_im=st[2].astype(np.float64),
+                flagbits=o["flags"].cpu().numpy().view(np.uint32),
+                avg=o["avg"].cpu().numpy().reshape(o["avg"].shape[0], -1, 8).astype(np.float64),
+                weight=o["weight"].cpu().numpy().astype(np.float64))
+
+
+def expand_window_flags(flagbits, M, T):
+    """Window flags from packed per-sample bits (requires all M bits equal)."""
+    R = flagbits.shape[0]
+    t = np.arange(T)
+    bits = (flagbits[:, t // 32] >> (t % 32).astype(np.uint32)) & 1
+    w = bits.reshape(R, T // M, M)
+    assert np.all(w == w[:, :, :1]), "flag bits differ inside one window"
+    # bits past T in the last word must be zero
+    if T % 32:
+        tail = flagbits[:, -1] >> np.uint32(T % 32)
+        assert np.all(tail == 0), "flag bits set past the end of the block"
+    return w[:, :, 0].astype(bool)
+
+
+def flag_rule_f32(tau, r_re, r_im, thr):
+    f = np.float32
+    tau, r_re, r_im = tau.astype(f), r_re.astype(f), r_im.astype(f)
+    inside = (tau >= f(thr["s_low"])) & (tau <= f(thr["s_high"]))
+    return ~inside | ~(r_re <= f(thr["gamma"])) | ~(r_im <= f(thr["gamma"]))
+
+
+def near_threshold(orc, thr, M):
+    """Windows whose oracle statistics lie within BAND of a threshold."""
+    def near(x, t, floor):
+        if not np.isfinite(t):
+            return np.zeros_like(x, bool)
+        return np.abs(x - t) <= BAND * max(abs(t), floor)
+    return (near(orc["tau"], thr["s_low"], 1.0) | near(orc["tau"], thr["s_high"], 1.0) |
+            near(orc["r_re"], thr["gamma"], M ** -0.5) | near(orc["r_im"], thr["gamma"], M ** -0.5))
+
+
+def rel_err(x, ref, floor):
+    return np.abs(x - ref) / np.maximum(np.abs(ref), floor)
+
+
+def compare(gpu, orc, thr, M, K, n_seen=0, stat_rtol=STAT_RTOL, avg_rtol=AVG_RTOL,
+            check_flags=True):
+    """Assert parity; return a dict of the observed worst errors and counts."""
+    T = gpu["tau"].shape[1] * M
+    rep = {}
+    for key, floor in (("tau", 1.0), ("r_re", M ** -0.5), ("r_im", M ** -0.5)):
+        both_nan = np.isnan(gpu[key]) & np.isnan(orc[key])
+        e = np.where(both_nan, 0.0, rel_err(gpu[key], orc[key], floor))
+        rep[key] = float(np.nanmax(e)) if e.size else 0.0
+        if stat_rtol is not None:
+            assert not np.isnan(e).any(), f"{key}: NaN on one side only"
+            assert rep[key] <= stat_rtol, f"{key}: worst relative error {rep[key]:.3g}"
+    wflag = expand_window_flags(gpu["flagbits"], M, T)
+    self_rule = flag_rule_f32(gpu["tau"], gpu["r_re"], gpu["r_im"], thr)
+    assert np.array_equal(wflag, self_rule), "packed flags disagree with the GPU's own statistics"
+    exempt = near_threshold(orc, thr, M)
+    diff = wflag != orc["wflag"].astype(bool)
+    rep["flag_disagree"] = int(diff.sum())
+    rep["flag_disagree_frac"] = float(diff.mean()) if diff.size else 0.0
+    rep["exempt"] = int(exempt.sum())
+    if check_flags:
+        bad = diff & ~exempt
+        assert not bad.any(), f"{int(bad.sum())} window flags differ outside the threshold band"
+    # averages: bins whose windows are all clear of the threshold band
+    n_out = gpu["weight"].shape[1]
+    rep["avg"] = 0.0
+    if n_out:
+        wpb = K // M
+        first_open = (n_seen % K) // M       # windows of the first bin seen in earlier blocks
+        R = exempt.shape[0]
+        ok = np.ones((R, n_out), bool)
+        for b in range(n_out):
+            lo = max(0, b * wpb - first_open)
+            hi = min(exempt.shape[1], (b + 1) * wpb - first_open)
+            ok[:, b] = ~(exempt[:, lo:hi].any(axis=1) | diff[:, lo:hi].any(axis=1))
+        ea = rel_err(gpu["avg"], orc["avg"], 1.0).max(axis=2)
+        rep["avg"] = float(ea[ok].max()) if ok.any() else 0.0
+        if avg_rtol is not None:
+            assert rep["avg"] <= avg_rtol, f"avg: worst relative error {rep['avg']:.3g}"
+            # weight = n/K: float32 division on the GPU, double in the oracle
+            assert np.allclose(gpu["weight"][ok], orc["weight"][ok], rtol=1.2e-7, atol=0), \
+                "weights differ"
+    return rep

@@ -1,0 +1,321 @@
+"""Parity of the sm_103a path (through the C ABI) with the FP64 oracle.
+
+Every case runs the CUDA kernels and the oracle on the same seeded input and compares
+them element by element with the tolerances stated in tests/parity.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2412_14775_b300 import RfiStream, binding, default_thresholds
+from paper_2412_14775_b300.binding import RfiError
+from parity import compare, gpu_to_numpy, run_gpu, to_device_rows
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_input(vis_np, dtype):
+    """The exact values the GPU reads: float32 as is, or rounded to binary16."""
+    v = vis_np.reshape(-1, *vis_np.shape[-3:])
+    return v.astype(np.float16) if dtype == "f16" else v
+
+
+def _check_stream(stations, channels, M, K, Ts, dtype, thr=None, seed=3, **opts):
+    """Run blocks of lengths Ts through one context and one oracle stream; compare
+    every block."""
+    thr = thr or default_thresholds(M)
+    data = synth.tiny_block(seed=seed, stations=stations, channels=channels, T=sum(Ts),
+                            duty=0.08)["vis"]
+    R = data.shape[0] * data.shape[1]
+    st = RfiStream(stations, channels, M, K, thr, dtype, **opts)
+    orc = oracle.OracleStream(R, M, K, **thr)
+    t0 = 0
+    reps = []
+    for T in Ts:
+        blk = data[:, :, t0:t0 + T]
+        n_seen = orc.n_seen
+        g = run_gpu(st, to_device_rows(blk, dtype))
+        o = orc.process(_oracle_input(blk, dtype))
+        reps.append(compare(g, o, thr, M, K, n_seen=n_seen))
+        t0 += T
+    st.close()
+    return reps
+
+
+def test_tiny_fp32_reference():
+    """6 stations, 16 channels, T = 1024, M = 16, K = 64, one block."""
+    d = synth.tiny_block(seed=1)
+    M, K = 16, 64
+    thr = default_thresholds(M)
+    st = RfiStream(6, 16, M, K, thr, "f32")
+    g = run_gpu(st, to_device_rows(d["vis"], "f32"))
+    o = oracle.OracleStream(st.R, M, K, **thr).process(d["vis"].reshape(st.R, 1024, 4, 2))
+    rep = compare(g, o, thr, M, K)
+    assert o["wflag"].mean() > 0.01          # the bursts do raise flags
+    print("tiny fp32", rep)
+
+
+def test_tiny_fp16_storage():
+    """Same block stored as binary16: FP32 arithmetic on exactly widened values."""
+    d = synth.tiny_block(seed=1)
+    M, K = 16, 64
+    thr = default_thresholds(M)
+    st = RfiStream(6, 16, M, K, thr, "f16")
+    g = run_gpu(st, to_device_rows(d["vis"], "f16"))
+    R = st.R
+    o16 = oracle.OracleStream(R, M, K, **thr).process(
+        d["vis"].reshape(R, 1024, 4, 2).astype(np.float16))
+    compare(g, o16, thr, M, K)
+    # against the oracle on the unrounded input: quantisation only, reported
+    o32 = oracle.OracleStream(R, M, K, **thr).process(d["vis"].reshape(R, 1024, 4, 2))
+    rep = compare(g, o32, thr, M, K, stat_rtol=None, avg_rtol=None, check_flags=False)
+    assert rep["flag_disagree_frac"] <= 1e-3, rep
+    print("tiny fp16 vs fp32 input", rep)
+
+
+SHAPES = [
+    # dtype, stations, channels, M, K, blocks, options
+    ("f32", 5, 3, 16, 64, [1024], {}),
+    ("f32", 3, 7, 16, 48, [48, 96, 16, 64], {"lanes_per_row": 4}),
+    ("f32", 4, 5, 2, 6, [6, 10, 2, 30], {}),
+    ("f32", 4, 5, 2, 4, [8, 4], {"lanes_per_row": 2}),
+    ("f32", 3, 4, 3, 9, [9, 27, 6], {}),
+    ("f32", 6, 3, 20, 40, [40, 60, 100], {"lanes_per_row": 4}),
+    ("f32", 6, 3, 20, 20, [40, 20], {"lanes_per_row": 1}),
+    ("f32", 5, 4, 64, 128, [128, 64, 192], {}),
+    ("f32", 5, 4, 64, 64, [128], {"lanes_per_row": 8, "compensated": -1}),
+    ("f32", 4, 6, 32, 32, [64, 96], {"lanes_per_row": 32}),
+    ("f32", 4, 6, 16, 32, [64, 32], {"lanes_per_row": 16}),
+    ("f32", 4, 6, 16, 16, [64], {"lanes_per_row": 8, "warps_per_block": 3}),
+    ("f32", 4, 6, 8, 8, [40, 24], {"lanes_per_row": 1, "warps_per_block": 1}),
+    ("f32", 10, 8, 16, 256, [256], {}),
+    ("f16", 5, 3, 16, 64, [256, 128], {}),
+    ("f16", 4, 5, 5, 10, [10, 20, 5], {}),
+    ("f16", 4, 5, 3, 6, [6, 12, 3], {}),
+    ("f16", 4, 5, 8, 16, [32, 48], {"lanes_per_row": 4}),
+    ("f16", 4, 5, 64, 64, [128], {"lanes_per_row": 8}),
+    ("f16", 6, 3, 20, 60, [60, 40, 20], {"lanes_per_row": 2}),
+    ("f16", 4, 6, 32, 64, [96, 32], {"lanes_per_row": 16}),
+    ("f16", 7, 5, 16, 32, [48], {"lanes_per_row": 1, "compensated": 1}),
+]
+
+
+@pytest.mark.parametrize("dtype,N,C,M,K,Ts,opts", SHAPES,
+                         ids=[f"{s[0]}-N{s[1]}-C{s[2]}-M{s[3]}-K{s[4]}-{len(s[5])}blk-"
+                              f"{'-'.join(f'{k[:3]}{v}' for k, v in s[6].items())}"
+                              for s in SHAPES])
+def test_shapes(dtype, N, C, M, K, Ts, opts):
+    _check_stream(N, C, M, K, Ts, dtype, **opts)
+
+
+@pytest.mark.parametrize("dtype,M", [("f32", 16), ("f16", 8), ("f16", 16), ("f16", 32),
+                                     ("f16", 64)])
+def test_lofar_scale_sampled_rows(dtype, M):
+    """62 stations (1953 baselines), 64 channels, T = 256, K = 256 in the launch shape
+    the bench times; the oracle checks a seeded sample of 2048 rows one by one."""
+    K = 256
+    thr = default_thresholds(M)
+    d = synth.lofar_block(seed=2)
+    st = RfiStream(62, 64, M, K, thr, dtype)
+    vis = to_device_rows(d["vis"], dtype)
+    g = run_gpu(st, vis)
+    del vis
+    rows = np.sort(np.random.default_rng(17).choice(st.R, size=2048, replace=False))
+    v = d["vis"].reshape(st.R, 256, 4, 2)[rows]
+    o = oracle.OracleStream(len(rows), M, K, **thr).process(_oracle_input(v, dtype))
+    gs = {k: val[rows] for k, val in g.items()}
+    rep = compare(gs, o, thr, M, K)
+    print(f"lofar {dtype} M={M}", rep)
+    st.close()
+
+
+def test_block_split_bit_identical():
+    """One block versus the same samples split at multiples of M: identical bits."""
+    M, K = 16, 64
+    thr = default_thresholds(M)
+    data = synth.tiny_block(seed=4, stations=5, channels=6, T=448)["vis"]
+    whole_s = RfiStream(5, 6, M, K, thr, "f32")
+    whole = gpu_to_numpy(whole_s.process(to_device_rows(data, "f32")))
+    for cuts in ((16, 224), (48, 64, 400), (208,)):
+        st = RfiStream(5, 6, M, K, thr, "f32")
+        parts = []
+        edges = (0,) + cuts + (448,)
+        for a, b in zip(edges[:-1], edges[1:]):
+            parts.append(gpu_to_numpy(st.process(to_device_rows(data[:, :, a:b], "f32"))))
+        for key in ("tau", "r_re", "r_im"):
+            assert np.array_equal(np.concatenate([p[key] for p in parts], 1), whole[key]), key
+        assert np.array_equal(np.concatenate([p["avg"] for p in parts], 1), whole["avg"])
+        assert np.array_equal(np.concatenate([p["weight"] for p in parts], 1), whole["weight"])
+        st.close()
+
+
+def _batch_setup(dtype, geoms, M, K, T, seed=9):
+    thr = default_thresholds(M)
+    streams, vis, datas = [], [], []
+    for i, (N, C) in enumerate(geoms):
+        d = synth.tiny_block(seed=seed + i, stations=N, channels=C, T=T, duty=0.06)["vis"]
+        datas.append(d)
+        streams.append(RfiStream(N, C, M, K, thr, dtype))
+        vis.append(to_device_rows(d, dtype))
+    return thr, streams, vis, datas
+
+
+def _alloc(streams, T):
+    return [s.alloc_outputs(T) for s in streams]
+
+
+def test_batch_matches_solo_bit_identical():
+    """Uneven streams in one persistent launch give the same bits as alone."""
+    M, K, T = 16, 64, 128
+    geoms = [(5, 3), (9, 7), (3, 2), (12, 5)]
+    for dtype in ("f32", "f16"):
+        thr, bs, vis, _ = _batch_setup(dtype, geoms, M, K, T)
+        _, ss, _, _ = _batch_setup(dtype, geoms, M, K, T)
+        for step in range(2):
+            outs = _alloc(bs, T)
+            binding.rfi_process_batch([s.ctx for s in bs], vis, [T] * len(bs),
+                                      [o["flags"] for o in outs], [o["avg"] for o in outs],
+                                      [o["weight"] for o in outs], [o["stats"] for o in outs])
+            torch.cuda.synchronize()
+            for s, v, o in zip(ss, vis, outs):
+                solo = s.process(v)
+                torch.cuda.synchronize()
+                for k in ("flags", "avg", "weight", "stats"):
+                    assert torch.equal(solo[k], o[k]), (dtype, step, k)
+
+
+def test_batch_graph_replay_matches_solo():
+    """The batch captured in a CUDA graph and replayed for three blocks."""
+    M, K, T = 16, 32, 48
+    geoms = [(4, 3), (7, 2), (2, 9)]
+    thr, bs, vis, _ = _batch_setup("f16", geoms, M, K, T)
+    _, ss, _, _ = _batch_setup("f16", geoms, M, K, T)
+    g = binding.rfi_batch_graph_create([s.ctx for s in bs], [T] * len(bs))
+    try:
+        for step in range(3):
+            outs = _alloc(bs, T)
+            binding.rfi_batch_graph_launch(g, vis, [o["flags"] for o in outs],
+                                           [o["avg"] for o in outs], [o["weight"] for o in outs],
+                                           [o["stats"] for o in outs])
+            torch.cuda.synchronize()
+            for s, v, o in zip(ss, vis, outs):
+                solo = s.process(v)
+                torch.cuda.synchronize()
+                for k in ("flags", "avg", "weight", "stats"):
+                    assert torch.equal(solo[k], o[k]), (step, k)
+    finally:
+        binding.rfi_batch_graph_destroy(g)
+
+
+def test_host_path_matches_device_path():
+    M, K, T = 16, 64, 256
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=6, stations=8, channels=5, T=T)["vis"]
+    dev = RfiStream(8, 5, M, K, thr, "f32")
+    host = RfiStream(8, 5, M, K, thr, "f32", host_max_T=T, host_chunks=3)
+    want = dev.process(to_device_rows(d, "f32"))
+    torch.cuda.synchronize()
+    hv = torch.from_numpy(d.reshape(-1, T, 4, 2).copy()).pin_memory()
+    got = host.process_host(hv)
+    for k in ("flags", "avg", "weight", "stats"):
+        assert torch.equal(want[k].cpu(), got[k]), k
+    # pageable host memory works too (copies are staged by the runtime)
+    got2 = RfiStream(8, 5, M, K, thr, "f32", host_max_T=T).process_host(
+        torch.from_numpy(d.reshape(-1, T, 4, 2).copy()))
+    for k in ("flags", "avg", "weight", "stats"):
+        assert torch.equal(want[k].cpu(), got2[k]), k
+
+
+def test_edge_values():
+    """All-zero windows (tau = -(Md+1)/(M-1), finite) and non-finite samples (flagged,
+    excluded from the averages)."""
+    M, K, T = 16, 32, 64
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=8, stations=3, channels=4, T=T)["vis"].copy()
+    d[0, 0] = 0.0                                # one row all zero
+    d[1, 1, 5, 2, 0] = np.nan                    # NaN in window 0
+    d[2, 3, 40, 0, 1] = np.inf                   # +inf in window 2
+    d[3, 2, 17, 3, 0] = -np.inf                  # -inf in window 1
+    R = 6 * 4
+    for dtype in ("f32", "f16"):
+        st = RfiStream(3, 4, M, K, thr, dtype)
+        g = run_gpu(st, to_device_rows(d, dtype))
+        o = oracle.OracleStream(R, M, K, **thr).process(_oracle_input(d, dtype))
+        assert g["tau"][0, 0] == np.float32(-(M * thr["d"] + 1) / (M - 1))
+        compare(g, o, thr, M, K)
+        rows = d.reshape(R, T, 4, 2)
+        for r in range(R):
+            bad = ~np.isfinite(rows[r]).all(axis=(1, 2))
+            for w in np.flatnonzero(bad.reshape(-1, M).any(axis=1)):
+                assert (g["flagbits"][r, (w * M) // 32] >> np.uint32((w * M) % 32)) & 1
+        assert np.isfinite(g["avg"]).all() and np.isfinite(g["weight"]).all()
+
+
+def test_threshold_update():
+    M, K, T = 16, 64, 128
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=10, stations=4, channels=4, T=T)["vis"]
+    st = RfiStream(4, 4, M, K, thr, "f32")
+    v = to_device_rows(d, "f32")
+    a = run_gpu(st, v)
+    never = dict(thr, s_low=-1e30, s_high=1e30, gamma=2.0)
+    binding.rfi_set_thresholds(st.ctx, never)
+    b = run_gpu(st, v)
+    assert a["flagbits"].any() and not b["flagbits"].any()
+    assert np.all(b["weight"] == 1.0)
+
+
+def test_invalid_arguments():
+    M, K, T = 16, 64, 128
+    thr = default_thresholds(M)
+    st = RfiStream(4, 4, M, K, thr, "f32")
+    v = torch.zeros((st.R, T, 4, 2), device="cuda")
+    out = st.alloc_outputs(T)
+    ctx = st.ctx
+    args = lambda **kw: dict(dict(vis=v, T=T, flags=out["flags"], avg=out["avg"],
+                                  weight=out["weight"], stats=out["stats"]), **kw)
+
+    def call(**kw):
+        a = args(**kw)
+        binding.rfi_process_block(ctx, a["vis"], a["T"], a["flags"], a["avg"], a["weight"],
+                                  a["stats"])
+
+    def status(**kw):
+        with pytest.raises(RfiError) as ei:
+            call(**kw)
+        return ei.value.status
+
+    assert status(T=120) == 1                                   # not a multiple of M
+    assert status(T=0) == 1
+    vv = torch.zeros(st.R * T * 8 + 8, device="cuda")
+    assert status(vis=vv[4:].data_ptr()) == 1                   # 16-byte misaligned
+    assert status(vis=v.cpu()) == 1                             # host memory
+    small = torch.zeros((st.R - 1, T, 4, 2), device="cuda")
+    assert status(vis=small) == 1                               # too small
+    assert status(stats=out["stats"][:, :-1].contiguous()) == 1
+    assert status(flags=None) == 1
+    assert status(avg=None) == 1
+    call()                                                      # the valid call works
+    torch.cuda.synchronize()
+    with pytest.raises(RfiError):
+        binding.rfi_create(0, 4, M, K, thr, "f32")
+    with pytest.raises(RfiError):
+        binding.rfi_create(4, 4, 1, K, thr, "f32")               # M < 2
+    with pytest.raises(RfiError):
+        binding.rfi_create(4, 4, 16, 24, thr, "f32")             # K not a multiple of M
+    with pytest.raises(RfiError):
+        binding.rfi_create(4, 4, 16, 32, dict(thr, s_low=3.0, s_high=1.0), "f32")
+    with pytest.raises(RfiError):
+        binding.rfi_create_ex(4, 4, 16, 32, thr, "f32", lanes_per_row=3)
+    with pytest.raises(RfiError):
+        binding.rfi_create_ex(4, 4, 3, 3, thr, "f16", lanes_per_row=2)   # odd M, f16
+    st.close()
+    with pytest.raises(RfiError) as ei:
+        call()
+    assert ei.value.status == 5                                 # destroyed context
+    with pytest.raises(RfiError) as ei:
+        binding.rfi_destroy(ctx)
+    assert ei.value.status == 5                                 # double destroy
+    binding.rfi_destroy(None)                                   # no-op
