@@ -41,6 +41,35 @@ def _peaks():
         return 6400.0, "fallback"
 
 
+def kernel_source_hash():
+    """Hash of the CUDA sources; a profile's traffic figure is used only while the
+    sources it was taken from are unchanged."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2412_14775_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(dtype):
+    """DRAM bytes per launch from profiles/k_block_lofar_block_<dtype>.md, or None
+    when the kernel sources changed after that capture."""
+    path = os.path.join(ROOT, "profiles", f"k_block_lofar_block_{dtype}.md")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith(("|", " ", "#")):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256_16") != kernel_source_hash():
+            return None
+        return int(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def algo_bytes(R, T, M, K, n_out, sample_bytes):
     """Bytes the method must move per launch: input, flag words, stats, averages."""
     return R * (T * sample_bytes + 4 * math.ceil(T / 32) + 12 * (T // M) + 36 * n_out)
@@ -176,6 +205,32 @@ def cpu_baseline(seconds_target=10.0):
                       f"{dt:.1f} s single-threaded"}
 
 
+def serving_extras(seconds, options, torch):
+    """The serving loop: 32 mixed FP16 streams at 1-4x real time, then the 62-station,
+    64-channel stream offered at 50x real time."""
+    import synth
+    from paper_2412_14775_b300.serve import ServingLoop
+    res = {}
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(0.5 * free, 32 << 30))
+    cfgs = synth.serving_streams(seed=5, n=32)
+    loop = ServingLoop(cfgs, M=16, K=256, T=256, dtype="f16", options=options,
+                       hbm_budget_bytes=budget, max_batch=32, cuda_streams=3)
+    res["mix32"] = dict(loop.run(seconds, seed=11), hbm_budget_gb=budget / 1e9, streams=32)
+    loop.close()
+    torch.cuda.empty_cache()
+    one = [dict(stations=62, channels=64, rho=50.0)]
+    loop = ServingLoop(one, M=16, K=256, T=256, dtype="f16", options=options,
+                       hbm_budget_bytes=budget, max_batch=1, cuda_streams=2)
+    r = loop.run(max(2.0, seconds / 2), seed=12)
+    R = 1953 * 64
+    r["real_time_factor"] = r["samples_per_s"] / (R * 256 / BLOCK_SECONDS)
+    res["lofar_50x"] = r
+    loop.close()
+    torch.cuda.empty_cache()
+    return res
+
+
 def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler_index=None):
     """Warm up, then time `steps` launches with per-launch CUDA events on the
     launching stream (the device time of the flagging kernel)."""
@@ -214,7 +269,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--tile", default="", help="lanes_per_row,warps_per_block override")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="wall time of the serving-loop run (0 = skip)")
+    ap.add_argument("--tile", default="",
+                    help="lanes_per_row,warps_per_block[,prefetch_groups,prefetch_bytes]")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f16"],
+                    help="input storage of the timed block (f16: same block in binary16)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -225,7 +285,7 @@ def main():
     import torch.distributed as dist
 
     import synth
-    from paper_2412_14775_b300 import RfiStream, default_thresholds
+    from paper_2412_14775_b300 import RfiStream, autotune, default_thresholds
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -235,22 +295,30 @@ def main():
     peak, peak_kind = _peaks()
     M, K, T = 16, 256, 256
     thr = default_thresholds(M)
-    opts = {}
-    if args.tile:
-        p, w = args.tile.split(",")
-        opts = dict(lanes_per_row=int(p), warps_per_block=int(w))
-
     d = synth.lofar_block(seed=2 + rank)
     R = d["vis"].shape[0] * d["vis"].shape[1]
     host32 = torch.from_numpy(d["vis"].reshape(R, T, 4, 2))
     vis32 = host32.to(dev)
-    st = RfiStream(62, 64, M, K, thr, "f32", **opts)
+
+    def tuned(Mw, dtype, vis):
+        if args.tile:
+            f = [int(x) for x in args.tile.split(",")]
+            keys = ["lanes_per_row", "warps_per_block", "prefetch_groups", "prefetch_bytes"]
+            return dict(zip(keys, f))
+        best, _ = autotune.tune(62, 64, Mw, K, default_thresholds(Mw), dtype, vis)
+        return autotune.options_of(best)
+
+    main_dt = args.dtype
+    sbytes = 32 if main_dt == "f32" else 16
+    vis_main = vis32 if main_dt == "f32" else vis32.half()
+    opts = tuned(M, main_dt, vis_main)
+    st = RfiStream(62, 64, M, K, thr, main_dt, **opts)
     out = st.alloc_outputs(T, device=dev)
     cs = torch.cuda.current_stream(dev)
 
     if ws > 1:
         dist.barrier()
-    total, per, clocks = time_kernel(st, vis32, out, args.steps, args.warmup, torch, cs,
+    total, per, clocks = time_kernel(st, vis_main, out, args.steps, args.warmup, torch, cs,
                                      sampler_index=local)
     if ws > 1:
         t = torch.tensor([total], device=dev, dtype=torch.float64)
@@ -259,7 +327,7 @@ def main():
     samples = R * T
     value = ws * samples * args.steps / total
     n_out = 1
-    bytes_launch = algo_bytes(R, T, M, K, n_out, 32)
+    bytes_launch = algo_bytes(R, T, M, K, n_out, sbytes)
     kern = statistics.mean(per)
     achieved = bytes_launch / kern / 1e9
 
@@ -267,11 +335,11 @@ def main():
     if not args.no_extras and rank == 0:
         # FP16 storage (same geometry), window sweep
         fp16 = {}
-        host16 = host32.half()
-        vis16 = host16.to(dev)
-        del vis32
+        vis16 = vis_main if main_dt == "f16" else vis32.half()
+        del vis32, vis_main
         for Mw in (8, 16, 32, 64):
-            s16 = RfiStream(62, 64, Mw, 256, default_thresholds(Mw), "f16", **opts)
+            o16opts = tuned(Mw, "f16", vis16)
+            s16 = RfiStream(62, 64, Mw, 256, default_thresholds(Mw), "f16", **o16opts)
             o16 = s16.alloc_outputs(T, device=dev)
             tot16, per16, _ = time_kernel(s16, vis16, o16, max(200, args.steps // 4), args.warmup,
                                           torch, cs)
@@ -279,17 +347,19 @@ def main():
             k16 = statistics.mean(per16)
             fp16[f"M{Mw}"] = {"samples_per_s": samples * len(per16) / tot16,
                               "kernel_us": k16 * 1e6, "achieved_gbs": b16 / k16 / 1e9,
-                              "frac": b16 / k16 / 1e9 / peak,
-                              "lanes_per_row": s16.options["lanes_per_row"]}
+                              "frac": b16 / k16 / 1e9 / peak, "options": o16opts}
             s16.close()
         extras["fp16"] = fp16
         del vis16
         torch.cuda.empty_cache()
+        if args.serve_seconds > 0:
+            extras["serving"] = serving_extras(args.serve_seconds,
+                                               fp16["M16"]["options"], torch)
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
     if rank == 0 and not args.no_e2e:
-        hst = RfiStream(62, 64, M, K, thr, "f32", host_max_T=T, host_chunks=8, **opts)
+        hst = RfiStream(62, 64, M, K, thr, "f32", **dict(opts, host_max_T=T, host_chunks=8))
         hin = host32.pin_memory()
         hout = hst.alloc_outputs(T, device="cpu", pin_memory=True)
         for _ in range(3):
@@ -313,14 +383,16 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": main_dt,
             "data": "synthetic",
-            "config": dict(WORKLOAD, dtype="complex64", l2="inputs 1.02 GB > 126 MB L2, no flush",
-                           lanes_per_row=st.options["lanes_per_row"],
-                           warps_per_block=st.options["warps_per_block"]),
+            "config": dict(WORKLOAD, dtype="complex64" if main_dt == "f32" else "complex32 (binary16)",
+                           l2=f"inputs {R * T * sbytes / 1e9:.2f} GB > 126 MB L2, no flush",
+                           options={k: st.options[k] for k in
+                                    ("lanes_per_row", "warps_per_block", "prefetch_bytes",
+                                     "prefetch_groups")}),
             "hbm_gbs": achieved * ws,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": profiled_traffic(main_dt),
                          "peak_kind": peak_kind, "kernel_us": kern * 1e6,
                          "algorithmic_bytes_per_launch": bytes_launch},
             "frac_of_8tbs": achieved / 8000.0,

@@ -89,6 +89,10 @@ typedef enum {
  *                  compute and copy out overlap across chunks); 0 = 4.
  *   compensated    Kahan-compensated S1 and S2 (the SK moments): 1 = on, -1 = off,
  *                  0 = on for windows of M >= 64 samples.
+ *   prefetch_bytes   size of one L2 bulk prefetch per row, rounded down to whole
+ *                  windows (at least one); a multiple of 16; 0 = 1024.
+ *   prefetch_groups  how many such groups each row keeps requested ahead of the
+ *                  window being loaded; -1 = no prefetch, 0 = 2.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -98,6 +102,8 @@ typedef struct {
     int host_max_T;
     int host_chunks;
     int compensated;
+    int prefetch_bytes;
+    int prefetch_groups;
 } rfi_options;
 
 /* Create a context for one stream of `stations` stations (B = N(N+1)/2 baselines)

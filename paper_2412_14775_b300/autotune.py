@@ -1,0 +1,106 @@
+"""Autotuner for the flagging kernel's launch shape.
+
+For one workload (dtype, M, K, T, rows) it times candidate options of rfi_create_ex
+-- lanes per row P, warps per block, L2 prefetch group size and distance -- on the
+caller's device data with CUDA events, and returns the fastest.  Results are cached
+in memory and, when `cache_path` is given, in a JSON file keyed by the workload.
+
+Every candidate computes the same statistics and flags; only the reduction order of
+a window (which depends on P) changes, within FP32 rounding.
+"""
+import json
+import os
+import statistics
+
+from . import binding as B
+from .stream import RfiStream
+
+_MEM = {}
+
+
+def _key(stations, channels, M, K, T, dtype):
+    return f"{B._dtype(dtype)}:{stations}x{channels}:M{M}:K{K}:T{T}"
+
+
+def candidates_p(M, dtype):
+    spu = 2 if (B._dtype(dtype) == B.RFI_C32H and M % 2 == 0) else 1
+    ps = [p for p in (1, 2, 4, 8, 16) if M % (p * spu) == 0]
+    if B._dtype(dtype) == B.RFI_C32H and spu == 1:
+        ps = [1]
+    return ps
+
+
+def time_options(stations, channels, M, K, thr, dtype, vis, reps=30, warmup=5, **opts):
+    """Mean per-launch time (s) of one option set on `vis` (device tensor)."""
+    import torch
+    st = RfiStream(stations, channels, M, K, thr, dtype, **opts)
+    T = vis.shape[-3]
+    out = st.alloc_outputs(T, device=vis.device)
+    try:
+        for _ in range(warmup):
+            st.process(vis, out=out)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record()
+            st.process(vis, out=out)
+            b.record()
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ev) * 1e-3
+    finally:
+        st.close()
+
+
+def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, verbose=False):
+    """Return (best_options, table) for this workload; coordinate search over the
+    launch shape, then the prefetch distance and size."""
+    T = vis.shape[-3]
+    key = _key(stations, channels, M, K, T, dtype)
+    if key in _MEM:
+        return _MEM[key], []
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            disk = json.load(f)
+        if key in disk:
+            _MEM[key] = disk[key]
+            return disk[key], []
+    table = []
+
+    def run(o):
+        t = time_options(stations, channels, M, K, thr, dtype, vis, reps=reps, **o)
+        table.append((dict(o), t))
+        if verbose:
+            print(f"  {o} {t * 1e6:.1f} us")
+        return t
+
+    best, best_t = None, float("inf")
+    for P in candidates_p(M, dtype):
+        for wpb in (4, 8, 16):
+            o = dict(lanes_per_row=P, warps_per_block=wpb)
+            t = run(o)
+            if t < best_t:
+                best, best_t = o, t
+    for pg in (-1, 1, 2, 4, 8):
+        for pb in (512, 1024, 2048, 4096):
+            if pg == -1 and pb != 1024:
+                continue
+            o = dict(best, prefetch_groups=pg, prefetch_bytes=pb)
+            t = run(o)
+            if t < best_t:
+                best, best_t = o, t
+    best = dict(best, seconds=best_t)
+    _MEM[key] = best
+    if cache_path:
+        disk = {}
+        if os.path.exists(cache_path):
+            with open(cache_path) as f:
+                disk = json.load(f)
+        disk[key] = best
+        with open(cache_path, "w") as f:
+            json.dump(disk, f, indent=1, sort_keys=True)
+    return best, table
+
+
+def options_of(best):
+    """Strip the timing from a tuned entry: the keyword options for RfiStream."""
+    return {k: v for k, v in best.items() if k != "seconds"}

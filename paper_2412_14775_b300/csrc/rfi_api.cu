@@ -114,6 +114,7 @@ struct rfi_ctx {
     rfi_dtype dtype;
     rfi_thresholds thr;
     int P, spu, S, ch, kahan, wpb;
+    int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     const Instance *inst;
     long long n_seen;
     int status;
@@ -255,6 +256,9 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.eps = (float)c->thr.eps;
     a.fM = (float)c->M;
     a.fK = (float)c->K;
+    const int wbytes = c->M * sample_bytes(c->dtype);
+    a.pf_windows = std::max(1, c->pf_bytes / wbytes);
+    a.pf_groups = c->pf_groups;
     return a;
 }
 
@@ -413,10 +417,11 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     if (dtype != RFI_C64 && dtype != RFI_C32H) return fail(RFI_EINVAL, "unknown dtype");
     int rc;
     if ((rc = check_thresholds(thr))) return rc;
-    rfi_options o = {0, 0, 0, 0, 0};
+    rfi_options o = {0, 0, 0, 0, 0, 0, 0};
     if (opt) o = *opt;
     if (o.warps_per_block < 0 || o.warps_per_block > 16 || o.host_max_T < 0 || o.host_chunks < 0 ||
-        o.compensated < -1 || o.compensated > 1)
+        o.compensated < -1 || o.compensated > 1 || o.prefetch_bytes < 0 ||
+        o.prefetch_bytes % 16 != 0 || o.prefetch_groups > 64)
         return fail(RFI_EINVAL, "bad options");
 
     rfi_ctx *c = new (std::nothrow) rfi_ctx();
@@ -439,6 +444,8 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->thr = *thr;
     c->kahan = o.compensated == 1 || (o.compensated == 0 && window_M >= 64);
     c->wpb = o.warps_per_block ? o.warps_per_block : 8;
+    c->pf_bytes = o.prefetch_bytes ? o.prefetch_bytes : 1024;
+    c->pf_groups = o.prefetch_groups == 0 ? 2 : (o.prefetch_groups < 0 ? 0 : o.prefetch_groups);
     c->status = RFI_OK;
     if ((rc = choose_shape(c, o.lanes_per_row))) {
         delete c;
@@ -526,6 +533,8 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->host_max_T = ctx->host_max_T;
     opt->host_chunks = ctx->host_chunks;
     opt->compensated = ctx->kahan ? 1 : -1;
+    opt->prefetch_bytes = ctx->pf_bytes;
+    opt->prefetch_groups = ctx->pf_groups ? ctx->pf_groups : -1;
     return RFI_OK;
 }
 

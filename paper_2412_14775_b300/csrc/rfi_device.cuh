@@ -40,6 +40,8 @@ struct StreamArgs {
     long long stats_plane;  // floats between the tau, r_Re and r_Im planes
     int T, M, K, Wpr, nwin, n_out;
     int bin_pos0;           // samples of the open bin consumed before this block
+    int pf_windows;         // windows per L2 prefetch group (>= 1)
+    int pf_groups;          // prefetch distance in groups (0 = no prefetch)
     float c0;               // (M d + 1)/(M - 1), Table 1 group 5
     float s_low, s_high, gamma, eps, fM, fK;
 };
@@ -53,15 +55,23 @@ struct BatchArgs {
 };
 
 // ---- hardware approximations (PTX ISA: sqrt.approx / rcp.approx) --------------
+// The .ftz forms are single MUFU operations; a subnormal argument (|I| or p below
+// 1e-19) is read as 0, which changes a sum by less than the FP32 rounding of S1.
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 by the TMA engine (no registers, no wait);
+// p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // ---- streaming loads of one 16- or 32-byte unit (read once: no L1 allocation) ---
@@ -81,64 +91,69 @@ __device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
         : "l"(p));
 }
 
-// Sample k of a unit as 8 floats: re/im of xx, xy, yx, yy.  Widening a binary16
-// value to float32 is exact.
+// Sample k of a unit as 4 complex correlations (xx, xy, yx, yy), each a float2
+// (re, im).  Widening a binary16 value to float32 is exact.
 template <int DT, int UB>
-__device__ __forceinline__ void decode(const Unit<UB> &u, int k, float x[8]) {
+__device__ __forceinline__ void decode(const Unit<UB> &u, int k, float2 x[4]) {
     if constexpr (DT == DT_F32) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) x[c] = __uint_as_float(u.r[c]);
+        for (int c = 0; c < 4; ++c)
+            x[c] = make_float2(__uint_as_float(u.r[2 * c]), __uint_as_float(u.r[2 * c + 1]));
     } else {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            __half2 h = *reinterpret_cast<const __half2 *>(&u.r[4 * k + c]);
-            float2 f = __half22float2(h);
-            x[2 * c] = f.x;
-            x[2 * c + 1] = f.y;
-        }
+        for (int c = 0; c < 4; ++c)
+            x[c] = __half22float2(*reinterpret_cast<const __half2 *>(&u.r[4 * k + c]));
     }
 }
+
+// ---- packed FP32 pairs (Blackwell f32x2 pipes) -------------------------------
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // ---- per-lane window accumulators ------------------------------------------
+// The real and imaginary parts of (Q, U, V) are carried side by side in float2
+// pairs, so one packed instruction advances both directional statistics.
 struct WinAcc {
-    float s1, s2;                 // Table 1 groups 3, 4
-    float c1, c2;                 // Kahan compensation of s1, s2 (when enabled)
-    float qr, ur, vr, qi, ui, vi; // Table 2 group 4, Re and Im parts
-    float a[8];                   // sum of the raw correlations (averaging)
+    float2 s;        // (S1, S2): Table 1 groups 3, 4
+    float2 c;        // Kahan compensation of (S1, S2) (when enabled)
+    float2 q, u, v;  // (Re, Im) of the resultant sums, Table 2 group 4
+    float2 a[4];     // sums of the raw correlations (averaging)
 };
 
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-}
-
 // One sample: Eq. IQUV, then Table 1 groups 1-4 and Table 2 groups 1-4 for the Re
-// and Im parts of (Q, U, V).
+// and Im parts of (Q, U, V) at once.
 template <bool KAHAN>
-__device__ __forceinline__ void accumulate(WinAcc &A, const float x[8], float eps) {
-    const float Ir = x[0] + x[6], Ii = x[1] + x[7];   // I = xx + yy
-    const float Qr = x[0] - x[6], Qi = x[1] - x[7];   // Q = xx - yy
-    const float Ur = x[2] + x[4], Ui = x[3] + x[5];   // U = xy + yx
-    const float Vr = x[5] - x[3], Vi = x[2] - x[4];   // V = j (xy - yx)
-    const float y = Ir * Ir + Ii * Ii;                // |I|^2
-    const float z = sqrt_approx(y);                   // |I|
+__device__ __forceinline__ void accumulate(WinAcc &A, const float2 x[4], float2 eps2) {
+    const float2 I = add2(x[0], x[3]);                       // I = xx + yy
+    const float2 Q = sub2(x[0], x[3]);                       // Q = xx - yy
+    const float2 U = add2(x[1], x[2]);                       // U = xy + yx
+    const float2 V = make_float2(x[2].y - x[1].y,            // V = j (xy - yx)
+                                 x[1].x - x[2].x);
+    const float2 I2 = mul2(I, I);
+    const float y = I2.x + I2.y;                             // |I|^2
+    const float z = sqrt_approx(y);                          // |I|
     if constexpr (KAHAN) {
-        kahan_add(A.s1, A.c1, z);
-        kahan_add(A.s2, A.c2, y);
+        const float2 yk = sub2(make_float2(z, y), A.c);
+        const float2 t = add2(A.s, yk);
+        A.c = sub2(sub2(t, A.s), yk);
+        A.s = t;
     } else {
-        A.s1 += z;
-        A.s2 += y;
+        A.s = add2(A.s, make_float2(z, y));
     }
-    const float pr = sqrt_approx(Qr * Qr + Ur * Ur + Vr * Vr) + eps;
-    const float ir = rcp_approx(pr);
-    A.qr += Qr * ir; A.ur += Ur * ir; A.vr += Vr * ir;
-    const float pi = sqrt_approx(Qi * Qi + Ui * Ui + Vi * Vi) + eps;
-    const float ii = rcp_approx(pi);
-    A.qi += Qi * ii; A.ui += Ui * ii; A.vi += Vi * ii;
+    float2 n = mul2(Q, Q);                                   // q^2 + u^2 + v^2, Re and Im
+    n = fma2(U, U, n);
+    n = fma2(V, V, n);
+    const float2 p = add2(make_float2(sqrt_approx(n.x), sqrt_approx(n.y)), eps2);
+    const float2 ip = make_float2(rcp_approx(p.x), rcp_approx(p.y));
+    A.q = fma2(Q, ip, A.q);                                  // sum of q / p
+    A.u = fma2(U, ip, A.u);
+    A.v = fma2(V, ip, A.v);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) A.a[c] += x[c];
+    for (int c = 0; c < 4; ++c) A.a[c] = add2(A.a[c], x[c]);
 }
 
 template <int P>
@@ -178,13 +193,28 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     int pos = a.bin_pos0;
     int bin = 0;
     uint32_t fword = 0;
+    // L2 prefetch: lane 0 of each row keeps pf_groups groups of pf_windows windows
+    // requested ahead of the window being loaded.
+    const bool pf = a.pf_groups > 0 && lead;
+    const unsigned wbytes = (unsigned)a.M * SB;
+    const char *row_base = static_cast<const char *>(a.vis) + row * (long long)a.T * SB;
+    if (pf) {
+        const int hi = min(a.nwin, (1 + a.pf_groups) * a.pf_windows);
+        if (hi > 1) prefetch_l2(row_base + wbytes, (unsigned)(hi - 1) * wbytes);
+    }
 
+    const float2 eps2 = make_float2(a.eps, a.eps);
     for (int w = 0; w < a.nwin; ++w) {
+        if (pf && w % a.pf_windows == 0 && w > 0) {
+            const int g0 = w + a.pf_groups * a.pf_windows;
+            const int g1 = min(a.nwin, g0 + a.pf_windows);
+            if (g0 < g1) prefetch_l2(row_base + (long long)g0 * wbytes, (unsigned)(g1 - g0) * wbytes);
+        }
         WinAcc A;
-        A.s1 = A.s2 = A.c1 = A.c2 = 0.f;
-        A.qr = A.ur = A.vr = A.qi = A.ui = A.vi = 0.f;
+        const float2 zero2 = make_float2(0.f, 0.f);
+        A.s = A.c = A.q = A.u = A.v = zero2;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) A.a[c] = 0.f;
+        for (int c = 0; c < 4; ++c) A.a[c] = zero2;
         const char *wp = rp + (long long)w * a.M * SB + j * UB;
         for (int s0 = 0; s0 < S; s0 += CH) {
             Unit<UB> u[CH];
@@ -194,20 +224,17 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             for (int c = 0; c < CH; ++c) {
 #pragma unroll
                 for (int k = 0; k < SPU; ++k) {
-                    float x[8];
+                    float2 x[4];
                     decode<DT, UB>(u[c], k, x);
-                    accumulate<KAHAN>(A, x, a.eps);
+                    accumulate<KAHAN>(A, x, eps2);
                 }
             }
         }
-        if constexpr (KAHAN) {
-            A.s1 -= A.c1;
-            A.s2 -= A.c2;
-        }
+        if constexpr (KAHAN) A.s = sub2(A.s, A.c);
         // complete the window over the P lanes of the row
-        const float S1 = allsum<P>(A.s1), S2 = allsum<P>(A.s2);
-        const float qr = allsum<P>(A.qr), ur = allsum<P>(A.ur), vr = allsum<P>(A.vr);
-        const float qi = allsum<P>(A.qi), ui = allsum<P>(A.ui), vi = allsum<P>(A.vi);
+        const float S1 = allsum<P>(A.s.x), S2 = allsum<P>(A.s.y);
+        const float qr = allsum<P>(A.q.x), ur = allsum<P>(A.u.x), vr = allsum<P>(A.v.x);
+        const float qi = allsum<P>(A.q.y), ui = allsum<P>(A.u.y), vi = allsum<P>(A.v.y);
         // Table 1 groups 6-7 and Sec. 2.1: tau = c0 * (M S2 / (S1^2 + eps) - 1)
         const float s12 = S1 * S1;
         const float tau = a.c0 * (a.fM * S2 / (s12 + a.eps) - 1.0f);
@@ -241,7 +268,10 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         // flagged samples are excluded from the average (end of Sec. 2.1)
         if (!f) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] += A.a[c];
+            for (int c = 0; c < 4; ++c) {
+                acc[2 * c] += A.a[c].x;
+                acc[2 * c + 1] += A.a[c].y;
+            }
             cnt += (float)(S * SPU);
         }
         pos += a.M;

@@ -164,3 +164,35 @@ def serving_streams(seed: int = 5, n: int = 32):
     ch = rng.choice([16, 32, 64, 128], size=n)
     rho = rng.uniform(1.0, 4.0, size=n)
     return [dict(stations=int(a), channels=int(b), rho=float(r)) for a, b, r in zip(st, ch, rho)]
+
+
+def device_block(stations: int, channels: int, T: int, seed: int, device="cuda",
+                 dtype="f16", rfi_channel_frac: float = 0.10, inr_db=(-5.0, 15.0),
+                 duty=(0.01, 0.10)):
+    """A block with the LOFAR-scale noise and interference model drawn on the GPU by
+    torch's generator (for the serving workload, whose many streams would take minutes
+    to draw on the host).  Returns a tensor [B*C, T, 4, 2] of float16 or float32.
+    Not bit-identical to lofar_block for the same seed (different generator)."""
+    import torch
+    B = n_baselines(stations)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    vis = torch.randn((B, channels, T, 4, 2), generator=g, device=device,
+                      dtype=torch.float32) * math.sqrt(0.5)
+    rng = np.random.default_rng([seed, 17])
+    gains = rng.uniform(0.8, 1.2, size=(stations, 2)).astype(np.float32)
+    p, q = baseline_pairs(stations)
+    ab = [(0, 0), (0, 1), (1, 0), (1, 1)]
+    gain = np.stack([gains[p, a] * gains[q, b] for a, b in ab], axis=-1)
+    vis *= torch.from_numpy(gain).to(device)[:, None, None, :, None]
+    n_rfi = max(1, int(round(rfi_channel_frac * channels)))
+    for c in rng.choice(channels, size=n_rfi, replace=False):
+        for t0, t1 in _bursts(rng, T, rng.uniform(*duty)):
+            A = 2.0 * math.sqrt(10 ** (rng.uniform(*inr_db) / 10))
+            coh = A * _coherency(_jones(rng))
+            ph = rng.uniform(0, 2 * math.pi, size=B)
+            val = (np.cos(ph) + 1j * np.sin(ph))[:, None] * coh[None, :]
+            v = torch.from_numpy(np.stack([val.real, val.imag], -1).astype(np.float32)).to(device)
+            vis[:, int(c), t0:t1] += v[:, None]
+    vis = vis.reshape(B * channels, T, 4, 2)
+    return vis.half() if dtype == "f16" else vis

@@ -292,9 +292,16 @@ def test_invalid_arguments():
     vv = torch.zeros(st.R * T * 8 + 8, device="cuda")
     assert status(vis=vv[4:].data_ptr()) == 1                   # 16-byte misaligned
     assert status(vis=v.cpu()) == 1                             # host memory
-    small = torch.zeros((st.R - 1, T, 4, 2), device="cuda")
-    assert status(vis=small) == 1                               # too small
-    assert status(stats=out["stats"][:, :-1].contiguous()) == 1
+    # a raw allocation 4 KB shorter than the block: the range check must refuse it
+    # (sub-blocks of torch's caching allocator sit inside larger allocations)
+    from cuda.bindings import runtime as rt
+    need = st.R * T * 32
+    err, raw = rt.cudaMalloc(need - 4096)
+    assert err == rt.cudaError_t.cudaSuccess
+    try:
+        assert status(vis=int(raw)) == 1                        # too small
+    finally:
+        rt.cudaFree(raw)
     assert status(flags=None) == 1
     assert status(avg=None) == 1
     call()                                                      # the valid call works
