@@ -227,6 +227,16 @@ def serving_extras(seconds, options, torch):
     r["real_time_factor"] = r["samples_per_s"] / (R * 256 / BLOCK_SECONDS)
     res["lofar_50x"] = r
     loop.close()
+    # the same stream backlogged (3000 blocks queued at once): the rate the loop
+    # sustains for one stream, whose blocks must run one after another
+    loop = ServingLoop([dict(stations=62, channels=64, rho=1.0)], M=16, K=256, T=256,
+                       dtype="f16", options=options, hbm_budget_bytes=budget, max_batch=1,
+                       cuda_streams=2)
+    r = loop.run(0.0, arrivals=[(0.0, 0, k) for k in range(3000)])
+    r["real_time_factor"] = r["samples_per_s"] / (R * 256 / BLOCK_SECONDS)
+    r.pop("p50_latency_s"); r.pop("p99_latency_s"); r.pop("max_latency_s"); r.pop("p99_over_block")
+    res["lofar_backlogged"] = r
+    loop.close()
     torch.cuda.empty_cache()
     return res
 

@@ -30,17 +30,39 @@ from .stream import RfiStream
 class _Stream:
     def __init__(self, idx, cfg, M, K, T, thr, dtype, options, blocks):
         self.idx = idx
+        self.T = T
         self.cfg = cfg
         self.st = RfiStream(cfg["stations"], cfg["channels"], M, K, thr, dtype, **options)
         self.blocks = blocks                      # device input blocks, used round robin
         self.queue = collections.deque()          # (arrival_time, seq)
         self.busy = False
         self.done = 0
-        self.out_pool = [self.st.alloc_outputs(T) for _ in range(2)]
+        # outputs: flags and stats have a fixed shape; a block completes between
+        # floor(T/K) and floor(T/K) + 1 averaging bins, so avg/weight storage is sized
+        # for the larger count and viewed at this block's exact count
+        import torch
+        R = self.st.R
+        self.n_out_max = T // K + 1
+        self.out_pool = []
+        for _ in range(2):
+            o = self.st.alloc_outputs(T)
+            o["avg_store"] = torch.empty(R * self.n_out_max * 8, device=o["flags"].device)
+            o["weight_store"] = torch.empty(R * self.n_out_max, device=o["flags"].device)
+            self.out_pool.append(o)
         self.out_next = 0
         self.bytes_in = blocks[0].numel() * blocks[0].element_size()
         o = self.out_pool[0]
-        self.bytes_out = sum(x.numel() * x.element_size() for x in o.values())
+        self.bytes_out = sum(o[k].numel() * o[k].element_size()
+                             for k in ("flags", "stats", "avg_store", "weight_store"))
+
+    def outputs(self):
+        """Output buffers for the next block, shaped for its number of completed bins."""
+        o = self.out_pool[self.out_next]
+        self.out_next = (self.out_next + 1) % len(self.out_pool)
+        R, n = self.st.R, self.st.outputs_for(self.T)
+        return dict(flags=o["flags"], stats=o["stats"],
+                    avg=o["avg_store"][:R * n * 8].view(R, n, 4, 2),
+                    weight=o["weight_store"][:R * n].view(R, n))
 
 
 class ServingLoop:
@@ -135,8 +157,7 @@ class ServingLoop:
                     if len(items) >= self.max_batch or nb + need > free_bytes:
                         break
                     ta, k = s.queue.popleft()
-                    out = s.out_pool[s.out_next]
-                    s.out_next = (s.out_next + 1) % len(s.out_pool)
+                    out = s.outputs()
                     s.busy = True
                     items.append((s, ta, k, out))
                     nb += need
@@ -146,8 +167,10 @@ class ServingLoop:
                     B.rfi_process_batch([s.st.ctx for s, _, _, _ in items], vis,
                                         [self.T] * len(items),
                                         [o["flags"] for _, _, _, o in items],
-                                        [o["avg"] for _, _, _, o in items],
-                                        [o["weight"] for _, _, _, o in items],
+                                        [o["avg"] if o["avg"].numel() else None
+                                         for _, _, _, o in items],
+                                        [o["weight"] if o["weight"].numel() else None
+                                         for _, _, _, o in items],
                                         [o["stats"] for _, _, _, o in items], stream=cs)
                     ev = torch.cuda.Event(enable_timing=True)
                     ev.record(cs)

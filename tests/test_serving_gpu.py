@@ -1,0 +1,54 @@
+"""Continuous batching: every stream's results in the serving mix equal, bit for bit,
+the results of the same blocks processed alone."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from paper_2412_14775_b300 import RfiStream, default_thresholds
+from paper_2412_14775_b300.serve import ServingLoop
+
+pytestmark = pytest.mark.gpu
+
+
+def test_serving_mix_equals_solo():
+    M, K, T = 16, 32, 48          # bins of 32 straddle blocks of 48: the carry is exercised
+    cfgs = [dict(stations=n, channels=c, rho=r) for n, c, r in
+            ((5, 4, 3.0), (9, 8, 2.0), (7, 16, 4.0), (12, 4, 1.5), (4, 8, 3.5), (8, 16, 2.5))]
+    thr = default_thresholds(M)
+    blocks = [[synth.generate.device_block(c["stations"], c["channels"], T, seed=100 + 7 * i + k)
+               for k in range(3)] for i, c in enumerate(cfgs)]
+    loop = ServingLoop(cfgs, M=M, K=K, T=T, thresholds=thr, dtype="f16", block_seconds=0.01,
+                       max_batch=4, cuda_streams=3, record_outputs=True, blocks=blocks,
+                       hbm_budget_bytes=1 << 30)
+    stats = loop.run(1.0, seed=3)
+    assert stats["blocks"] > 200
+    assert stats["mean_batch"] > 1.0, stats          # blocks were batched together
+    opts = loop.streams[0].st.options
+    for i, cfg in enumerate(cfgs):
+        got = sorted(loop.outputs[i], key=lambda t: t[0])
+        assert [k for k, _ in got] == list(range(len(got)))
+        solo = RfiStream(cfg["stations"], cfg["channels"], M, K, thr, "f16",
+                         lanes_per_row=opts["lanes_per_row"],
+                         warps_per_block=opts["warps_per_block"])
+        for k, mixed in got:
+            o = solo.process(blocks[i][k % 3])
+            torch.cuda.synchronize()
+            for name in ("flags", "avg", "weight", "stats"):
+                assert np.array_equal(o[name].cpu().numpy(), mixed[name]), (i, k, name)
+        solo.close()
+    loop.close()
+
+
+def test_serving_admission_respects_memory_budget():
+    """With a budget that fits one block at a time, batches hold a single block and
+    every block is still served."""
+    M, K, T = 16, 16, 32
+    cfgs = [dict(stations=6, channels=8, rho=4.0), dict(stations=6, channels=8, rho=4.0)]
+    loop = ServingLoop(cfgs, M=M, K=K, T=T, dtype="f16", block_seconds=0.01, max_batch=8,
+                       pool_blocks=1)
+    s0 = loop.streams[0]
+    loop.budget = s0.bytes_in + s0.bytes_out        # room for exactly one block
+    stats = loop.run(0.3, seed=1)
+    assert stats["blocks"] > 0 and stats["mean_batch"] == 1.0
+    loop.close()
