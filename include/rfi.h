@@ -171,6 +171,36 @@ int rfi_batch_graph_launch(rfi_batch_graph *g, const void *const *vis, uint32_t 
                            void *stream);
 int rfi_batch_graph_destroy(rfi_batch_graph *g);
 
+/* ---- Entry point that allocates nothing ------------------------------------
+ * The paper has no counterpart; this serves callers that may not allocate device
+ * memory -- e.g. a pipeline stage whose GPU memory is reserved up front by its own
+ * pool, or a real-time thread that cannot risk the implicit synchronisation of an
+ * allocation.  They pass their own inputs and outputs; the only working memory, the
+ * carry of each row's open averaging bin, lives in a fixed device array of
+ * RFI_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until exit.
+ *
+ * rfi_process_block_noalloc processes one block like rfi_process_block, without a
+ * context: geometry, thresholds and dtype come with every call, and n_seen is the
+ * number of samples of this stream processed before the block (a multiple of M).
+ * Buffers, layouts and alignment are those of rfi_process_block.  The kernel uses
+ * one lane per row, so results equal rfi_process_block on a context created with
+ * lanes_per_row = 1 and otherwise default options.
+ *   - Limit: R * 36 bytes of carry must fit the array, i.e. at most
+ *     RFI_NOALLOC_SCRATCH_BYTES / 36 = 116508 rows; larger streams get RFI_EINVAL.
+ *   - The first call on each device looks up the array's device address with
+ *     cudaGetSymbolAddress (which may load the module); make that first call before
+ *     any stream capture.
+ *   - Every call shares the array, and it keeps what the last call wrote.  A block
+ *     that continues an open bin (n_seen % K != 0) reads the carry left by the
+ *     previous call, so such blocks of one stream must follow each other with no
+ *     call for another stream in between.  Calls that overlap on the GPU race.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine. */
+#define RFI_NOALLOC_SCRATCH_BYTES (4u << 20)
+int rfi_process_block_noalloc(int stations, int channels, int window_M, int avg_K,
+                              const rfi_thresholds *thr, rfi_dtype dtype, long long n_seen,
+                              const void *vis, int T, uint32_t *flags, float *avg,
+                              float *weight, float *stats, void *stream);
+
 /* Drop the averaging carry and the sample count (stream restart); clears a sticky
  * error.  Synchronises with work already issued for the context. */
 int rfi_reset(rfi_ctx *ctx);

@@ -23,7 +23,10 @@ EXPORTED = ["rfi_create", "rfi_create_ex", "rfi_rows", "rfi_outputs_for", "rfi_g
             "rfi_set_thresholds", "rfi_process_block", "rfi_process_block_host",
             "rfi_process_batch", "rfi_batch_graph_create", "rfi_batch_graph_launch",
             "rfi_batch_graph_destroy", "rfi_reset", "rfi_destroy", "rfi_status_str",
-            "rfi_last_error"]
+            "rfi_last_error", "rfi_process_block_noalloc"]
+
+# Fixed size of the library's no-allocation scratch (RFI_NOALLOC_SCRATCH_BYTES).
+RFI_NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
 class RfiError(RuntimeError):
@@ -75,6 +78,8 @@ def load_library(path=None):
         "rfi_batch_graph_destroy": ([vp], ip),
         "rfi_reset": ([vp], ip),
         "rfi_destroy": ([vp], ip),
+        "rfi_process_block_noalloc": ([ip, ip, ip, ip, ctypes.POINTER(rfi_thresholds), ip,
+                                       ctypes.c_longlong, vp, ip, vp, vp, vp, vp, vp], ip),
         "rfi_status_str": ([ip], ctypes.c_char_p),
         "rfi_last_error": ([], ctypes.c_char_p),
     }
@@ -226,6 +231,16 @@ def rfi_batch_graph_launch(g, vis, flags, avg, weight, stats, stream=None):
 
 def rfi_batch_graph_destroy(g):
     _check(load_library().rfi_batch_graph_destroy(g), "rfi_batch_graph_destroy")
+
+
+def rfi_process_block_noalloc(stations, channels, window_M, avg_K, thresholds, dtype, n_seen,
+                              vis, T, flags, avg, weight, stats, stream=None):
+    """Context-free block processing that allocates nothing (see include/rfi.h)."""
+    t = _thr(thresholds)
+    _check(load_library().rfi_process_block_noalloc(
+        stations, channels, window_M, avg_K, ctypes.byref(t), _dtype(dtype), n_seen, _ptr(vis),
+        T, _ptr(flags), _ptr(avg), _ptr(weight), _ptr(stats), _stream(stream)),
+        "rfi_process_block_noalloc")
 
 
 def rfi_reset(ctx):

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "_lib", "librfi.so")
-SOURCES = ["rfi_api.cu"]
+SOURCES = ["rfi_api.cu", "rfi_noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -33,11 +33,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if os.path.getmtime(LIB) >= newest:
             return LIB
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    objdir = os.path.join(HERE, "_lib", "obj")
+    os.makedirs(objdir, exist_ok=True)
+    # translation units compile in parallel, then one link step
+    procs, objs = [], []
+    for src in SOURCES:
+        obj = os.path.join(objdir, src.replace(".cu", f".{os.getpid()}.o"))
+        cmd = [NVCC, *ARCH, *FLAGS, "-c", "-o", obj, os.path.join(CSRC, src)]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    failed = [p.wait() for p in procs]
+    if any(failed):
+        raise RuntimeError(f"nvcc failed for {[s for s, r in zip(SOURCES, failed) if r]}")
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, *FLAGS, "-shared", "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+    subprocess.check_call([NVCC, *ARCH, "--cudart", "static", "-shared", "-o", tmp, *objs])
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

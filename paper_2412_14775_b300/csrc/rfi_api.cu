@@ -7,6 +7,7 @@
 // persistent batch launch, optionally replayed from a CUDA graph.
 #include "rfi.h"
 #include "rfi_device.cuh"
+#include "rfi_internal.h"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -387,6 +388,13 @@ void free_ctx(rfi_ctx *c) {
 }
 
 }  // namespace
+
+int rfi_internal_fail(int status, const char *msg) { return fail(status, "%s", msg); }
+
+int rfi_internal_check_dev(const void *p, size_t bytes, size_t align, int device,
+                           const char *what) {
+    return check_dev(p, bytes, align, device, what);
+}
 
 extern "C" {
 
