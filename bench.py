@@ -205,6 +205,56 @@ def cpu_baseline(seconds_target=10.0):
                       f"{dt:.1f} s single-threaded"}
 
 
+def batched_extras(options, torch, steps=300, warmup=10):
+    """8 uneven binary16 subbands (stations 24..76, channels 16..128, T = 256) in one
+    persistent launch replayed from a CUDA graph, against the same 8 streams launched
+    one after another."""
+    import synth
+    from paper_2412_14775_b300 import RfiStream, binding, default_thresholds
+    M, K, T = 16, 256, 256
+    thr = default_thresholds(M)
+    opts = {k: v for k, v in options.items() if k != "max_registers"}
+    geo = list(zip(synth.BATCH_STATIONS, synth.BATCH_CHANNELS))
+    streams = [RfiStream(n, c, M, K, thr, "f16", **opts) for n, c in geo]
+    solo = [RfiStream(n, c, M, K, thr, "f16", **opts) for n, c in geo]
+    vis = [synth.generate.device_block(n, c, T, seed=300 + i) for i, (n, c) in enumerate(geo)]
+    outs = [s.alloc_outputs(T) for s in streams]
+    samples = sum(s.R for s in streams) * T
+    nbytes = sum(algo_bytes(s.R, T, M, K, 1, 16) for s in streams)
+    g = binding.rfi_batch_graph_create([s.ctx for s in streams], [T] * len(streams))
+    cs = torch.cuda.current_stream()
+
+    def step_graph():
+        binding.rfi_batch_graph_launch(g, vis, [o["flags"] for o in outs],
+                                       [o["avg"] for o in outs], [o["weight"] for o in outs],
+                                       [o["stats"] for o in outs], stream=cs)
+
+    def step_solo():
+        for st, v, o in zip(solo, vis, outs):
+            st.process(v, out=o, stream=cs)
+
+    res = {"streams": len(geo), "samples_per_step": samples, "algorithmic_bytes": nbytes}
+    for name, fn in (("graph_persistent", step_graph), ("sequential_launches", step_solo)):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cs)
+        for _ in range(steps):
+            fn()
+        b.record(cs)
+        torch.cuda.synchronize()
+        dt = a.elapsed_time(b) * 1e-3 / steps
+        res[name] = {"us_per_step": dt * 1e6, "samples_per_s": samples / dt,
+                     "achieved_gbs": nbytes / dt / 1e9}
+    binding.rfi_batch_graph_destroy(g)
+    for s in streams + solo:
+        s.close()
+    del vis, outs
+    torch.cuda.empty_cache()
+    return res
+
+
 def serving_extras(seconds, options, torch):
     """The serving loop: 32 mixed FP16 streams at 1-4x real time, then the 62-station,
     64-channel stream offered at 50x real time."""
@@ -362,6 +412,7 @@ def main():
         extras["fp16"] = fp16
         del vis16
         torch.cuda.empty_cache()
+        extras["batched"] = batched_extras(fp16["M16"]["options"], torch)
         if args.serve_seconds > 0:
             extras["serving"] = serving_extras(args.serve_seconds,
                                                fp16["M16"]["options"], torch)

@@ -92,7 +92,10 @@ typedef enum {
  *   prefetch_bytes   size of one L2 bulk prefetch per row, rounded down to whole
  *                  windows (at least one); a multiple of 16; 0 = 1024.
  *   prefetch_groups  how many such groups each row keeps requested ahead of the
- *                  window being loaded; -1 = no prefetch, 0 = 2.
+ *                  window being loaded; 0 or -1 = no prefetch (default).
+ *   max_registers  register budget per thread of the single-stream kernel: 0 or 128
+ *                  (default), 80 or 64 (more resident warps; at most 8 warps per
+ *                  block; lanes_per_row <= 8).  Results do not depend on it.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -104,6 +107,7 @@ typedef struct {
     int compensated;
     int prefetch_bytes;
     int prefetch_groups;
+    int max_registers;
 } rfi_options;
 
 /* Create a context for one stream of `stations` stations (B = N(N+1)/2 baselines)

@@ -47,6 +47,13 @@ def _load():
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.oracle_process_block.restype = ctypes.c_int
+        lib.oracle_process_block_tf.argtypes = [
+            ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+            ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_process_block_tf.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -118,10 +125,12 @@ class OracleStream:
     results as one long block.
     """
 
-    def __init__(self, R, M, K, d, s_low, s_high, gamma, eps, compensated=False):
-        if M < 2 or K % M != 0:
-            raise ValueError("need M >= 2 and K a multiple of M")
-        self.R, self.M, self.K = int(R), int(M), int(K)
+    def __init__(self, R, M, K, d, s_low, s_high, gamma, eps, compensated=False, F=1):
+        """M: samples per row in a window; F: adjacent rows (channels) per window, so
+        a window holds W = M * F samples; R must be a multiple of F."""
+        if M * F < 2 or K % M != 0 or R % F != 0:
+            raise ValueError("need M*F >= 2, K a multiple of M and R a multiple of F")
+        self.R, self.M, self.K, self.F = int(R), int(M), int(K), int(F)
         self.thr = np.array([d, s_low, s_high, gamma, eps], dtype=np.float64)
         self.compensated = bool(compensated)
         self.n_seen = 0
@@ -142,13 +151,15 @@ class OracleStream:
         nw = T // self.M
         nwords = (T + 31) // 32
         n_out = self.outputs_for(T)
+        G = R // self.F
         out = dict(
-            tau=np.zeros((R, nw)), r_re=np.zeros((R, nw)), r_im=np.zeros((R, nw)),
-            wflag=np.zeros((R, nw), dtype=np.uint8),
+            tau=np.zeros((G, nw)), r_re=np.zeros((G, nw)), r_im=np.zeros((G, nw)),
+            wflag=np.zeros((G, nw), dtype=np.uint8),
             flagbits=np.zeros((R, nwords), dtype=np.uint32),
             avg=np.zeros((R, n_out, 8)), weight=np.zeros((R, n_out)))
-        rc = _load().oracle_process_block(
-            v.ctypes.data, R, T, self.M, self.K, self.thr.ctypes.data, int(self.compensated),
+        rc = _load().oracle_process_block_tf(
+            v.ctypes.data, R, T, self.M, self.F, self.K, self.thr.ctypes.data,
+            int(self.compensated),
             self.n_seen, self.carry_sum.ctypes.data, self.carry_cnt.ctypes.data,
             out["tau"].ctypes.data, out["r_re"].ctypes.data, out["r_im"].ctypes.data,
             out["wflag"].ctypes.data, out["flagbits"].ctypes.data,

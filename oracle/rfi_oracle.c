@@ -132,81 +132,115 @@ long long oracle_outputs_for(long long n_seen, int T, int K)
 
 /* ---- One block of one stream ----------------------------------------------------
  * vis      [R][T][8] doubles: rows are (baseline, channel) streams, 8 = re/im of
- *          xx, xy, yx, yy.  Every row is processed separately (Sec. 2: each of the
- *          N(N+1)/2 streams is mitigated on its own).
+ *          xx, xy, yx, yy.  Rows are mitigated separately (Sec. 2), except that a
+ *          window may span F adjacent rows (F channels of one baseline): the paper's
+ *          windows are time-frequency footprints of W = T x F samples (Secs. 3.2, 4).
+ * Mt       samples per row in a window (the time extent); W = Mt * F.
  * thr      {d, s_low, s_high, gamma, eps}
- * n_seen   samples of this stream already consumed by earlier blocks (multiple of W)
+ * n_seen   samples of this stream already consumed by earlier blocks (multiple of Mt)
  * carry_sum [R][8], carry_cnt [R]: running sum of unflagged samples and their count
- *          in the open averaging bin; read at entry, written at exit.
+ *          in the open averaging bin of every row; read at entry, written at exit.
  * Outputs (caller-allocated):
- *   tau, r_re, r_im, wflag  [R][T/W]
+ *   tau, r_re, r_im, wflag  [R/F][T/Mt]
  *   flagbits                [R][ceil(T/32)]  bit (t mod 32) of word t/32 = flag of sample t
  *   avg                     [R][n_out][8]    mean of unflagged samples of each completed bin
  *   weight                  [R][n_out]       unflagged count / K
  * Returns 0, or -1 on invalid sizes.  */
+int oracle_process_block_tf(const double *vis, int R, int T, int Mt, int F, int K,
+                            const double thr[5], int compensated, long long n_seen,
+                            double *carry_sum, double *carry_cnt,
+                            double *tau, double *r_re, double *r_im, uint8_t *wflag,
+                            uint32_t *flagbits, double *avg, double *weight)
+{
+    if (R < 0 || T < 0 || Mt < 1 || F < 1 || Mt * F < 2 || R % F != 0 || K < Mt ||
+        T % Mt != 0 || K % Mt != 0 || n_seen % Mt != 0)
+        return -1;
+    const double d = thr[0], s_low = thr[1], s_high = thr[2], gamma = thr[3], eps = thr[4];
+    const int W = Mt * F;                     /* samples in one window */
+    const int nwin = T / Mt;
+    const int nwords = (T + 31) / 32;
+    const int G = R / F;                      /* window rows (channel groups) */
+    const long long n_out = oracle_outputs_for(n_seen, T, K);
+    const long long first_bin = n_seen / K;
+    double *stokes = (double *)malloc(sizeof(double) * 8 * (size_t)W);
+    acc_t *bins = (acc_t *)malloc(sizeof(acc_t) * 8 * (size_t)F);
+    double *bins_n = (double *)malloc(sizeof(double) * (size_t)F);
+    if (!stokes || !bins || !bins_n) {
+        free(stokes); free(bins); free(bins_n);
+        return -1;
+    }
+
+    for (int g = 0; g < G; ++g) {
+        for (int k = 0; k < F; ++k) {
+            const int row = g * F + k;
+            uint32_t *fb = flagbits + (size_t)row * nwords;
+            for (int q = 0; q < nwords; ++q) fb[q] = 0;
+            /* open-bin running sums continue from the previous block (Kahan state not
+             * carried: the carry is the plain value) */
+            acc_t *bin = bins + 8 * k;
+            for (int c = 0; c < 8; ++c) { bin[c].s = carry_sum[(size_t)row * 8 + c]; bin[c].c = 0; }
+            bins_n[k] = carry_cnt[row];
+        }
+        for (int w = 0; w < nwin; ++w) {
+            /* the window's W samples: Mt samples of each of the F rows, row by row */
+            for (int k = 0; k < F; ++k) {
+                const double *vw = vis + ((size_t)(g * F + k) * T + (size_t)w * Mt) * 8;
+                for (int i = 0; i < Mt; ++i) oracle_stokes(vw + 8 * i, stokes + 8 * (k * Mt + i));
+            }
+            const double t  = oracle_sk_window(stokes, W, d, eps, compensated, 0, 0);
+            const double rr = oracle_ds_window(stokes, W, 0, eps, compensated, 0);
+            const double ri = oracle_ds_window(stokes, W, 1, eps, compensated, 0);
+            const int f = oracle_flag(t, rr, ri, s_low, s_high, gamma);
+
+            const size_t o = (size_t)g * nwin + w;
+            tau[o] = t; r_re[o] = rr; r_im[o] = ri; wflag[o] = (uint8_t)f;
+
+            const long long g_end = n_seen + (long long)(w + 1) * Mt;   /* stream index */
+            for (int k = 0; k < F; ++k) {
+                const int row = g * F + k;
+                const double *vw = vis + ((size_t)row * T + (size_t)w * Mt) * 8;
+                uint32_t *fb = flagbits + (size_t)row * nwords;
+                acc_t *bin = bins + 8 * k;
+                /* every sample of a flagged window is flagged (Sec. 2.1, last sentence) */
+                for (int i = 0; i < Mt; ++i) {
+                    const int ts = w * Mt + i;
+                    if (f) fb[ts / 32] |= (uint32_t)1u << (ts % 32);
+                }
+                /* flagged samples are left out of the time average (Sec. 2.1) */
+                if (!f) {
+                    for (int i = 0; i < Mt; ++i)
+                        for (int c = 0; c < 8; ++c) acc_add(&bin[c], vw[8 * i + c], compensated);
+                    bins_n[k] += Mt;
+                }
+                if (g_end % K == 0) {
+                    const long long b = g_end / K - 1 - first_bin;          /* output slot */
+                    double *ao = avg + ((size_t)row * n_out + b) * 8;
+                    const double bin_n = bins_n[k];
+                    for (int c = 0; c < 8; ++c) ao[c] = bin_n > 0 ? acc_val(&bin[c]) / bin_n : 0.0;
+                    weight[(size_t)row * n_out + b] = bin_n / (double)K;
+                    for (int c = 0; c < 8; ++c) { bin[c].s = 0; bin[c].c = 0; }
+                    bins_n[k] = 0;
+                }
+            }
+        }
+        for (int k = 0; k < F; ++k) {
+            const int row = g * F + k;
+            for (int c = 0; c < 8; ++c) carry_sum[(size_t)row * 8 + c] = acc_val(&bins[8 * k + c]);
+            carry_cnt[row] = bins_n[k];
+        }
+    }
+    free(stokes); free(bins); free(bins_n);
+    return 0;
+}
+
+/* Time-only windows of W samples per row (F = 1). */
 int oracle_process_block(const double *vis, int R, int T, int W, int K,
                          const double thr[5], int compensated, long long n_seen,
                          double *carry_sum, double *carry_cnt,
                          double *tau, double *r_re, double *r_im, uint8_t *wflag,
                          uint32_t *flagbits, double *avg, double *weight)
 {
-    if (R < 0 || T < 0 || W < 2 || K < W || T % W != 0 || K % W != 0 || n_seen % W != 0)
-        return -1;
-    const double d = thr[0], s_low = thr[1], s_high = thr[2], gamma = thr[3], eps = thr[4];
-    const int nwin = T / W;
-    const int nwords = (T + 31) / 32;
-    const long long n_out = oracle_outputs_for(n_seen, T, K);
-    const long long first_bin = n_seen / K;
-    double *stokes = (double *)malloc(sizeof(double) * 8 * (size_t)W);
-    if (!stokes) return -1;
-
-    for (int row = 0; row < R; ++row) {
-        const double *vr = vis + (size_t)row * T * 8;
-        uint32_t *fb = flagbits + (size_t)row * nwords;
-        for (int k = 0; k < nwords; ++k) fb[k] = 0;
-
-        /* open-bin running sums continue from the previous block (Kahan state not
-         * carried: the carry is the plain value) */
-        acc_t bin[8];
-        for (int c = 0; c < 8; ++c) { bin[c].s = carry_sum[(size_t)row * 8 + c]; bin[c].c = 0; }
-        double bin_n = carry_cnt[row];
-
-        for (int w = 0; w < nwin; ++w) {
-            const double *vw = vr + (size_t)w * W * 8;
-            for (int i = 0; i < W; ++i) oracle_stokes(vw + 8 * i, stokes + 8 * i);
-
-            const double t  = oracle_sk_window(stokes, W, d, eps, compensated, 0, 0);
-            const double rr = oracle_ds_window(stokes, W, 0, eps, compensated, 0);
-            const double ri = oracle_ds_window(stokes, W, 1, eps, compensated, 0);
-            const int f = oracle_flag(t, rr, ri, s_low, s_high, gamma);
-
-            const size_t o = (size_t)row * nwin + w;
-            tau[o] = t; r_re[o] = rr; r_im[o] = ri; wflag[o] = (uint8_t)f;
-
-            /* every sample of a flagged window is flagged (Sec. 2.1, last sentence) */
-            for (int i = 0; i < W; ++i) {
-                const int ts = w * W + i;
-                if (f) fb[ts / 32] |= (uint32_t)1u << (ts % 32);
-            }
-            /* flagged samples are left out of the time average (Sec. 2.1) */
-            if (!f) {
-                for (int i = 0; i < W; ++i)
-                    for (int c = 0; c < 8; ++c) acc_add(&bin[c], vw[8 * i + c], compensated);
-                bin_n += W;
-            }
-            const long long g_end = n_seen + (long long)(w + 1) * W;   /* stream index */
-            if (g_end % K == 0) {
-                const long long b = g_end / K - 1 - first_bin;          /* output slot */
-                double *ao = avg + ((size_t)row * n_out + b) * 8;
-                for (int c = 0; c < 8; ++c) ao[c] = bin_n > 0 ? acc_val(&bin[c]) / bin_n : 0.0;
-                weight[(size_t)row * n_out + b] = bin_n / (double)K;
-                for (int c = 0; c < 8; ++c) { bin[c].s = 0; bin[c].c = 0; }
-                bin_n = 0;
-            }
-        }
-        for (int c = 0; c < 8; ++c) carry_sum[(size_t)row * 8 + c] = acc_val(&bin[c]);
-        carry_cnt[row] = bin_n;
-    }
-    free(stokes);
-    return 0;
+    if (W < 2) return -1;
+    return oracle_process_block_tf(vis, R, T, W, 1, K, thr, compensated, n_seen, carry_sum,
+                                   carry_cnt, tau, r_re, r_im, wflag, flagbits, avg, weight);
 }

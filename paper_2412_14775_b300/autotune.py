@@ -1,7 +1,8 @@
 """Autotuner for the flagging kernel's launch shape.
 
 For one workload (dtype, M, K, T, rows) it times candidate options of rfi_create_ex
--- lanes per row P, warps per block, L2 prefetch group size and distance -- on the
+-- lanes per row P, warps per block, register budget, L2 prefetch group size and
+distance -- on the
 caller's device data with CUDA events, and returns the fastest.  Results are cached
 in memory and, when `cache_path` is given, in a JSON file keyed by the workload.
 
@@ -73,21 +74,26 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
             print(f"  {o} {t * 1e6:.1f} us")
         return t
 
-    best, best_t = None, float("inf")
+    # stage 1: launch shape without prefetch; stage 2: prefetch for the three best
+    shapes = [(4, 0), (8, 0), (16, 0), (4, 80), (8, 80), (4, 64), (8, 64)]
+    stage1 = []
     for P in candidates_p(M, dtype):
-        for wpb in (4, 8, 16):
-            o = dict(lanes_per_row=P, warps_per_block=wpb)
-            t = run(o)
-            if t < best_t:
-                best, best_t = o, t
-    for pg in (-1, 1, 2, 4, 8):
-        for pb in (512, 1024, 2048, 4096):
-            if pg == -1 and pb != 1024:
+        for wpb, regs in shapes:
+            o = dict(lanes_per_row=P, warps_per_block=wpb, max_registers=regs,
+                     prefetch_groups=0, prefetch_bytes=1024)
+            try:
+                stage1.append((run(o), o))
+            except B.RfiError:          # no kernel with this register budget
                 continue
-            o = dict(best, prefetch_groups=pg, prefetch_bytes=pb)
-            t = run(o)
-            if t < best_t:
-                best, best_t = o, t
+    stage1.sort(key=lambda x: x[0])
+    best_t, best = stage1[0]
+    for _, base in stage1[:3]:
+        for pg in (1, 2):
+            for pb in (512, 1024):
+                o = dict(base, prefetch_groups=pg, prefetch_bytes=pb)
+                t = run(o)
+                if t < best_t:
+                    best, best_t = o, t
     best = dict(best, seconds=best_t)
     _MEM[key] = best
     if cache_path:

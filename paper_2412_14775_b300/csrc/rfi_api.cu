@@ -8,6 +8,7 @@
 #include "rfi.h"
 #include "rfi_device.cuh"
 #include "rfi_internal.h"
+#include "rfi_kernels.h"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -36,45 +37,21 @@ int fail(int status, const char *fmt, ...) {
     return status;
 }
 
-// ---- kernel instance table ------------------------------------------------------
-typedef void (*BlockFn)(StreamArgs);
-typedef void (*BatchFn)(BatchArgs);
-
-struct Instance {
-    int dt, spu, P, ch, kahan;
-    const void *block_fn;
-    const void *batch_fn;
-};
-
-#define RFI_INST(DT, SPU, P, CH, K)                                                         \
-    {DT, SPU, P, CH, K, (const void *)&k_block<DT, SPU, P, CH, (bool)K>,                   \
-     (const void *)&k_batch<DT, SPU, P, CH, (bool)K>}
-#define RFI_INST_CH(DT, SPU, P, K)                                                           \
-    RFI_INST(DT, SPU, P, 1, K), RFI_INST(DT, SPU, P, 2, K), RFI_INST(DT, SPU, P, 4, K),     \
-        RFI_INST(DT, SPU, P, 5, K), RFI_INST(DT, SPU, P, 8, K)
-#define RFI_INST_P(DT, SPU, K)                                                               \
-    RFI_INST_CH(DT, SPU, 1, K), RFI_INST_CH(DT, SPU, 2, K), RFI_INST_CH(DT, SPU, 4, K),     \
-        RFI_INST_CH(DT, SPU, 8, K), RFI_INST_CH(DT, SPU, 16, K), RFI_INST_CH(DT, SPU, 32, K)
-
-const Instance g_instances[] = {
-    RFI_INST_P(DT_F32, 1, 0),
-    RFI_INST_P(DT_F16, 2, 0),
-    RFI_INST_P(DT_F32, 1, 1),
-    RFI_INST_P(DT_F16, 2, 1),
-    // binary16 input with an odd window: one sample per 16-byte unit, one lane per row
-    RFI_INST_CH(DT_F16, 1, 1, 0),
-    RFI_INST_CH(DT_F16, 1, 1, 1),
-};
-
-const Instance *find_instance(int dt, int spu, int P, int ch, int kahan) {
-    for (const Instance &in : g_instances)
-        if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan)
-            return &in;
+// ---- kernel instances (rfi_inst_f32.cu, rfi_inst_f16.cu) ----------------------
+const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb) {
+    const InstanceTable tabs[] = {instances_f32(), instances_f16()};
+    for (const InstanceTable &t : tabs)
+        for (int i = 0; i < t.n; ++i) {
+            const Instance &in = t.items[i];
+            if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan &&
+                in.lb == lb)
+                return &in;
+        }
     return nullptr;
 }
 
 int largest_chunk(int S) {
-    static const int opts[] = {8, 5, 4, 2, 1};
+    static const int opts[] = {5, 4, 2, 1};
     for (int c : opts)
         if (S % c == 0) return c;
     return 1;
@@ -114,7 +91,7 @@ struct rfi_ctx {
     long long B, C, R;
     rfi_dtype dtype;
     rfi_thresholds thr;
-    int P, spu, S, ch, kahan, wpb;
+    int P, spu, S, ch, kahan, wpb, lb;
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     const Instance *inst;
     long long n_seen;
@@ -223,8 +200,11 @@ int choose_shape(rfi_ctx *c, int P_req) {
     c->spu = spu;
     c->S = c->M / (P * spu);
     c->ch = largest_chunk(c->S);
-    c->inst = find_instance(dt, spu, P, c->ch, c->kahan);
-    if (!c->inst) return fail(RFI_EUNSUPPORTED, "no kernel for this launch shape");
+    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb);
+    if (!c->inst)
+        return fail(RFI_EUNSUPPORTED,
+                    "no kernel for this launch shape (reduced register budgets exist for "
+                    "lanes_per_row <= 8, 2-5 load units per chunk, no Kahan summation)");
     return RFI_OK;
 }
 
@@ -257,6 +237,7 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.eps = (float)c->thr.eps;
     a.fM = (float)c->M;
     a.fK = (float)c->K;
+    a.invM = (float)(1.0 / c->M);
     const int wbytes = c->M * sample_bytes(c->dtype);
     a.pf_windows = std::max(1, c->pf_bytes / wbytes);
     a.pf_groups = c->pf_groups;
@@ -337,7 +318,8 @@ int build_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *
         if ((rc = check_ctx(ctxs[i]))) return rc;
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return fail(RFI_EINVAL, "context %d appears twice", i);
-        if (ctxs[i]->inst != ctxs[0]->inst || ctxs[i]->device != ctxs[0]->device)
+        if (ctxs[i]->inst->batch_fn != ctxs[0]->inst->batch_fn ||
+            ctxs[i]->device != ctxs[0]->device)
             return fail(RFI_EINVAL, "context %d differs in dtype, M or launch shape", i);
     }
     b->n = n;
@@ -425,11 +407,12 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     if (dtype != RFI_C64 && dtype != RFI_C32H) return fail(RFI_EINVAL, "unknown dtype");
     int rc;
     if ((rc = check_thresholds(thr))) return rc;
-    rfi_options o = {0, 0, 0, 0, 0, 0, 0};
+    rfi_options o = {0, 0, 0, 0, 0, 0, 0, 0};
     if (opt) o = *opt;
     if (o.warps_per_block < 0 || o.warps_per_block > 16 || o.host_max_T < 0 || o.host_chunks < 0 ||
         o.compensated < -1 || o.compensated > 1 || o.prefetch_bytes < 0 ||
-        o.prefetch_bytes % 16 != 0 || o.prefetch_groups > 64)
+        o.prefetch_bytes % 16 != 0 || o.prefetch_groups > 64 ||
+        (o.max_registers != 0 && o.max_registers < 64))
         return fail(RFI_EINVAL, "bad options");
 
     rfi_ctx *c = new (std::nothrow) rfi_ctx();
@@ -452,8 +435,13 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->thr = *thr;
     c->kahan = o.compensated == 1 || (o.compensated == 0 && window_M >= 64);
     c->wpb = o.warps_per_block ? o.warps_per_block : 8;
+    c->lb = o.max_registers == 0 || o.max_registers >= 128 ? 0 : (o.max_registers >= 80 ? 1 : 2);
+    if (c->lb > 0 && c->wpb > 8) {
+        delete c;
+        return fail(RFI_EINVAL, "max_registers below 128 allows at most 8 warps per block");
+    }
     c->pf_bytes = o.prefetch_bytes ? o.prefetch_bytes : 1024;
-    c->pf_groups = o.prefetch_groups == 0 ? 2 : (o.prefetch_groups < 0 ? 0 : o.prefetch_groups);
+    c->pf_groups = o.prefetch_groups > 0 ? o.prefetch_groups : 0;
     c->status = RFI_OK;
     if ((rc = choose_shape(c, o.lanes_per_row))) {
         delete c;
@@ -542,7 +530,8 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->host_chunks = ctx->host_chunks;
     opt->compensated = ctx->kahan ? 1 : -1;
     opt->prefetch_bytes = ctx->pf_bytes;
-    opt->prefetch_groups = ctx->pf_groups ? ctx->pf_groups : -1;
+    opt->prefetch_groups = ctx->pf_groups;
+    opt->max_registers = ctx->lb == 0 ? 128 : (ctx->lb == 1 ? 80 : 64);
     return RFI_OK;
 }
 

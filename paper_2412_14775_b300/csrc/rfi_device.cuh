@@ -44,6 +44,7 @@ struct StreamArgs {
     int pf_groups;          // prefetch distance in groups (0 = no prefetch)
     float c0;               // (M d + 1)/(M - 1), Table 1 group 5
     float s_low, s_high, gamma, eps, fM, fK;
+    float invM;             // 1/M (exact when M is a power of two)
 };
 
 struct BatchArgs {
@@ -166,7 +167,9 @@ __device__ __forceinline__ float allsum(float v) {
 // ---- one row group of one stream ---------------------------------------------
 // DT: input dtype; SPU: samples per load unit (1 or 2); P: lanes per row;
 // CH: load units issued together per lane; KAHAN: compensated S1, S2.
-template <int DT, int SPU, int P, int CH, bool KAHAN>
+// DB: double-buffered loads (two chunks in flight per lane) or one chunk at a time
+// (fewer registers, more resident warps).  The arithmetic is the same either way.
+template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
     constexpr int RW = 32 / P;
     constexpr int SB = (DT == DT_F32) ? 32 : 16;   // bytes per sample
@@ -178,7 +181,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     const long long rowc = active ? row : a.R - 1;  // inactive lanes re-read a valid row
     const int S = a.M / (P * SPU);                  // load units per lane per window
     const char *rp = static_cast<const char *>(a.vis) + rowc * (long long)a.T * SB;
-    const bool lead = active && j == 0;
+    const bool lead = active && j == 0;     // writes the row's outputs
 
     float acc[8];
     float cnt = 0.f;
@@ -190,46 +193,62 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         for (int c = 0; c < 8; ++c) acc[c] = cp[c];
         cnt = cp[8];
     }
-    int pos = a.bin_pos0;
+    // Per-row cursors and counters, set up once per task so that the per-window
+    // bookkeeping is a handful of integer operations.
+    float *const st_row = a.stats + rowc * a.nwin;          // written by the lead lane
+    uint32_t *const fl_row = a.flags + rowc * a.Wpr;
+    const long long plane = a.stats_plane;
+    const int wpbin = a.K / a.M;                              // windows per averaging bin
+    int wib = a.bin_pos0 / a.M;                               // windows of the open bin seen
     int bin = 0;
+    const float lane_samples = (float)(S * SPU);
+    // flag words: mode 0 when M divides 32 (whole windows per word), 1 when 32 divides
+    // M (whole words per window), 2 otherwise (windows straddle words)
+    const int fmode = (32 % a.M == 0) ? 0 : ((a.M % 32 == 0) ? 1 : 2);
+    const uint32_t wmask = a.M >= 32 ? FULL : ((1u << a.M) - 1u);
+    const int words_per_window = a.M >> 5;
     uint32_t fword = 0;
+    int fbit = 0, fwi = 0;
     // L2 prefetch: lane 0 of each row keeps pf_groups groups of pf_windows windows
     // requested ahead of the window being loaded.
     const bool pf = a.pf_groups > 0 && lead;
     const unsigned wbytes = (unsigned)a.M * SB;
-    const char *row_base = static_cast<const char *>(a.vis) + row * (long long)a.T * SB;
     if (pf) {
         const int hi = min(a.nwin, (1 + a.pf_groups) * a.pf_windows);
-        if (hi > 1) prefetch_l2(row_base + wbytes, (unsigned)(hi - 1) * wbytes);
+        if (hi > 1) prefetch_l2(rp + wbytes, (unsigned)(hi - 1) * wbytes);
     }
+    int pf_next = a.pf_windows;
 
     const float2 eps2 = make_float2(a.eps, a.eps);
-    for (int w = 0; w < a.nwin; ++w) {
-        if (pf && w % a.pf_windows == 0 && w > 0) {
-            const int g0 = w + a.pf_groups * a.pf_windows;
-            const int g1 = min(a.nwin, g0 + a.pf_windows);
-            if (g0 < g1) prefetch_l2(row_base + (long long)g0 * wbytes, (unsigned)(g1 - g0) * wbytes);
-        }
-        WinAcc A;
-        const float2 zero2 = make_float2(0.f, 0.f);
-        A.s = A.c = A.q = A.u = A.v = zero2;
+    // The load units of a lane form one contiguous stream over the row: chunk q (CH
+    // units) starts at rp + j*UB + q*CHB.  Two register buffers let the loads of chunk
+    // q+1 be in flight while chunk q is consumed.
+    constexpr int CHB = CH * P * UB;
+    const int nch = S / CH;                       // chunks per window
+    const int Q = a.nwin * nch;                   // chunks per lane in this block
+    const char *cp_ = rp + j * UB;
+    WinAcc A;
+    const float2 zero2 = make_float2(0.f, 0.f);
+    A.s = A.c = A.q = A.u = A.v = zero2;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) A.a[c] = zero2;
-        const char *wp = rp + (long long)w * a.M * SB + j * UB;
-        for (int s0 = 0; s0 < S; s0 += CH) {
-            Unit<UB> u[CH];
+    for (int c = 0; c < 4; ++c) A.a[c] = zero2;
+    int w = 0, cw = 0;
+    Unit<UB> ua[CH], ub[DB ? CH : 1];
 #pragma unroll
-            for (int c = 0; c < CH; ++c) load_unit(wp + (s0 + c) * (P * UB), u[c]);
+    for (int c = 0; c < CH; ++c) load_unit(cp_ + c * (P * UB), ua[c]);
+
+    auto consume = [&](const Unit<UB>(&u)[CH]) {
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
+        for (int c = 0; c < CH; ++c) {
 #pragma unroll
-                for (int k = 0; k < SPU; ++k) {
-                    float2 x[4];
-                    decode<DT, UB>(u[c], k, x);
-                    accumulate<KAHAN>(A, x, eps2);
-                }
+            for (int k = 0; k < SPU; ++k) {
+                float2 x[4];
+                decode<DT, UB>(u[c], k, x);
+                accumulate<KAHAN>(A, x, eps2);
             }
         }
+    };
+    auto end_window = [&]() {
         if constexpr (KAHAN) A.s = sub2(A.s, A.c);
         // complete the window over the P lanes of the row
         const float S1 = allsum<P>(A.s.x), S2 = allsum<P>(A.s.y);
@@ -237,21 +256,33 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         const float qi = allsum<P>(A.q.y), ui = allsum<P>(A.u.y), vi = allsum<P>(A.v.y);
         // Table 1 groups 6-7 and Sec. 2.1: tau = c0 * (M S2 / (S1^2 + eps) - 1)
         const float s12 = S1 * S1;
-        const float tau = a.c0 * (a.fM * S2 / (s12 + a.eps) - 1.0f);
+        const float tau = a.c0 * (a.fM * S2 * rcp_approx(s12 + a.eps) - 1.0f);
         // Table 2 groups 5-6: r = sqrt(q^2 + u^2 + v^2) / M, per part
-        const float r_re = sqrtf(qr * qr + ur * ur + vr * vr) / a.fM;
-        const float r_im = sqrtf(qi * qi + ui * ui + vi * vi) / a.fM;
+        const float r_re = sqrt_approx(qr * qr + ur * ur + vr * vr) * a.invM;
+        const float r_im = sqrt_approx(qi * qi + ui * ui + vi * vi) * a.invM;
         // SK flag OR (DS Re OR DS Im); a NaN statistic fails its "inside" test
         const bool f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
                        !(r_im <= a.gamma);
         if (lead) {
-            float *sp = a.stats + row * a.nwin + w;
-            sp[0] = tau;
-            sp[a.stats_plane] = r_re;
-            sp[2 * a.stats_plane] = r_im;
+            st_row[w] = tau;
+            st_row[w + plane] = r_re;
+            st_row[w + 2 * plane] = r_im;
         }
-        // the flag covers every sample of the window: set bits [w*M, w*M + M)
-        {
+        // the flag covers every sample of the window: bits [w*M, w*M + M) of the row
+        if (fmode == 0) {
+            if (f) fword |= wmask << fbit;
+            fbit += a.M;
+            if (fbit == 32) {
+                if (lead) fl_row[fwi] = fword;
+                ++fwi;
+                fword = 0;
+                fbit = 0;
+            }
+        } else if (fmode == 1) {
+            if (lead)
+                for (int k = 0; k < words_per_window; ++k) fl_row[fwi + k] = f ? FULL : 0u;
+            fwi += words_per_window;
+        } else {
             int lo = w * a.M;
             const int hi = lo + a.M;
             while (lo < hi) {
@@ -260,7 +291,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
                 if (f) fword |= (nb == 32 ? FULL : ((1u << nb) - 1u)) << b0;
                 lo += nb;
                 if ((lo & 31) == 0) {
-                    if (lead) a.flags[row * a.Wpr + ((lo - 1) >> 5)] = fword;
+                    if (lead) fl_row[(lo - 1) >> 5] = fword;
                     fword = 0;
                 }
             }
@@ -272,34 +303,72 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
                 acc[2 * c] += A.a[c].x;
                 acc[2 * c + 1] += A.a[c].y;
             }
-            cnt += (float)(S * SPU);
+            cnt += lane_samples;
         }
-        pos += a.M;
-        if (pos == a.K) {
+        if (++wib == wpbin) {
             float tot[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
             const float n = allsum<P>(cnt);
             if (lead) {
                 float4 *ap = reinterpret_cast<float4 *>(a.avg + (row * a.n_out + bin) * 8);
-                float o[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) o[c] = n > 0.f ? tot[c] / n : 0.f;
-                ap[0] = make_float4(o[0], o[1], o[2], o[3]);
-                ap[1] = make_float4(o[4], o[5], o[6], o[7]);
-                a.weight[row * a.n_out + bin] = n / a.fK;
+                const float inv = n > 0.f ? __frcp_rn(n) : 0.f;
+                ap[0] = make_float4(tot[0] * inv, tot[1] * inv, tot[2] * inv, tot[3] * inv);
+                ap[1] = make_float4(tot[4] * inv, tot[5] * inv, tot[6] * inv, tot[7] * inv);
+                a.weight[row * a.n_out + bin] = __fdiv_rn(n, a.fK);
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = 0.f;
             cnt = 0.f;
-            pos = 0;
+            wib = 0;
             ++bin;
         }
+        A.s = A.c = A.q = A.u = A.v = zero2;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) A.a[c] = zero2;
+        ++w;
+        if (pf && w == pf_next) {
+            const int g0 = w + a.pf_groups * a.pf_windows;
+            const int g1 = min(a.nwin, g0 + a.pf_windows);
+            if (g0 < g1) prefetch_l2(rp + (long long)g0 * wbytes, (unsigned)(g1 - g0) * wbytes);
+            pf_next += a.pf_windows;
+        }
+    };
+
+    if constexpr (DB) {
+        for (int q = 0; q < Q; q += 2) {
+            if (q + 1 < Q) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    load_unit(cp_ + (long long)(q + 1) * CHB + c * (P * UB), ub[c]);
+            }
+            consume(ua);
+            if (++cw == nch) { cw = 0; end_window(); }
+            if (q + 1 >= Q) break;
+            if (q + 2 < Q) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    load_unit(cp_ + (long long)(q + 2) * CHB + c * (P * UB), ua[c]);
+            }
+            consume(ub);
+            if (++cw == nch) { cw = 0; end_window(); }
+        }
+    } else {
+        for (int q = 0; q < Q; ++q) {
+            if (q > 0) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    load_unit(cp_ + (long long)q * CHB + c * (P * UB), ua[c]);
+            }
+            consume(ua);
+            if (++cw == nch) { cw = 0; end_window(); }
+        }
     }
+    // a last, partly filled flag word (T not a multiple of 32)
     if (a.T & 31) {
-        if (lead) a.flags[row * a.Wpr + (a.T >> 5)] = fword;
+        if (lead) fl_row[a.T >> 5] = fword;
     }
-    if (pos != 0 && active) {
+    if (wib != 0 && active) {
         float *cp = a.carry + (row * P + j) * 9;
 #pragma unroll
         for (int c = 0; c < 8; ++c) cp[c] = acc[c];
@@ -308,11 +377,23 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
 }
 
 // ---- kernels ---------------------------------------------------------------------
-template <int DT, int SPU, int P, int CH, bool KAHAN>
-__global__ void __launch_bounds__(512, 1) k_block(const __grid_constant__ StreamArgs a) {
+// LB selects the register budget through the launch bounds: 0 -> at most 128
+// registers (blocks up to 512 threads), 1 -> 80 (256 threads, 3 blocks per SM),
+// 2 -> 64 (256 threads, 4 blocks per SM).  The arithmetic, hence every result, is the
+// same for all budgets; only residency changes.
+template <int LB> struct Bounds;
+template <> struct Bounds<0> { static constexpr int threads = 512, blocks = 1; };
+template <> struct Bounds<1> { static constexpr int threads = 256, blocks = 3; };
+template <> struct Bounds<2> { static constexpr int threads = 256, blocks = 4; };
+
+template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0>
+__global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
+    k_block(const __grid_constant__ StreamArgs a) {
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
-    process_group<DT, SPU, P, CH, KAHAN>(a, group);
+    // the 128-register budget keeps two chunks in flight; tighter budgets load one
+    // chunk at a time and rely on more resident warps instead
+    process_group<DT, SPU, P, CH, KAHAN, LB == 0>(a, group);
 }
 
 // Persistent batch: every warp takes (stream, row group) tasks from a device counter

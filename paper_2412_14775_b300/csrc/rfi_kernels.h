@@ -1,0 +1,46 @@
+// rfi_kernels.h -- the table of compiled kernel instances (internal).
+//
+// One entry per (input dtype, samples per load unit, lanes per row P, load units per
+// chunk CH in {1, 2, 4, 5} (two chunks are in flight per lane), Kahan on/off, register budget LB).  The instances live in two translation
+// units (complex64 and binary16) so that they compile in parallel.
+#pragma once
+
+namespace rfi {
+
+struct Instance {
+    int dt, spu, P, ch, kahan, lb;
+    const void *block_fn;   // k_block<...>
+    const void *batch_fn;   // k_batch<...>; the register budget does not change results,
+                            // so every budget shares the LB = 0 batch kernel
+};
+
+struct InstanceTable {
+    const Instance *items;
+    int n;
+};
+
+InstanceTable instances_f32();
+InstanceTable instances_f16();
+
+}  // namespace rfi
+
+// Entries for one (DT, SPU, P, CH, K): LB = 0 with its own batch kernel.
+#define RFI_INST0(DT, SPU, P, CH, K)                                                        \
+    {DT, SPU, P, CH, K, 0, (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0>,        \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K>}
+// A tighter register budget LB for the single-stream kernel.
+#define RFI_INSTB(DT, SPU, P, CH, LB)                                                       \
+    {DT, SPU, P, CH, 0, LB, (const void *)&rfi::k_block<DT, SPU, P, CH, false, LB>,        \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
+#define RFI_INST0_CH(DT, SPU, P, K)                                                         \
+    RFI_INST0(DT, SPU, P, 1, K), RFI_INST0(DT, SPU, P, 2, K), RFI_INST0(DT, SPU, P, 4, K),  \
+        RFI_INST0(DT, SPU, P, 5, K)
+#define RFI_INSTB_CH(DT, SPU, P, LB)                                                        \
+    RFI_INSTB(DT, SPU, P, 2, LB), RFI_INSTB(DT, SPU, P, 4, LB), RFI_INSTB(DT, SPU, P, 5, LB)
+#define RFI_INST0_P(DT, SPU, K)                                                             \
+    RFI_INST0_CH(DT, SPU, 1, K), RFI_INST0_CH(DT, SPU, 2, K), RFI_INST0_CH(DT, SPU, 4, K),  \
+        RFI_INST0_CH(DT, SPU, 8, K), RFI_INST0_CH(DT, SPU, 16, K),                         \
+        RFI_INST0_CH(DT, SPU, 32, K)
+#define RFI_INSTB_P(DT, SPU, LB)                                                            \
+    RFI_INSTB_CH(DT, SPU, 1, LB), RFI_INSTB_CH(DT, SPU, 2, LB), RFI_INSTB_CH(DT, SPU, 4, LB), \
+        RFI_INSTB_CH(DT, SPU, 8, LB)

@@ -65,7 +65,6 @@ typedef const void *KernelPtr;
 template <int DT, int SPU, bool K>
 KernelPtr pick_chunk(int ch) {
     switch (ch) {
-        case 8: return (KernelPtr)&k_block<DT, SPU, 1, 8, K>;
         case 5: return (KernelPtr)&k_block<DT, SPU, 1, 5, K>;
         case 4: return (KernelPtr)&k_block<DT, SPU, 1, 4, K>;
         case 2: return (KernelPtr)&k_block<DT, SPU, 1, 2, K>;
@@ -80,7 +79,7 @@ KernelPtr pick_kernel(int dt, int spu, int ch, bool kahan) {
 }
 
 int chunk_of(int S) {
-    static const int opts[] = {8, 5, 4, 2, 1};
+    static const int opts[] = {5, 4, 2, 1};
     for (int c : opts)
         if (S % c == 0) return c;
     return 1;
@@ -162,7 +161,7 @@ extern "C" int rfi_process_block_noalloc(int stations, int channels, int window_
     a.n_out = (int)n_out;
     a.bin_pos0 = (int)(n_seen % avg_K);
     a.pf_windows = std::max(1, 1024 / (window_M * sb));
-    a.pf_groups = 2;
+    a.pf_groups = 0;
     const double Md = window_M;
     a.c0 = (float)((Md * thr->d + 1.0) / (Md - 1.0));
     a.s_low = (float)thr->s_low;
@@ -171,6 +170,7 @@ extern "C" int rfi_process_block_noalloc(int stations, int channels, int window_
     a.eps = (float)thr->eps;
     a.fM = (float)window_M;
     a.fK = (float)avg_K;
+    a.invM = (float)(1.0 / window_M);
     const int S = window_M / spu;
     const bool kahan = window_M >= 64;
     KernelPtr fn = pick_kernel(dt, spu, chunk_of(S), kahan);

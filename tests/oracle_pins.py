@@ -330,3 +330,75 @@ def pin_p8_block_split(seed=9):
 ALL_PINS = [pin_p1_sk_null_gamma, pin_p1_sk_null_autocorrelation, pin_p2_sk_bounds,
             pin_p3_fully_polarised, pin_p4_isotropic_null, pin_p5_autocorrelation_r_im,
             pin_p6_averaging_bruteforce, pin_p7_exact_grid, pin_p8_block_split]
+
+
+def pin_p9_tf_footprints(seed=10):
+    """P9: time-frequency footprints (W = M x F samples over F adjacent channels).
+
+    (a) A footprint's statistics depend only on its W samples: they equal, bit for bit,
+        those of a time-only window holding the same samples row after row.
+    (b) P1 holds with W = M F: Gamma(d) magnitudes over a 8x2 footprint have E[tau] = 1
+        and the closed-form variance for W = 16.
+    (c) P4 holds with W = M F: isotropic noise over a 5x4 footprint has E[r^2] = 1/20.
+    (d) A window flagged by one channel flags every channel of the footprint, and each
+        channel's average leaves it out."""
+    rng = np.random.default_rng(seed)
+    # (a)
+    for M, F in ((10, 2), (5, 4), (3, 2)):
+        G, nw = 6, 4
+        v = rng.standard_normal((G * F, M * nw, 4)) + 1j * rng.standard_normal((G * F, M * nw, 4))
+        v[:, :M] *= 5.0
+        a = OracleStream(G * F, M, M, 1.0, 0.2, 2.5, 0.5, EPS32, F=F).process(v)
+        # rows of w hold, window by window, the F channels' samples one after another
+        w = np.stack([np.concatenate([np.concatenate([v[g * F + k, M * t:M * (t + 1)]
+                                                      for k in range(F)]) for t in range(nw)])
+                      for g in range(G)])
+        b = OracleStream(G, M * F, M * F, 1.0, 0.2, 2.5, 0.5, EPS32).process(w)
+        for key in ("tau", "r_re", "r_im", "wflag"):
+            assert np.array_equal(a[key], b[key]), (M, F, key)
+    # (b)
+    M, F, d, n = 8, 2, 1.5, 100000
+    g = rng.gamma(shape=d, size=(n * F, M))
+    vis = np.zeros((n * F, M, 4), np.complex128)
+    vis[..., 0] = g
+    out = OracleStream(n * F, M, M, d, -1e300, 1e300, 1e300, 0.0, F=F).process(vis)
+    _check_mean_var(out["tau"].ravel(), M * F, d)
+    # (c)
+    M, F, n = 5, 4, 50000
+    vis = (rng.standard_normal((n * F, M, 4)) + 1j * rng.standard_normal((n * F, M, 4))) / math.sqrt(2)
+    out = OracleStream(n * F, M, M, 1.0, -1e300, 1e300, 1e300, 0.0, F=F).process(vis)
+    for key in ("r_re", "r_im"):
+        r2 = out[key].ravel() ** 2
+        assert abs(r2.mean() - 1.0 / (M * F)) < 4 * r2.std() / math.sqrt(r2.size), key
+    # (d)
+    M, F, nb = 4, 2, 4
+    K = M * nb
+    subsets = list(itertools.product((0, 1), repeat=nb))
+    G = len(subsets)
+    vis = np.zeros((G * F, K, 4), np.complex128)
+    for gi, sub in enumerate(subsets):
+        for k in range(F):
+            row = vis[gi * F + k]
+            row[:, 1] = rng.standard_normal(K) + 1j * rng.standard_normal(K)
+            row[:, 0] = 2.0 * np.exp(1j * rng.uniform(0, 2 * np.pi, size=K))   # flat |I|
+        for w, fl in enumerate(sub):
+            if fl:   # a spike in one channel only: that footprint's |I| is no longer flat
+                vis[gi * F + 1, w * M + 1, 0] = 40.0
+    # a flat footprint has tau = 0; the spiked one has tau = lead * (W*1628/54**2 - 1) > 4
+    st = OracleStream(G * F, M, K, 1.0, -0.5, 2.0, 2.0, EPS32, F=F)
+    out = st.process(vis)
+    assert np.array_equal(out["wflag"], np.array(subsets, dtype=np.uint8))
+    for gi, sub in enumerate(subsets):
+        keep = np.repeat(1 - np.array(sub), M).astype(bool)
+        for k in range(F):
+            row = gi * F + k
+            bits = sum(1 << t for t in range(K) if not keep[t])
+            assert int(out["flagbits"][row, 0]) == bits, (sub, k)
+            exp = vis[row][keep].mean(axis=0) if keep.any() else np.zeros(4)
+            got = out["avg"][row, 0].reshape(4, 2)
+            assert np.allclose(got[:, 0], exp.real, rtol=1e-13, atol=1e-14)
+            assert np.allclose(got[:, 1], exp.imag, rtol=1e-13, atol=1e-14)
+            assert out["weight"][row, 0] == keep.sum() / K
+
+
+ALL_PINS.append(pin_p9_tf_footprints)

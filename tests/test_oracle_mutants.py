@@ -34,13 +34,19 @@ MUTANTS = {
     # flag rule
     "sk_and_ds": ("return f_sk | (f_re | f_im);", "return f_sk & (f_re | f_im);"),
     "im_part_ignored": ("return f_sk | (f_re | f_im);", "return f_sk | f_re;"),
-    "flag_bit_shifted": ("(uint32_t)1u << (ts % 32)", "(uint32_t)1u << ((ts + 1) % 32)"),
+    "flag_bit_shifted": ("fb[ts / 32] |= (uint32_t)1u << (ts % 32)",
+                         "fb[ts / 32] |= (uint32_t)1u << ((ts + 1) % 32)"),
     # averaging and carry
     "avg_divides_by_K": ("acc_val(&bin[c]) / bin_n", "acc_val(&bin[c]) / (double)K"),
+    # T x F footprints
+    "tf_sk_first_channel_only": ("oracle_sk_window(stokes, W, d", "oracle_sk_window(stokes, Mt, d"),
+    "tf_ds_im_first_channel_only": ("oracle_ds_window(stokes, W, 1,", "oracle_ds_window(stokes, Mt, 1,"),
+    "tf_flag_first_channel_only": ("if (f) fb[ts / 32] |= (uint32_t)1u << (ts % 32);",
+                                   "if (f && k == 0) fb[ts / 32] |= (uint32_t)1u << (ts % 32);"),
     "weight_counts_windows": ("weight[(size_t)row * n_out + b] = bin_n / (double)K;",
                               "weight[(size_t)row * n_out + b] = bin_n / (double)W / (double)K;"),
-    "flagged_samples_averaged": ("if (!f) {\n                for (int i = 0; i < W; ++i)",
-                                 "if (1) {\n                for (int i = 0; i < W; ++i)"),
+    "flagged_samples_averaged": ("if (!f) {\n                    for (int i = 0; i < Mt; ++i)",
+                                 "if (1) {\n                    for (int i = 0; i < Mt; ++i)"),
     "carry_dropped": ("bin[c].s = carry_sum[(size_t)row * 8 + c]; bin[c].c = 0;",
                       "bin[c].s = 0; bin[c].c = 0;"),
 }

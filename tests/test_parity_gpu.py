@@ -99,6 +99,9 @@ SHAPES = [
     ("f16", 6, 3, 20, 60, [60, 40, 20], {"lanes_per_row": 2}),
     ("f16", 4, 6, 32, 64, [96, 32], {"lanes_per_row": 16}),
     ("f16", 7, 5, 16, 32, [48], {"lanes_per_row": 1, "compensated": 1}),
+    ("f32", 5, 6, 16, 32, [64, 32], {"lanes_per_row": 4, "max_registers": 64}),
+    ("f16", 5, 6, 20, 40, [40, 80], {"lanes_per_row": 2, "max_registers": 80}),
+    ("f16", 4, 5, 5, 10, [10, 20], {"max_registers": 64}),
 ]
 
 
@@ -151,13 +154,14 @@ def test_block_split_bit_identical():
         st.close()
 
 
-def _batch_setup(dtype, geoms, M, K, T, seed=9):
+def _batch_setup(dtype, geoms, M, K, T, seed=9, regs=None):
     thr = default_thresholds(M)
     streams, vis, datas = [], [], []
     for i, (N, C) in enumerate(geoms):
         d = synth.tiny_block(seed=seed + i, stations=N, channels=C, T=T, duty=0.06)["vis"]
         datas.append(d)
-        streams.append(RfiStream(N, C, M, K, thr, dtype))
+        opts = {"max_registers": regs[i]} if regs else {}
+        streams.append(RfiStream(N, C, M, K, thr, dtype, **opts))
         vis.append(to_device_rows(d, dtype))
     return thr, streams, vis, datas
 
@@ -171,8 +175,10 @@ def test_batch_matches_solo_bit_identical():
     M, K, T = 16, 64, 128
     geoms = [(5, 3), (9, 7), (3, 2), (12, 5)]
     for dtype in ("f32", "f16"):
-        thr, bs, vis, _ = _batch_setup(dtype, geoms, M, K, T)
-        _, ss, _, _ = _batch_setup(dtype, geoms, M, K, T)
+        # the batch mixes register budgets; the solo runs use other budgets again:
+        # the budget changes residency only, never a result
+        thr, bs, vis, _ = _batch_setup(dtype, geoms, M, K, T, regs=[0, 64, 80, 0])
+        _, ss, _, _ = _batch_setup(dtype, geoms, M, K, T, regs=[64, 0, 0, 80])
         for step in range(2):
             outs = _alloc(bs, T)
             binding.rfi_process_batch([s.ctx for s in bs], vis, [T] * len(bs),
