@@ -205,6 +205,38 @@ def cpu_baseline(seconds_target=10.0):
                       f"{dt:.1f} s single-threaded"}
 
 
+def footprint_extras(torch, cs, peak, steps=500, warmup=10):
+    """The paper's time-frequency windows (10 x 2 and 5 x 4, W = 20) on the 62-station,
+    64-channel geometry with blocks of T = 250 samples (a multiple of both time
+    extents), averaging 250 -> 1, complex64 and binary16."""
+    import synth
+    from paper_2412_14775_b300 import RfiStream, autotune, default_thresholds
+    T, K = 250, 250
+    R = 1953 * 64
+    res = {}
+    v32 = synth.generate.device_block(62, 64, T, seed=400, dtype="f32")
+    for dtype in ("f32", "f16"):
+        vis = v32 if dtype == "f32" else v32.half()
+        sb = 32 if dtype == "f32" else 16
+        for M, F in ((10, 2), (5, 4)):
+            thr = default_thresholds(M * F)
+            best, _ = autotune.tune(62, 64, M, K, thr, dtype, vis, fixed={"window_F": F})
+            opts = autotune.options_of(best)
+            st = RfiStream(62, 64, M, K, thr, dtype, **opts)
+            out = st.alloc_outputs(T)
+            tot, per, _ = time_kernel(st, vis, out, steps, warmup, torch, cs)
+            k = statistics.mean(per)
+            nbytes = R * (T * sb + 4 * math.ceil(T / 32) + 12 * (T // M) // F + 36)
+            res[f"{dtype}_{M}x{F}"] = {"kernel_us": k * 1e6, "samples_per_s": R * T / k,
+                                       "achieved_gbs": nbytes / k / 1e9,
+                                       "frac": nbytes / k / 1e9 / peak, "options": opts}
+            st.close()
+        del vis
+    del v32
+    torch.cuda.empty_cache()
+    return res
+
+
 def batched_extras(options, torch, steps=300, warmup=10):
     """8 uneven binary16 subbands (stations 24..76, channels 16..128, T = 256) in one
     persistent launch replayed from a CUDA graph, against the same 8 streams launched
@@ -269,10 +301,13 @@ def serving_extras(seconds, options, torch):
     res["mix32"] = dict(loop.run(seconds, seed=11), hbm_budget_gb=budget / 1e9, streams=32)
     loop.close()
     torch.cuda.empty_cache()
+    # one 62-station, 64-channel stream delivering a block every 1/50 of a block time
     one = [dict(stations=62, channels=64, rho=50.0)]
     loop = ServingLoop(one, M=16, K=256, T=256, dtype="f16", options=options,
                        hbm_budget_bytes=budget, max_batch=1, cuda_streams=2)
-    r = loop.run(max(2.0, seconds / 2), seed=12)
+    dur = max(2.0, seconds / 2)
+    period = BLOCK_SECONDS / 50.0
+    r = loop.run(dur, arrivals=[(k * period, 0, k) for k in range(int(dur / period))])
     R = 1953 * 64
     r["real_time_factor"] = r["samples_per_s"] / (R * 256 / BLOCK_SECONDS)
     res["lofar_50x"] = r
@@ -413,6 +448,7 @@ def main():
         del vis16
         torch.cuda.empty_cache()
         extras["batched"] = batched_extras(fp16["M16"]["options"], torch)
+        extras["footprints"] = footprint_extras(torch, cs, peak)
         if args.serve_seconds > 0:
             extras["serving"] = serving_extras(args.serve_seconds,
                                                fp16["M16"]["options"], torch)
@@ -431,9 +467,22 @@ def main():
             _ = float(hout["weight"][0, 0])        # the result is read on the host
         dt = time.perf_counter() - t0
         d2h = sum(x.numel() * x.element_size() for x in hout.values())
+        # the host link alone: a plain pinned -> device copy of the same bytes
+        dst = torch.empty_like(hin, device=dev)
+        for _ in range(2):
+            dst.copy_(hin, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(5):
+            dst.copy_(hin, non_blocking=True)
+        torch.cuda.synchronize()
+        link = 5 * hin.numel() * hin.element_size() / (time.perf_counter() - t1) / 1e9
+        del dst
         e2e = {"value": samples * args.e2e_steps / dt, "unit": "samples/s",
                "h2d_bytes_per_step": hin.numel() * hin.element_size(),
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h,
+               "h2d_link_gbs_plain_copy": link,
+               "h2d_gbs_in_e2e": hin.numel() * hin.element_size() * args.e2e_steps / dt / 1e9}
         hst.close()
 
     cpu = None

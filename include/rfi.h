@@ -96,6 +96,12 @@ typedef enum {
  *   max_registers  register budget per thread of the single-stream kernel: 0 or 128
  *                  (default), 80 or 64 (more resident warps; at most 8 warps per
  *                  block; lanes_per_row <= 8).  Results do not depend on it.
+ *   window_F       channels per window footprint (0 = 1): a window is M consecutive
+ *                  samples of F adjacent channels of one baseline, W = M F samples
+ *                  (the time-frequency windows of Sections 3.2 and 4).  A power of two
+ *                  dividing `channels`, with lanes_per_row * window_F <= 32.  The
+ *                  statistics then have shape [3][B][C/F][T/M]; every channel of a
+ *                  flagged footprint is flagged; averages stay per channel.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -108,6 +114,7 @@ typedef struct {
     int prefetch_bytes;
     int prefetch_groups;
     int max_registers;
+    int window_F;
 } rfi_options;
 
 /* Create a context for one stream of `stations` stations (B = N(N+1)/2 baselines)
@@ -142,7 +149,8 @@ int rfi_set_thresholds(rfi_ctx *ctx, const rfi_thresholds *thr);
  *          averaging bin that completes in this call (n_out = rfi_outputs_for);
  *          0 where every sample of the bin was flagged.  16-byte aligned.
  *   weight [R][n_out] float32: unflagged samples of the bin / K.
- *   stats  [3][R][T/M] float32: tau, r_Re, r_Im of every window (SoA).
+ *   stats  [3][R/F][T/M] float32: tau, r_Re, r_Im of every window (SoA; F = 1
+ *          unless the context has a T x F footprint).
  * avg and weight may be NULL only when n_out == 0.  Asynchronous on `stream`. */
 int rfi_process_block(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags, float *avg,
                       float *weight, float *stats, void *stream);

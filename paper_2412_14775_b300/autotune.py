@@ -52,11 +52,15 @@ def time_options(stations, channels, M, K, thr, dtype, vis, reps=30, warmup=5, *
         st.close()
 
 
-def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, verbose=False):
+def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, verbose=False,
+         fixed=None):
     """Return (best_options, table) for this workload; coordinate search over the
-    launch shape, then the prefetch distance and size."""
+    launch shape, then the prefetch distance and size.  `fixed` options (for example
+    window_F) are part of every candidate."""
+    fixed = dict(fixed or {})
     T = vis.shape[-3]
-    key = _key(stations, channels, M, K, T, dtype)
+    key = _key(stations, channels, M, K, T, dtype) + "".join(
+        f":{k}={v}" for k, v in sorted(fixed.items()))
     if key in _MEM:
         return _MEM[key], []
     if cache_path and os.path.exists(cache_path):
@@ -68,7 +72,7 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
     table = []
 
     def run(o):
-        t = time_options(stations, channels, M, K, thr, dtype, vis, reps=reps, **o)
+        t = time_options(stations, channels, M, K, thr, dtype, vis, reps=reps, **o, **fixed)
         table.append((dict(o), t))
         if verbose:
             print(f"  {o} {t * 1e6:.1f} us")
@@ -77,7 +81,8 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
     # stage 1: launch shape without prefetch; stage 2: prefetch for the three best
     shapes = [(4, 0), (8, 0), (16, 0), (4, 80), (8, 80), (4, 64), (8, 64)]
     stage1 = []
-    for P in candidates_p(M, dtype):
+    F = fixed.get("window_F", 1)
+    for P in [p for p in candidates_p(M, dtype) if p * F <= 32]:
         for wpb, regs in shapes:
             o = dict(lanes_per_row=P, warps_per_block=wpb, max_registers=regs,
                      prefetch_groups=0, prefetch_bytes=1024)
@@ -94,7 +99,7 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
                 t = run(o)
                 if t < best_t:
                     best, best_t = o, t
-    best = dict(best, seconds=best_t)
+    best = dict(best, seconds=best_t, **fixed)
     _MEM[key] = best
     if cache_path:
         disk = {}

@@ -92,6 +92,7 @@ struct rfi_ctx {
     rfi_dtype dtype;
     rfi_thresholds thr;
     int P, spu, S, ch, kahan, wpb, lb;
+    int F;                              // channels per window footprint
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     const Instance *inst;
     long long n_seen;
@@ -185,6 +186,8 @@ int choose_shape(rfi_ctx *c, int P_req) {
         P = 2;
         while (P > 1 && (c->M % (P * spu)) != 0) P >>= 1;
     }
+    if (P * c->F > 32)
+        return fail(RFI_EINVAL, "lanes_per_row (%d) x window_F (%d) must not exceed 32", P, c->F);
     if (P != 1 && P != 2 && P != 4 && P != 8 && P != 16 && P != 32)
         return fail(RFI_EINVAL, "lanes_per_row must be a power of two <= 32");
     if (c->M % (P * spu) != 0) {
@@ -218,10 +221,11 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.flags = flags + r0 * Wpr;
     a.avg = avg ? avg + r0 * n_out * 8 : nullptr;
     a.weight = weight ? weight + r0 * n_out : nullptr;
-    a.stats = stats + r0 * nwin;
+    a.stats = stats + (r0 / c->F) * nwin;     // r0 is a multiple of F
     a.carry = c->carry + r0 * c->P * 9;
     a.R = nrows;
-    a.stats_plane = c->R * nwin;
+    a.stats_plane = (c->R / c->F) * nwin;
+    a.F = c->F;
     a.T = T;
     a.M = c->M;
     a.K = c->K;
@@ -229,15 +233,15 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.nwin = nwin;
     a.n_out = (int)n_out;
     a.bin_pos0 = (int)(c->n_seen % c->K);
-    const double Md = c->M;
+    const double Md = (double)c->M * c->F;     // W = M F samples per window
     a.c0 = (float)((Md * c->thr.d + 1.0) / (Md - 1.0));
     a.s_low = (float)c->thr.s_low;
     a.s_high = (float)c->thr.s_high;
     a.gamma = (float)c->thr.gamma;
     a.eps = (float)c->thr.eps;
-    a.fM = (float)c->M;
+    a.fM = (float)Md;
     a.fK = (float)c->K;
-    a.invM = (float)(1.0 / c->M);
+    a.invM = (float)(1.0 / Md);
     const int wbytes = c->M * sample_bytes(c->dtype);
     a.pf_windows = std::max(1, c->pf_bytes / wbytes);
     a.pf_groups = c->pf_groups;
@@ -262,7 +266,7 @@ int check_block_args(const rfi_ctx *c, const void *vis, int T, const uint32_t *f
     int rc;
     if ((rc = check_dev(vis, R * T * sb, vis_align, c->device, "vis"))) return rc;
     if ((rc = check_dev(flags, R * wpr * 4, 4, c->device, "flags"))) return rc;
-    if ((rc = check_dev(stats, 3 * R * nw * 4, 4, c->device, "stats"))) return rc;
+    if ((rc = check_dev(stats, 3 * (R / c->F) * nw * 4, 4, c->device, "stats"))) return rc;
     if (n_out > 0) {
         if ((rc = check_dev(avg, R * n_out * 32, 16, c->device, "avg"))) return rc;
         if ((rc = check_dev(weight, R * n_out * 4, 4, c->device, "weight"))) return rc;
@@ -400,19 +404,20 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     if (!out) return fail(RFI_EINVAL, "null output handle");
     *out = nullptr;
     if (stations < 1 || channels < 1) return fail(RFI_EINVAL, "stations and channels must be >= 1");
-    if (window_M < 2) return fail(RFI_EINVAL, "window M must be >= 2 (tau divides by M-1)");
+    if (window_M < 1 || (window_M < 2 && !(opt && opt->window_F > 1)))
+        return fail(RFI_EINVAL, "a window needs at least 2 samples (tau divides by W-1)");
     if (avg_K < window_M || avg_K % window_M != 0)
         return fail(RFI_EINVAL, "averaging factor K=%d must be a positive multiple of M=%d", avg_K,
                     window_M);
     if (dtype != RFI_C64 && dtype != RFI_C32H) return fail(RFI_EINVAL, "unknown dtype");
     int rc;
     if ((rc = check_thresholds(thr))) return rc;
-    rfi_options o = {0, 0, 0, 0, 0, 0, 0, 0};
+    rfi_options o = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (opt) o = *opt;
     if (o.warps_per_block < 0 || o.warps_per_block > 16 || o.host_max_T < 0 || o.host_chunks < 0 ||
         o.compensated < -1 || o.compensated > 1 || o.prefetch_bytes < 0 ||
         o.prefetch_bytes % 16 != 0 || o.prefetch_groups > 64 ||
-        (o.max_registers != 0 && o.max_registers < 64))
+        (o.max_registers != 0 && o.max_registers < 64) || o.window_F < 0)
         return fail(RFI_EINVAL, "bad options");
 
     rfi_ctx *c = new (std::nothrow) rfi_ctx();
@@ -436,6 +441,12 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->kahan = o.compensated == 1 || (o.compensated == 0 && window_M >= 64);
     c->wpb = o.warps_per_block ? o.warps_per_block : 8;
     c->lb = o.max_registers == 0 || o.max_registers >= 128 ? 0 : (o.max_registers >= 80 ? 1 : 2);
+    c->F = o.window_F ? o.window_F : 1;
+    if (c->F & (c->F - 1) || c->F > 32 || channels % c->F != 0 || c->M * c->F < 2) {
+        delete c;
+        return fail(RFI_EINVAL, "window_F must be a power of two <= 32 dividing channels=%d",
+                    channels);
+    }
     if (c->lb > 0 && c->wpb > 8) {
         delete c;
         return fail(RFI_EINVAL, "max_registers below 128 allows at most 8 warps per block");
@@ -532,6 +543,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->prefetch_bytes = ctx->pf_bytes;
     opt->prefetch_groups = ctx->pf_groups;
     opt->max_registers = ctx->lb == 0 ? 128 : (ctx->lb == 1 ? 80 : 64);
+    opt->window_F = ctx->F;
     return RFI_OK;
 }
 
@@ -574,7 +586,9 @@ int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags
         (e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_start, 0)) != cudaSuccess)
         return set_cuda_error(ctx, e, "host path setup");
     for (int k = 0; k < nch; ++k) {
-        const long long r0 = R * k / nch, r1 = R * (k + 1) / nch, nr = r1 - r0;
+        const long long F = ctx->F;
+        const long long r0 = (R / F) * k / nch * F, r1 = (R / F) * (k + 1) / nch * F;
+        const long long nr = r1 - r0;
         if (nr <= 0) continue;
         e = cudaMemcpyAsync(ctx->h_vis + r0 * T * sb, static_cast<const char *>(vis) + r0 * T * sb,
                             nr * T * sb, cudaMemcpyHostToDevice, ctx->s_in);
@@ -590,9 +604,9 @@ int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags
             e = cudaMemcpyAsync(flags + r0 * wpr, ctx->h_flags + r0 * wpr, nr * wpr * 4,
                                 cudaMemcpyDeviceToHost, ctx->s_out);
         if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(stats + r0 * nwin, (size_t)R * nwin * 4,
-                                  ctx->h_stats + r0 * nwin, (size_t)R * nwin * 4, nr * nwin * 4, 3,
-                                  cudaMemcpyDeviceToHost, ctx->s_out);
+            e = cudaMemcpy2DAsync(stats + (r0 / F) * nwin, (size_t)(R / F) * nwin * 4,
+                                  ctx->h_stats + (r0 / F) * nwin, (size_t)(R / F) * nwin * 4,
+                                  (nr / F) * nwin * 4, 3, cudaMemcpyDeviceToHost, ctx->s_out);
         if (e == cudaSuccess && n_out > 0)
             e = cudaMemcpyAsync(avg + r0 * n_out * 8, ctx->h_avg + r0 * n_out * 8,
                                 nr * n_out * 32, cudaMemcpyDeviceToHost, ctx->s_out);

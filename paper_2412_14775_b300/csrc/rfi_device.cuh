@@ -40,11 +40,14 @@ struct StreamArgs {
     long long stats_plane;  // floats between the tau, r_Re and r_Im planes
     int T, M, K, Wpr, nwin, n_out;
     int bin_pos0;           // samples of the open bin consumed before this block
+    int F;                  // adjacent rows (channels) per window footprint (power of 2)
     int pf_windows;         // windows per L2 prefetch group (>= 1)
     int pf_groups;          // prefetch distance in groups (0 = no prefetch)
-    float c0;               // (M d + 1)/(M - 1), Table 1 group 5
-    float s_low, s_high, gamma, eps, fM, fK;
-    float invM;             // 1/M (exact when M is a power of two)
+    float c0;               // (W d + 1)/(W - 1), W = M F, Table 1 group 5
+    float s_low, s_high, gamma, eps;
+    float fM;               // W = M F as float (samples in one window)
+    float fK;
+    float invM;             // 1/W (exact when W is a power of two)
 };
 
 struct BatchArgs {
@@ -164,6 +167,16 @@ __device__ __forceinline__ float allsum(float v) {
     return v;
 }
 
+// Continue an allsum<P> over the F adjacent rows of a footprint (their lanes form one
+// aligned block of P*F lanes); PF = P * F is warp-uniform.
+template <int P>
+__device__ __forceinline__ float rowsum(float v, int PF) {
+#pragma unroll
+    for (int o = P; o < 32; o <<= 1)
+        if (o < PF) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
 // ---- one row group of one stream ---------------------------------------------
 // DT: input dtype; SPU: samples per load unit (1 or 2); P: lanes per row;
 // CH: load units issued together per lane; KAHAN: compensated S1, S2.
@@ -195,7 +208,10 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     }
     // Per-row cursors and counters, set up once per task so that the per-window
     // bookkeeping is a handful of integer operations.
-    float *const st_row = a.stats + rowc * a.nwin;          // written by the lead lane
+    // statistics are per footprint (F rows); the first row's lead lane writes them
+    float *const st_row = a.stats + (rowc / a.F) * a.nwin;
+    const bool st_lead = lead && (row % a.F) == 0;
+    const int PF = P * a.F;
     uint32_t *const fl_row = a.flags + rowc * a.Wpr;
     const long long plane = a.stats_plane;
     const int wpbin = a.K / a.M;                              // windows per averaging bin
@@ -250,20 +266,25 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     };
     auto end_window = [&]() {
         if constexpr (KAHAN) A.s = sub2(A.s, A.c);
-        // complete the window over the P lanes of the row
-        const float S1 = allsum<P>(A.s.x), S2 = allsum<P>(A.s.y);
-        const float qr = allsum<P>(A.q.x), ur = allsum<P>(A.u.x), vr = allsum<P>(A.v.x);
-        const float qi = allsum<P>(A.q.y), ui = allsum<P>(A.u.y), vi = allsum<P>(A.v.y);
-        // Table 1 groups 6-7 and Sec. 2.1: tau = c0 * (M S2 / (S1^2 + eps) - 1)
+        // complete the window over the P lanes of the row (and the F rows of a footprint)
+        float S1 = allsum<P>(A.s.x), S2 = allsum<P>(A.s.y);
+        float qr = allsum<P>(A.q.x), ur = allsum<P>(A.u.x), vr = allsum<P>(A.v.x);
+        float qi = allsum<P>(A.q.y), ui = allsum<P>(A.u.y), vi = allsum<P>(A.v.y);
+        if (PF > P) {
+            S1 = rowsum<P>(S1, PF); S2 = rowsum<P>(S2, PF);
+            qr = rowsum<P>(qr, PF); ur = rowsum<P>(ur, PF); vr = rowsum<P>(vr, PF);
+            qi = rowsum<P>(qi, PF); ui = rowsum<P>(ui, PF); vi = rowsum<P>(vi, PF);
+        }
+        // Table 1 groups 6-7 and Sec. 2.1: tau = c0 * (W S2 / (S1^2 + eps) - 1)
         const float s12 = S1 * S1;
         const float tau = a.c0 * (a.fM * S2 * rcp_approx(s12 + a.eps) - 1.0f);
-        // Table 2 groups 5-6: r = sqrt(q^2 + u^2 + v^2) / M, per part
+        // Table 2 groups 5-6: r = sqrt(q^2 + u^2 + v^2) / W, per part
         const float r_re = sqrt_approx(qr * qr + ur * ur + vr * vr) * a.invM;
         const float r_im = sqrt_approx(qi * qi + ui * ui + vi * vi) * a.invM;
         // SK flag OR (DS Re OR DS Im); a NaN statistic fails its "inside" test
         const bool f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
                        !(r_im <= a.gamma);
-        if (lead) {
+        if (st_lead) {
             st_row[w] = tau;
             st_row[w + plane] = r_re;
             st_row[w + 2 * plane] = r_im;

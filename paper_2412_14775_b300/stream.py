@@ -16,6 +16,7 @@ class RfiStream:
         self.ctx = B.rfi_create_ex(stations, channels, M, K, thresholds, self.dtype, **options)
         self.R = B.rfi_rows(self.ctx)
         self.options = B.rfi_get_options(self.ctx)
+        self.F = self.options["window_F"]
 
     # -- outputs ------------------------------------------------------------------
     def outputs_for(self, T):
@@ -29,7 +30,7 @@ class RfiStream:
             flags=torch.empty((self.R, (T + 31) // 32), dtype=torch.int32, **kw),
             avg=torch.empty((self.R, n_out, 4, 2), dtype=torch.float32, **kw),
             weight=torch.empty((self.R, n_out), dtype=torch.float32, **kw),
-            stats=torch.empty((3, self.R, T // self.M), dtype=torch.float32, **kw))
+            stats=torch.empty((3, self.R // self.F, T // self.M), dtype=torch.float32, **kw))
 
     def _T(self, vis):
         if vis.shape[-2:] != (4, 2):

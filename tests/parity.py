@@ -79,22 +79,26 @@ def rel_err(x, ref, floor):
 
 
 def compare(gpu, orc, thr, M, K, n_seen=0, stat_rtol=STAT_RTOL, avg_rtol=AVG_RTOL,
-            check_flags=True):
-    """Assert parity; return a dict of the observed worst errors and counts."""
+            check_flags=True, F=1):
+    """Assert parity; return a dict of the observed worst errors and counts.
+
+    With a T x F footprint (F > 1) the statistics are per footprint [R/F, T/M] while
+    flags and averages are per row; W = M F is the window size."""
     T = gpu["tau"].shape[1] * M
+    W = M * F
     rep = {}
-    for key, floor in (("tau", 1.0), ("r_re", M ** -0.5), ("r_im", M ** -0.5)):
+    for key, floor in (("tau", 1.0), ("r_re", W ** -0.5), ("r_im", W ** -0.5)):
         both_nan = np.isnan(gpu[key]) & np.isnan(orc[key])
         e = np.where(both_nan, 0.0, rel_err(gpu[key], orc[key], floor))
         rep[key] = float(np.nanmax(e)) if e.size else 0.0
         if stat_rtol is not None:
             assert not np.isnan(e).any(), f"{key}: NaN on one side only"
             assert rep[key] <= stat_rtol, f"{key}: worst relative error {rep[key]:.3g}"
-    wflag = expand_window_flags(gpu["flagbits"], M, T)
-    self_rule = flag_rule_f32(gpu["tau"], gpu["r_re"], gpu["r_im"], thr)
+    wflag = expand_window_flags(gpu["flagbits"], M, T)                 # per row
+    self_rule = np.repeat(flag_rule_f32(gpu["tau"], gpu["r_re"], gpu["r_im"], thr), F, axis=0)
     assert np.array_equal(wflag, self_rule), "packed flags disagree with the GPU's own statistics"
-    exempt = near_threshold(orc, thr, M)
-    diff = wflag != orc["wflag"].astype(bool)
+    exempt = np.repeat(near_threshold(orc, thr, W), F, axis=0)
+    diff = wflag != np.repeat(orc["wflag"].astype(bool), F, axis=0)
     rep["flag_disagree"] = int(diff.sum())
     rep["flag_disagree_frac"] = float(diff.mean()) if diff.size else 0.0
     rep["exempt"] = int(exempt.sum())

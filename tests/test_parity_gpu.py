@@ -25,12 +25,13 @@ def _oracle_input(vis_np, dtype):
 def _check_stream(stations, channels, M, K, Ts, dtype, thr=None, seed=3, **opts):
     """Run blocks of lengths Ts through one context and one oracle stream; compare
     every block."""
-    thr = thr or default_thresholds(M)
+    F = opts.get("window_F", 1)
+    thr = thr or default_thresholds(M * F)
     data = synth.tiny_block(seed=seed, stations=stations, channels=channels, T=sum(Ts),
                             duty=0.08)["vis"]
     R = data.shape[0] * data.shape[1]
     st = RfiStream(stations, channels, M, K, thr, dtype, **opts)
-    orc = oracle.OracleStream(R, M, K, **thr)
+    orc = oracle.OracleStream(R, M, K, **thr, F=F)
     t0 = 0
     reps = []
     for T in Ts:
@@ -38,7 +39,7 @@ def _check_stream(stations, channels, M, K, Ts, dtype, thr=None, seed=3, **opts)
         n_seen = orc.n_seen
         g = run_gpu(st, to_device_rows(blk, dtype))
         o = orc.process(_oracle_input(blk, dtype))
-        reps.append(compare(g, o, thr, M, K, n_seen=n_seen))
+        reps.append(compare(g, o, thr, M, K, n_seen=n_seen, F=F))
         t0 += T
     st.close()
     return reps
@@ -102,6 +103,14 @@ SHAPES = [
     ("f32", 5, 6, 16, 32, [64, 32], {"lanes_per_row": 4, "max_registers": 64}),
     ("f16", 5, 6, 20, 40, [40, 80], {"lanes_per_row": 2, "max_registers": 80}),
     ("f16", 4, 5, 5, 10, [10, 20], {"max_registers": 64}),
+    # time-frequency footprints: the paper's 10 x 2 and 5 x 4 windows (W = 20)
+    ("f32", 5, 4, 10, 20, [20, 40, 60], {"window_F": 2}),
+    ("f16", 5, 4, 10, 30, [40, 20, 60], {"window_F": 2}),
+    ("f32", 4, 8, 5, 10, [10, 20, 40], {"window_F": 4}),
+    ("f16", 4, 8, 5, 20, [20, 40], {"window_F": 4}),
+    ("f32", 3, 16, 16, 32, [48, 16], {"window_F": 8, "lanes_per_row": 4}),
+    ("f16", 3, 16, 8, 16, [32, 32], {"window_F": 16, "lanes_per_row": 2}),
+    ("f32", 3, 4, 1, 4, [8, 4], {"window_F": 4}),
 ]
 
 
@@ -213,6 +222,37 @@ def test_batch_graph_replay_matches_solo():
                     assert torch.equal(solo[k], o[k]), (step, k)
     finally:
         binding.rfi_batch_graph_destroy(g)
+
+
+def test_footprints_in_batch_and_host_path():
+    """Streams with 10 x 2 footprints next to time-only streams in one persistent
+    launch, and the chunked host path with a footprint: identical to the device path."""
+    M, K, T = 10, 20, 40
+    thr = default_thresholds(M * 2)
+    geoms = [(4, 6, 2), (5, 4, 1), (3, 8, 2)]
+    datas = [synth.tiny_block(seed=40 + i, stations=n, channels=c, T=T)["vis"]
+             for i, (n, c, _) in enumerate(geoms)]
+    mk = lambda: [RfiStream(n, c, M, K, thr, "f32", window_F=f) for n, c, f in geoms]
+    bs, ss = mk(), mk()
+    vis = [to_device_rows(d, "f32") for d in datas]
+    outs = [s.alloc_outputs(T) for s in bs]
+    binding.rfi_process_batch([s.ctx for s in bs], vis, [T] * 3, [o["flags"] for o in outs],
+                              [o["avg"] for o in outs], [o["weight"] for o in outs],
+                              [o["stats"] for o in outs])
+    torch.cuda.synchronize()
+    for s, v, o in zip(ss, vis, outs):
+        solo = s.process(v)
+        torch.cuda.synchronize()
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(solo[k], o[k]), k
+    n, c, f = geoms[0]
+    host = RfiStream(n, c, M, K, thr, "f32", window_F=f, host_max_T=T, host_chunks=3)
+    dev = RfiStream(n, c, M, K, thr, "f32", window_F=f)
+    want = dev.process(vis[0])
+    torch.cuda.synchronize()
+    got = host.process_host(torch.from_numpy(datas[0].reshape(-1, T, 4, 2).copy()).pin_memory())
+    for k in ("flags", "avg", "weight", "stats"):
+        assert torch.equal(want[k].cpu(), got[k]), k
 
 
 def test_host_path_matches_device_path():
