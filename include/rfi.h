@@ -102,6 +102,12 @@ typedef enum {
  *                  dividing `channels`, with lanes_per_row * window_F <= 32.  The
  *                  statistics then have shape [3][B][C/F][T/M]; every channel of a
  *                  flagged footprint is flagged; averages stay per channel.
+ *   precision      0 = float32 arithmetic (default).  1 = the mixed precision the
+ *                  paper's reinforcement-learning agent chose (Tables 3 and 4): SK
+ *                  groups 5 and 7 and DS groups 4-7 in IEEE binary16, the rest in
+ *                  binary32, every operation rounded in the tables' order, eps =
+ *                  2^-10 inside binary16 groups; one lane per row, time-only windows,
+ *                  no Kahan.  Statistics are then binary16 values.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -115,6 +121,7 @@ typedef struct {
     int prefetch_groups;
     int max_registers;
     int window_F;
+    int precision;
 } rfi_options;
 
 /* Create a context for one stream of `stations` stations (B = N(N+1)/2 baselines)

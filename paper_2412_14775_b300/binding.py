@@ -45,7 +45,7 @@ class rfi_options(ctypes.Structure):
                 ("host_max_T", ctypes.c_int), ("host_chunks", ctypes.c_int),
                 ("compensated", ctypes.c_int), ("prefetch_bytes", ctypes.c_int),
                 ("prefetch_groups", ctypes.c_int), ("max_registers", ctypes.c_int),
-                ("window_F", ctypes.c_int)]
+                ("window_F", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 _lib = None
@@ -153,7 +153,8 @@ def rfi_create_ex(stations, channels, window_M, avg_K, thresholds, dtype, option
     o = options if isinstance(options, rfi_options) else rfi_options(
         kw.get("lanes_per_row", 0), kw.get("warps_per_block", 0), kw.get("host_max_T", 0),
         kw.get("host_chunks", 0), kw.get("compensated", 0), kw.get("prefetch_bytes", 0),
-        kw.get("prefetch_groups", 0), kw.get("max_registers", 0), kw.get("window_F", 0))
+        kw.get("prefetch_groups", 0), kw.get("max_registers", 0), kw.get("window_F", 0),
+        kw.get("precision", 0))
     _check(load_library().rfi_create_ex(ctypes.byref(h), stations, channels, window_M, avg_K,
                                         ctypes.byref(t), _dtype(dtype), ctypes.byref(o)),
            "rfi_create_ex")

@@ -38,13 +38,13 @@ int fail(int status, const char *fmt, ...) {
 }
 
 // ---- kernel instances (rfi_inst_f32.cu, rfi_inst_f16.cu) ----------------------
-const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb) {
+const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb, int mixed) {
     const InstanceTable tabs[] = {instances_f32(), instances_f16()};
     for (const InstanceTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const Instance &in = t.items[i];
             if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan &&
-                in.lb == lb)
+                in.lb == lb && in.mixed == mixed)
                 return &in;
         }
     return nullptr;
@@ -93,6 +93,7 @@ struct rfi_ctx {
     rfi_thresholds thr;
     int P, spu, S, ch, kahan, wpb, lb;
     int F;                              // channels per window footprint
+    int mixed;                          // 1: the paper's trained mixed precision
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     const Instance *inst;
     long long n_seen;
@@ -182,6 +183,12 @@ int choose_shape(rfi_ctx *c, int P_req) {
     // samples per 32-byte load unit: binary16 packs two samples when M is even
     int spu = (dt == DT_F16 && c->M % 2 == 0) ? 2 : 1;
     int P = P_req;
+    if (c->mixed) {
+        // sums run sample after sample in one lane, as the tables order them
+        if (P != 0 && P != 1) return fail(RFI_EINVAL, "precision = 1 needs lanes_per_row = 1");
+        if (c->F != 1) return fail(RFI_EINVAL, "precision = 1 supports time-only windows");
+        P = 1;
+    }
     if (P == 0) {
         P = 2;
         while (P > 1 && (c->M % (P * spu)) != 0) P >>= 1;
@@ -203,7 +210,7 @@ int choose_shape(rfi_ctx *c, int P_req) {
     c->spu = spu;
     c->S = c->M / (P * spu);
     c->ch = largest_chunk(c->S);
-    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb);
+    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed);
     if (!c->inst)
         return fail(RFI_EUNSUPPORTED,
                     "no kernel for this launch shape (reduced register budgets exist for "
@@ -226,6 +233,7 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.R = nrows;
     a.stats_plane = (c->R / c->F) * nwin;
     a.F = c->F;
+    a.d = (float)c->thr.d;
     a.T = T;
     a.M = c->M;
     a.K = c->K;
@@ -412,12 +420,13 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     if (dtype != RFI_C64 && dtype != RFI_C32H) return fail(RFI_EINVAL, "unknown dtype");
     int rc;
     if ((rc = check_thresholds(thr))) return rc;
-    rfi_options o = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    rfi_options o = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (opt) o = *opt;
     if (o.warps_per_block < 0 || o.warps_per_block > 16 || o.host_max_T < 0 || o.host_chunks < 0 ||
         o.compensated < -1 || o.compensated > 1 || o.prefetch_bytes < 0 ||
         o.prefetch_bytes % 16 != 0 || o.prefetch_groups > 64 ||
-        (o.max_registers != 0 && o.max_registers < 64) || o.window_F < 0)
+        (o.max_registers != 0 && o.max_registers < 64) || o.window_F < 0 || o.precision < 0 ||
+        o.precision > 1)
         return fail(RFI_EINVAL, "bad options");
 
     rfi_ctx *c = new (std::nothrow) rfi_ctx();
@@ -442,6 +451,14 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->wpb = o.warps_per_block ? o.warps_per_block : 8;
     c->lb = o.max_registers == 0 || o.max_registers >= 128 ? 0 : (o.max_registers >= 80 ? 1 : 2);
     c->F = o.window_F ? o.window_F : 1;
+    c->mixed = o.precision;
+    if (c->mixed) {
+        if (o.compensated == 1 || c->lb != 0) {
+            delete c;
+            return fail(RFI_EINVAL, "precision = 1 has no Kahan or register-budget variants");
+        }
+        c->kahan = 0;
+    }
     if (c->F & (c->F - 1) || c->F > 32 || channels % c->F != 0 || c->M * c->F < 2) {
         delete c;
         return fail(RFI_EINVAL, "window_F must be a power of two <= 32 dividing channels=%d",
@@ -544,6 +561,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->prefetch_groups = ctx->pf_groups;
     opt->max_registers = ctx->lb == 0 ? 128 : (ctx->lb == 1 ? 80 : 64);
     opt->window_F = ctx->F;
+    opt->precision = ctx->mixed;
     return RFI_OK;
 }
 

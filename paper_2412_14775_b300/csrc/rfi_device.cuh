@@ -41,6 +41,7 @@ struct StreamArgs {
     int T, M, K, Wpr, nwin, n_out;
     int bin_pos0;           // samples of the open bin consumed before this block
     int F;                  // adjacent rows (channels) per window footprint (power of 2)
+    float d;                // SK shape parameter (used by the mixed-precision mode)
     int pf_windows;         // windows per L2 prefetch group (>= 1)
     int pf_groups;          // prefetch distance in groups (0 = no prefetch)
     float c0;               // (W d + 1)/(W - 1), W = M F, Table 1 group 5
@@ -95,19 +96,32 @@ __device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
         : "l"(p));
 }
 
-// Sample k of a unit as 4 complex correlations (xx, xy, yx, yy), each a float2
-// (re, im).  Widening a binary16 value to float32 is exact.
+// Complex Stokes parameters (Sec. 2, Eq. IQUV) of sample k of a unit, each as a float2
+// (re, im): I = xx + yy, Q = xx - yy, U = xy + yx, V = j (xy - yx), i.e.
+// Re V = Im yx - Im xy and Im V = Re xy - Re yx.  Binary16 values are widened to
+// float32 exactly first.
+struct Stokes { float2 I, Q, U, V; };
+
 template <int DT, int UB>
-__device__ __forceinline__ void decode(const Unit<UB> &u, int k, float2 x[4]) {
+__device__ __forceinline__ Stokes stokes_of(const Unit<UB> &u, int k) {
+    float2 xx, xy, yx, yy;
     if constexpr (DT == DT_F32) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            x[c] = make_float2(__uint_as_float(u.r[2 * c]), __uint_as_float(u.r[2 * c + 1]));
+        xx = make_float2(__uint_as_float(u.r[0]), __uint_as_float(u.r[1]));
+        xy = make_float2(__uint_as_float(u.r[2]), __uint_as_float(u.r[3]));
+        yx = make_float2(__uint_as_float(u.r[4]), __uint_as_float(u.r[5]));
+        yy = make_float2(__uint_as_float(u.r[6]), __uint_as_float(u.r[7]));
     } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            x[c] = __half22float2(*reinterpret_cast<const __half2 *>(&u.r[4 * k + c]));
+        xx = __half22float2(*reinterpret_cast<const __half2 *>(&u.r[4 * k + 0]));
+        xy = __half22float2(*reinterpret_cast<const __half2 *>(&u.r[4 * k + 1]));
+        yx = __half22float2(*reinterpret_cast<const __half2 *>(&u.r[4 * k + 2]));
+        yy = __half22float2(*reinterpret_cast<const __half2 *>(&u.r[4 * k + 3]));
     }
+    Stokes s;
+    s.I = __fadd2_rn(xx, yy);
+    s.Q = __fadd2_rn(xx, make_float2(-yy.x, -yy.y));
+    s.U = __fadd2_rn(xy, yx);
+    s.V = make_float2(yx.y - xy.y, xy.x - yx.x);
+    return s;
 }
 
 // ---- packed FP32 pairs (Blackwell f32x2 pipes) -------------------------------
@@ -125,18 +139,15 @@ struct WinAcc {
     float2 s;        // (S1, S2): Table 1 groups 3, 4
     float2 c;        // Kahan compensation of (S1, S2) (when enabled)
     float2 q, u, v;  // (Re, Im) of the resultant sums, Table 2 group 4
-    float2 a[4];     // sums of the raw correlations (averaging)
+    float2 a[4];     // sums of I, Q, U, V (averaging; converted back to correlations
+                     // once per completed bin)
 };
 
-// One sample: Eq. IQUV, then Table 1 groups 1-4 and Table 2 groups 1-4 for the Re
-// and Im parts of (Q, U, V) at once.
+// One sample: Table 1 groups 1-4 and Table 2 groups 1-4 for the Re and Im parts of
+// (Q, U, V) at once, plus the Stokes sums used for the averaged output.
 template <bool KAHAN>
-__device__ __forceinline__ void accumulate(WinAcc &A, const float2 x[4], float2 eps2) {
-    const float2 I = add2(x[0], x[3]);                       // I = xx + yy
-    const float2 Q = sub2(x[0], x[3]);                       // Q = xx - yy
-    const float2 U = add2(x[1], x[2]);                       // U = xy + yx
-    const float2 V = make_float2(x[2].y - x[1].y,            // V = j (xy - yx)
-                                 x[1].x - x[2].x);
+__device__ __forceinline__ void accumulate(WinAcc &A, const Stokes &x, float2 eps2) {
+    const float2 I = x.I, Q = x.Q, U = x.U, V = x.V;
     const float2 I2 = mul2(I, I);
     const float y = I2.x + I2.y;                             // |I|^2
     const float z = sqrt_approx(y);                          // |I|
@@ -156,8 +167,68 @@ __device__ __forceinline__ void accumulate(WinAcc &A, const float2 x[4], float2 
     A.q = fma2(Q, ip, A.q);                                  // sum of q / p
     A.u = fma2(U, ip, A.u);
     A.v = fma2(V, ip, A.v);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) A.a[c] = add2(A.a[c], x[c]);
+    A.a[0] = add2(A.a[0], I);                                // sums of I, Q, U, V
+    A.a[1] = add2(A.a[1], Q);
+    A.a[2] = add2(A.a[2], U);
+    A.a[3] = add2(A.a[3], V);
+}
+
+// ---- paper-mixed precision (Tables 3 and 4) -----------------------------------
+// Binary16 values are carried in float registers; h16 rounds a float32 result to the
+// nearest binary16 (ties to even).  Binary32 groups use correctly rounded operations
+// without fused multiply-add, so every rounding matches the tables' operation order.
+__device__ __forceinline__ float h16(float x) { return __half2float(__float2half_rn(x)); }
+
+__device__ __forceinline__ void accumulate_mixed(WinAcc &A, const Stokes &x, float eps) {
+    // Table 3, groups 1-4 (binary32): y = xr^2 + xi^2, z = sqrt(y), s1 += z, s2 += y
+    const float y = __fadd_rn(__fmul_rn(x.I.x, x.I.x), __fmul_rn(x.I.y, x.I.y));
+    const float z = __fsqrt_rn(y);
+    A.s.x = __fadd_rn(A.s.x, z);
+    A.s.y = __fadd_rn(A.s.y, y);
+    // Table 4, groups 1-3 (binary32) and group 4 (binary16 sums), Re then Im part
+    {
+        const float n = __fadd_rn(__fadd_rn(__fmul_rn(x.Q.x, x.Q.x), __fmul_rn(x.U.x, x.U.x)),
+                                  __fmul_rn(x.V.x, x.V.x));
+        const float p = __fadd_rn(__fsqrt_rn(n), eps);
+        A.q.x = h16(A.q.x + h16(__fdiv_rn(x.Q.x, p)));
+        A.u.x = h16(A.u.x + h16(__fdiv_rn(x.U.x, p)));
+        A.v.x = h16(A.v.x + h16(__fdiv_rn(x.V.x, p)));
+    }
+    {
+        const float n = __fadd_rn(__fadd_rn(__fmul_rn(x.Q.y, x.Q.y), __fmul_rn(x.U.y, x.U.y)),
+                                  __fmul_rn(x.V.y, x.V.y));
+        const float p = __fadd_rn(__fsqrt_rn(n), eps);
+        A.q.y = h16(A.q.y + h16(__fdiv_rn(x.Q.y, p)));
+        A.u.y = h16(A.u.y + h16(__fdiv_rn(x.U.y, p)));
+        A.v.y = h16(A.v.y + h16(__fdiv_rn(x.V.y, p)));
+    }
+    A.a[0] = add2(A.a[0], x.I);
+    A.a[1] = add2(A.a[1], x.Q);
+    A.a[2] = add2(A.a[2], x.U);
+    A.a[3] = add2(A.a[3], x.V);
+}
+
+// Table 3 groups 5-7 and Table 4 groups 5-7 on one window's sums; returns the flag
+// and the statistics (binary16 values).  Adding two binary16 values in float32 is
+// exact, so h16(a + b) is the binary16 sum; products of two binary16 values are exact
+// in float32 too; division and square root are correctly rounded in float32 first.
+__device__ __forceinline__ bool finish_mixed(const StreamArgs &a, float S1, float S2, float qr,
+                                             float ur, float vr, float qi, float ui, float vi,
+                                             float &tau, float &r_re, float &r_im) {
+    const float eps16 = 0.0009765625f;                       // 2^-10
+    const float Wh = h16(a.fM), one = 1.0f;
+    const float lead = h16(__fdiv_rn(h16(h16(Wh * h16(a.d)) + one), h16(Wh - one)));  // g5
+    const float s12 = __fmul_rn(S1, S1);                                               // g6
+    float t = h16(Wh * h16(S2));                                                       // g7
+    t = h16(__fdiv_rn(t, h16(h16(s12) + eps16)));
+    tau = h16(lead * h16(t - one));                  // Sec. 2.1: lead * (W s2/s12 - 1)
+    const bool f_sk = !(tau >= h16(a.s_low) && tau <= h16(a.s_high));
+    const float rre2 = h16(h16(h16(qr * qr) + h16(ur * ur)) + h16(vr * vr));           // g5
+    const float rim2 = h16(h16(h16(qi * qi) + h16(ui * ui)) + h16(vi * vi));
+    r_re = h16(__fdiv_rn(h16(__fsqrt_rn(rre2)), Wh));                                  // g6
+    r_im = h16(__fdiv_rn(h16(__fsqrt_rn(rim2)), Wh));
+    const float g = h16(a.gamma);
+    return f_sk || !(r_re <= g) || !(r_im <= g);                                       // g7
 }
 
 template <int P>
@@ -182,8 +253,11 @@ __device__ __forceinline__ float rowsum(float v, int PF) {
 // CH: load units issued together per lane; KAHAN: compensated S1, S2.
 // DB: double-buffered loads (two chunks in flight per lane) or one chunk at a time
 // (fewer registers, more resident warps).  The arithmetic is the same either way.
-template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true>
+// MIXED: the paper's trained mixed precision (Tables 3 and 4; one lane per row, no
+// footprint, no Kahan), else float32 arithmetic throughout.
+template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
+    static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
     constexpr int RW = 32 / P;
     constexpr int SB = (DT == DT_F32) ? 32 : 16;   // bytes per sample
     constexpr int UB = SB * SPU;                   // bytes per load unit
@@ -196,12 +270,12 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     const char *rp = static_cast<const char *>(a.vis) + rowc * (long long)a.T * SB;
     const bool lead = active && j == 0;     // writes the row's outputs
 
-    float acc[8];
+    float acc[8];            // running bin sums of (I, Q, U, V), re and im
     float cnt = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = 0.f;
     if (a.bin_pos0 != 0) {
-        const float *cp = a.carry + (rowc * P + j) * 9;
+        const float *cp = a.carry + (rowc * P + j) * 9;   // open-bin Stokes sums and count
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = cp[c];
         cnt = cp[8];
@@ -258,9 +332,10 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         for (int c = 0; c < CH; ++c) {
 #pragma unroll
             for (int k = 0; k < SPU; ++k) {
-                float2 x[4];
-                decode<DT, UB>(u[c], k, x);
-                accumulate<KAHAN>(A, x, eps2);
+                if constexpr (MIXED)
+                    accumulate_mixed(A, stokes_of<DT, UB>(u[c], k), a.eps);
+                else
+                    accumulate<KAHAN>(A, stokes_of<DT, UB>(u[c], k), eps2);
             }
         }
     };
@@ -275,15 +350,21 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             qr = rowsum<P>(qr, PF); ur = rowsum<P>(ur, PF); vr = rowsum<P>(vr, PF);
             qi = rowsum<P>(qi, PF); ui = rowsum<P>(ui, PF); vi = rowsum<P>(vi, PF);
         }
-        // Table 1 groups 6-7 and Sec. 2.1: tau = c0 * (W S2 / (S1^2 + eps) - 1)
-        const float s12 = S1 * S1;
-        const float tau = a.c0 * (a.fM * S2 * rcp_approx(s12 + a.eps) - 1.0f);
-        // Table 2 groups 5-6: r = sqrt(q^2 + u^2 + v^2) / W, per part
-        const float r_re = sqrt_approx(qr * qr + ur * ur + vr * vr) * a.invM;
-        const float r_im = sqrt_approx(qi * qi + ui * ui + vi * vi) * a.invM;
-        // SK flag OR (DS Re OR DS Im); a NaN statistic fails its "inside" test
-        const bool f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
-                       !(r_im <= a.gamma);
+        float tau, r_re, r_im;
+        bool f;
+        if constexpr (MIXED) {
+            f = finish_mixed(a, S1, S2, qr, ur, vr, qi, ui, vi, tau, r_re, r_im);
+        } else {
+            // Table 1 groups 6-7 and Sec. 2.1: tau = c0 * (W S2 / (S1^2 + eps) - 1)
+            const float s12 = S1 * S1;
+            tau = a.c0 * (a.fM * S2 * rcp_approx(s12 + a.eps) - 1.0f);
+            // Table 2 groups 5-6: r = sqrt(q^2 + u^2 + v^2) / W, per part
+            r_re = sqrt_approx(qr * qr + ur * ur + vr * vr) * a.invM;
+            r_im = sqrt_approx(qi * qi + ui * ui + vi * vi) * a.invM;
+            // SK flag OR (DS Re OR DS Im); a NaN statistic fails its "inside" test
+            f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
+                !(r_im <= a.gamma);
+        }
         if (st_lead) {
             st_row[w] = tau;
             st_row[w + plane] = r_re;
@@ -332,10 +413,14 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
             const float n = allsum<P>(cnt);
             if (lead) {
+                // tot holds sums of (I, Q, U, V); the correlations are xx = (I + Q)/2,
+                // yy = (I - Q)/2, xy = (U - jV)/2, yx = (U + jV)/2
                 float4 *ap = reinterpret_cast<float4 *>(a.avg + (row * a.n_out + bin) * 8);
-                const float inv = n > 0.f ? __frcp_rn(n) : 0.f;
-                ap[0] = make_float4(tot[0] * inv, tot[1] * inv, tot[2] * inv, tot[3] * inv);
-                ap[1] = make_float4(tot[4] * inv, tot[5] * inv, tot[6] * inv, tot[7] * inv);
+                const float h = n > 0.f ? 0.5f * __frcp_rn(n) : 0.f;
+                const float Ir = tot[0], Ii = tot[1], Qr = tot[2], Qi = tot[3];
+                const float Ur = tot[4], Ui = tot[5], Vr = tot[6], Vi = tot[7];
+                ap[0] = make_float4((Ir + Qr) * h, (Ii + Qi) * h, (Ur + Vi) * h, (Ui - Vr) * h);
+                ap[1] = make_float4((Ur - Vi) * h, (Ui + Vr) * h, (Ir - Qr) * h, (Ii - Qi) * h);
                 a.weight[row * a.n_out + bin] = __fdiv_rn(n, a.fK);
             }
 #pragma unroll
@@ -407,20 +492,20 @@ template <> struct Bounds<0> { static constexpr int threads = 512, blocks = 1; }
 template <> struct Bounds<1> { static constexpr int threads = 256, blocks = 3; };
 template <> struct Bounds<2> { static constexpr int threads = 256, blocks = 4; };
 
-template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0>
+template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, bool MIXED = false>
 __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_block(const __grid_constant__ StreamArgs a) {
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     // the 128-register budget keeps two chunks in flight; tighter budgets load one
     // chunk at a time and rely on more resident warps instead
-    process_group<DT, SPU, P, CH, KAHAN, LB == 0>(a, group);
+    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED>(a, group);
 }
 
 // Persistent batch: every warp takes (stream, row group) tasks from a device counter
 // until none is left; the last block to finish resets the counter for the next
 // launch in stream order.
-template <int DT, int SPU, int P, int CH, bool KAHAN>
+template <int DT, int SPU, int P, int CH, bool KAHAN, bool MIXED = false>
 __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchArgs b) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -435,7 +520,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchA
             const bool le = k < b.n && b.prefix[k + 1] <= (long long)t;
             i += __popc(__ballot_sync(FULL, le));
         }
-        process_group<DT, SPU, P, CH, KAHAN>(b.s[i], (long long)t - b.prefix[i]);
+        process_group<DT, SPU, P, CH, KAHAN, true, MIXED>(b.s[i], (long long)t - b.prefix[i]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

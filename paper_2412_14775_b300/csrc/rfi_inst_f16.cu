@@ -6,6 +6,8 @@
 namespace rfi {
 
 static const Instance k_table[] = {
+    RFI_INSTM_CH(DT_F16, 2),
+    RFI_INSTM_CH(DT_F16, 1),
     RFI_INST0_P(DT_F16, 2, 0),
     RFI_INST0_P(DT_F16, 2, 1),
     RFI_INSTB_P(DT_F16, 2, 1),

@@ -5,6 +5,7 @@
 namespace rfi {
 
 static const Instance k_table[] = {
+    RFI_INSTM_CH(DT_F32, 1),
     RFI_INST0_P(DT_F32, 1, 0),
     RFI_INST0_P(DT_F32, 1, 1),
     RFI_INSTB_P(DT_F32, 1, 1),

@@ -8,7 +8,7 @@
 namespace rfi {
 
 struct Instance {
-    int dt, spu, P, ch, kahan, lb;
+    int dt, spu, P, ch, kahan, lb, mixed;
     const void *block_fn;   // k_block<...>
     const void *batch_fn;   // k_batch<...>; the register budget does not change results,
                             // so every budget shares the LB = 0 batch kernel
@@ -26,12 +26,18 @@ InstanceTable instances_f16();
 
 // Entries for one (DT, SPU, P, CH, K): LB = 0 with its own batch kernel.
 #define RFI_INST0(DT, SPU, P, CH, K)                                                        \
-    {DT, SPU, P, CH, K, 0, (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0>,        \
+    {DT, SPU, P, CH, K, 0, 0, (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0>,     \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K>}
 // A tighter register budget LB for the single-stream kernel.
 #define RFI_INSTB(DT, SPU, P, CH, LB)                                                       \
-    {DT, SPU, P, CH, 0, LB, (const void *)&rfi::k_block<DT, SPU, P, CH, false, LB>,        \
+    {DT, SPU, P, CH, 0, LB, 0, (const void *)&rfi::k_block<DT, SPU, P, CH, false, LB>,     \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
+// The paper-mixed precision mode (one lane per row).
+#define RFI_INSTM(DT, SPU, CH)                                                              \
+    {DT, SPU, 1, CH, 0, 0, 1, (const void *)&rfi::k_block<DT, SPU, 1, CH, false, 0, true>, \
+     (const void *)&rfi::k_batch<DT, SPU, 1, CH, false, true>}
+#define RFI_INSTM_CH(DT, SPU)                                                               \
+    RFI_INSTM(DT, SPU, 1), RFI_INSTM(DT, SPU, 2), RFI_INSTM(DT, SPU, 4), RFI_INSTM(DT, SPU, 5)
 #define RFI_INST0_CH(DT, SPU, P, K)                                                         \
     RFI_INST0(DT, SPU, P, 1, K), RFI_INST0(DT, SPU, P, 2, K), RFI_INST0(DT, SPU, P, 4, K),  \
         RFI_INST0(DT, SPU, P, 5, K)

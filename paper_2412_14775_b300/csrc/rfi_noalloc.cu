@@ -161,6 +161,7 @@ extern "C" int rfi_process_block_noalloc(int stations, int channels, int window_
     a.n_out = (int)n_out;
     a.bin_pos0 = (int)(n_seen % avg_K);
     a.F = 1;
+    a.d = (float)thr->d;
     a.pf_windows = std::max(1, 1024 / (window_M * sb));
     a.pf_groups = 0;
     const double Md = window_M;
