@@ -108,6 +108,20 @@ typedef enum {
  *                  binary32, every operation rounded in the tables' order, eps =
  *                  2^-10 inside binary16 groups; one lane per row, time-only windows,
  *                  no Kahan.  Statistics are then binary16 values.
+ *   loader         0 = direct 32-byte global loads (default).  1 = each lane owns a
+ *                  row, staged in shared memory a few windows at a time by
+ *                  cp.async.bulk (TMA) copies that complete on one mbarrier per stage;
+ *                  rows are padded so that the lanes' reads are bank-conflict free.
+ *                  Every stage wait is bounded (about 2 s); a wait that gives up sets
+ *                  the context's error word, read by rfi_check.  Needs lanes_per_row 1,
+ *                  float32 arithmetic and the 128-register budget; results equal the
+ *                  direct loader with lanes_per_row = 1.
+ *   tma_stage_windows  windows of every row per stage (0 = 1).
+ *   tma_stages     stages in flight per warp (0 = 2); shared memory per block must
+ *                  stay within 227 KB.
+ *   debug_inject_wait_timeout  1 = for testing failure detection only: the staged
+ *                  loader expects 16 more bytes per stage than it copies, so every
+ *                  stage wait gives up after about 1 ms and the error word is set.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -122,6 +136,10 @@ typedef struct {
     int max_registers;
     int window_F;
     int precision;
+    int loader;
+    int tma_stage_windows;
+    int tma_stages;
+    int debug_inject_wait_timeout;
 } rfi_options;
 
 /* Create a context for one stream of `stations` stations (B = N(N+1)/2 baselines)
@@ -219,6 +237,11 @@ int rfi_process_block_noalloc(int stations, int channels, int window_M, int avg_
                               const rfi_thresholds *thr, rfi_dtype dtype, long long n_seen,
                               const void *vis, int T, uint32_t *flags, float *avg,
                               float *weight, float *stats, void *stream);
+
+/* Synchronise `stream` and report a device-side failure of work issued for the
+ * context: RFI_ETIMEOUT when a bounded wait in the kernel gave up (the context then
+ * stays failed until rfi_reset), RFI_OK otherwise. */
+int rfi_check(rfi_ctx *ctx, void *stream);
 
 /* Drop the averaging carry and the sample count (stream restart); clears a sticky
  * error.  Synchronises with work already issued for the context. */

@@ -90,6 +90,14 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
                 stage1.append((run(o), o))
             except B.RfiError:          # no kernel with this register budget
                 continue
+    if F * 1 <= 32:      # rows staged in shared memory by TMA, one lane per row
+        for wpb, G, NS in ((4, 1, 2), (8, 1, 2), (4, 2, 2), (4, 1, 3), (8, 2, 2), (2, 4, 2)):
+            o = dict(lanes_per_row=1, warps_per_block=wpb, max_registers=0, prefetch_groups=0,
+                     prefetch_bytes=1024, loader=1, tma_stage_windows=G, tma_stages=NS)
+            try:
+                stage1.append((run(o), o))
+            except B.RfiError:          # does not fit the shared memory
+                continue
     stage1.sort(key=lambda x: x[0])
     best_t, best = stage1[0]
     for _, base in stage1[:3]:

@@ -23,7 +23,7 @@ EXPORTED = ["rfi_create", "rfi_create_ex", "rfi_rows", "rfi_outputs_for", "rfi_g
             "rfi_set_thresholds", "rfi_process_block", "rfi_process_block_host",
             "rfi_process_batch", "rfi_batch_graph_create", "rfi_batch_graph_launch",
             "rfi_batch_graph_destroy", "rfi_reset", "rfi_destroy", "rfi_status_str",
-            "rfi_last_error", "rfi_process_block_noalloc"]
+            "rfi_last_error", "rfi_process_block_noalloc", "rfi_check"]
 
 # Fixed size of the library's no-allocation scratch (RFI_NOALLOC_SCRATCH_BYTES).
 RFI_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -45,7 +45,9 @@ class rfi_options(ctypes.Structure):
                 ("host_max_T", ctypes.c_int), ("host_chunks", ctypes.c_int),
                 ("compensated", ctypes.c_int), ("prefetch_bytes", ctypes.c_int),
                 ("prefetch_groups", ctypes.c_int), ("max_registers", ctypes.c_int),
-                ("window_F", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("window_F", ctypes.c_int), ("precision", ctypes.c_int),
+                ("loader", ctypes.c_int), ("tma_stage_windows", ctypes.c_int),
+                ("tma_stages", ctypes.c_int), ("debug_inject_wait_timeout", ctypes.c_int)]
 
 
 _lib = None
@@ -78,6 +80,7 @@ def load_library(path=None):
         "rfi_batch_graph_launch": ([vp, pp, pp, pp, pp, pp, vp], ip),
         "rfi_batch_graph_destroy": ([vp], ip),
         "rfi_reset": ([vp], ip),
+        "rfi_check": ([vp, vp], ip),
         "rfi_destroy": ([vp], ip),
         "rfi_process_block_noalloc": ([ip, ip, ip, ip, ctypes.POINTER(rfi_thresholds), ip,
                                        ctypes.c_longlong, vp, ip, vp, vp, vp, vp, vp], ip),
@@ -150,11 +153,13 @@ def rfi_create(stations, channels, window_M, avg_K, thresholds, dtype):
 def rfi_create_ex(stations, channels, window_M, avg_K, thresholds, dtype, options=None, **kw):
     h = ctypes.c_void_p()
     t = _thr(thresholds)
-    o = options if isinstance(options, rfi_options) else rfi_options(
-        kw.get("lanes_per_row", 0), kw.get("warps_per_block", 0), kw.get("host_max_T", 0),
-        kw.get("host_chunks", 0), kw.get("compensated", 0), kw.get("prefetch_bytes", 0),
-        kw.get("prefetch_groups", 0), kw.get("max_registers", 0), kw.get("window_F", 0),
-        kw.get("precision", 0))
+    if isinstance(options, rfi_options):
+        o = options
+    else:
+        unknown = set(kw) - {f for f, _ in rfi_options._fields_}
+        if unknown:
+            raise TypeError(f"unknown options {sorted(unknown)}")
+        o = rfi_options(*[int(kw.get(f, 0)) for f, _ in rfi_options._fields_])
     _check(load_library().rfi_create_ex(ctypes.byref(h), stations, channels, window_M, avg_K,
                                         ctypes.byref(t), _dtype(dtype), ctypes.byref(o)),
            "rfi_create_ex")
@@ -243,6 +248,10 @@ def rfi_process_block_noalloc(stations, channels, window_M, avg_K, thresholds, d
         stations, channels, window_M, avg_K, ctypes.byref(t), _dtype(dtype), n_seen, _ptr(vis),
         T, _ptr(flags), _ptr(avg), _ptr(weight), _ptr(stats), _stream(stream)),
         "rfi_process_block_noalloc")
+
+
+def rfi_check(ctx, stream=None):
+    _check(load_library().rfi_check(ctx, _stream(stream)), "rfi_check")
 
 
 def rfi_reset(ctx):

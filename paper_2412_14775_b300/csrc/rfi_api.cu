@@ -50,6 +50,16 @@ const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb,
     return nullptr;
 }
 
+const void *find_tma(int dt, int spu, int ch, int kahan) {
+    const TmaTable tabs[] = {tma_instances_f32(), tma_instances_f16()};
+    for (const TmaTable &t : tabs)
+        for (int i = 0; i < t.n; ++i) {
+            const TmaInstance &in = t.items[i];
+            if (in.dt == dt && in.spu == spu && in.ch == ch && in.kahan == kahan) return in.fn;
+        }
+    return nullptr;
+}
+
 int largest_chunk(int S) {
     static const int opts[] = {5, 4, 2, 1};
     for (int c : opts)
@@ -92,14 +102,22 @@ struct rfi_ctx {
     rfi_dtype dtype;
     rfi_thresholds thr;
     int P, spu, S, ch, kahan, wpb, lb;
+    int wpb_auto;                       // warps_per_block was left to the library
     int F;                              // channels per window footprint
     int mixed;                          // 1: the paper's trained mixed precision
+    int loader;                         // 0: direct loads, 1: TMA staging in shared memory
+    const void *tma_fn;
+    int tma_G, tma_NS;                  // windows per stage, stages per warp
+    unsigned tma_pitch;
+    size_t tma_smem;                    // dynamic shared memory per block
+    int inject;                         // fault injection: stage waits cannot complete
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     const Instance *inst;
     long long n_seen;
     int status;
     float *carry;                       // [R][P][9]
-    unsigned long long *counter;        // [2]: batch task counter, blocks done
+    unsigned long long *counter;        // [0] batch task counter, [1] blocks done,
+                                        // [2] low word: device error word
     // host-buffer path
     int host_max_T, host_chunks;
     char *h_vis;
@@ -183,6 +201,10 @@ int choose_shape(rfi_ctx *c, int P_req) {
     // samples per 32-byte load unit: binary16 packs two samples when M is even
     int spu = (dt == DT_F16 && c->M % 2 == 0) ? 2 : 1;
     int P = P_req;
+    if (c->loader == 1) {
+        if (P != 0 && P != 1) return fail(RFI_EINVAL, "loader = 1 runs one lane per row");
+        P = 1;
+    }
     if (c->mixed) {
         // sums run sample after sample in one lane, as the tables order them
         if (P != 0 && P != 1) return fail(RFI_EINVAL, "precision = 1 needs lanes_per_row = 1");
@@ -211,6 +233,25 @@ int choose_shape(rfi_ctx *c, int P_req) {
     c->S = c->M / (P * spu);
     c->ch = largest_chunk(c->S);
     c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed);
+    if (c->loader == 1) {
+        c->tma_fn = find_tma(dt, spu, c->ch, c->kahan);
+        if (!c->tma_fn || c->mixed || c->lb != 0)
+            return fail(RFI_EUNSUPPORTED, "no shared-memory loader for this shape "
+                                          "(float32 arithmetic, 128-register budget only)");
+        const unsigned SR = (unsigned)(c->tma_G * c->M * (dt == DT_F32 ? 32 : 16));
+        c->tma_pitch = SR + (((SR / 16) % 2 == 0) ? 16u : 32u);   // odd multiple of 16 B
+        auto smem_for = [&](int wpb) {
+            const size_t bars = (8u * c->tma_NS * wpb + 127u) & ~(size_t)127u;
+            return bars + (size_t)wpb * c->tma_NS * 32 * c->tma_pitch;
+        };
+        if (c->wpb_auto)      // the largest block that fits the shared memory
+            while (c->wpb > 1 && smem_for(c->wpb) > 227 * 1024) c->wpb >>= 1;
+        c->tma_smem = smem_for(c->wpb);
+        if (c->tma_smem > 227 * 1024)
+            return fail(RFI_EINVAL, "shared-memory staging needs %zu bytes per block (max "
+                                    "232448): fewer warps, stages or windows per stage",
+                        c->tma_smem);
+    }
     if (!c->inst)
         return fail(RFI_EUNSUPPORTED,
                     "no kernel for this launch shape (reduced register budgets exist for "
@@ -234,6 +275,12 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.stats_plane = (c->R / c->F) * nwin;
     a.F = c->F;
     a.d = (float)c->thr.d;
+    a.stage_windows = c->tma_G;
+    a.stages = c->tma_NS;
+    a.pitch = c->tma_pitch;
+    a.tx_extra = c->inject ? 16u : 0u;
+    a.wait_limit = c->inject ? 2000000ll : 4000000000ll;   // ~1 ms / ~2 s at 2 GHz
+    a.err = reinterpret_cast<int *>(c->counter + 2);
     a.T = T;
     a.M = c->M;
     a.K = c->K;
@@ -287,14 +334,35 @@ int set_cuda_error(rfi_ctx *c, cudaError_t e, const char *where) {
     return fail(RFI_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+// Allow a kernel the dynamic shared memory it asks for (once per kernel and size).
+cudaError_t allow_smem(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, size_t>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &d : done)
+        if (d.first == fn && d.second >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e == cudaSuccess) done.push_back({fn, bytes});
+    return e;
+}
+
 int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
     if (a.R <= 0) return RFI_OK;
     const int RW = 32 / c->P;
     const long long groups = (a.R + RW - 1) / RW;
     const long long blocks = (groups + c->wpb - 1) / c->wpb;
     void *args[] = {const_cast<StreamArgs *>(&a)};
-    cudaError_t e = cudaLaunchKernel(c->inst->block_fn, dim3((unsigned)blocks),
-                                     dim3(32 * c->wpb), args, 0, st);
+    cudaError_t e;
+    if (c->loader == 1) {
+        e = allow_smem(c->tma_fn, c->tma_smem);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args,
+                                 c->tma_smem, st);
+    } else {
+        e = cudaLaunchKernel(c->inst->block_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args,
+                             0, st);
+    }
     if (e != cudaSuccess) return set_cuda_error(c, e, "kernel launch");
     return RFI_OK;
 }
@@ -420,13 +488,15 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     if (dtype != RFI_C64 && dtype != RFI_C32H) return fail(RFI_EINVAL, "unknown dtype");
     int rc;
     if ((rc = check_thresholds(thr))) return rc;
-    rfi_options o = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    rfi_options o = {};
     if (opt) o = *opt;
     if (o.warps_per_block < 0 || o.warps_per_block > 16 || o.host_max_T < 0 || o.host_chunks < 0 ||
         o.compensated < -1 || o.compensated > 1 || o.prefetch_bytes < 0 ||
         o.prefetch_bytes % 16 != 0 || o.prefetch_groups > 64 ||
         (o.max_registers != 0 && o.max_registers < 64) || o.window_F < 0 || o.precision < 0 ||
-        o.precision > 1)
+        o.precision > 1 || o.loader < 0 || o.loader > 1 || o.tma_stage_windows < 0 ||
+        o.tma_stage_windows > 64 || o.tma_stages < 0 || o.tma_stages > 8 ||
+        o.debug_inject_wait_timeout < 0 || o.debug_inject_wait_timeout > 1)
         return fail(RFI_EINVAL, "bad options");
 
     rfi_ctx *c = new (std::nothrow) rfi_ctx();
@@ -449,9 +519,14 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->thr = *thr;
     c->kahan = o.compensated == 1 || (o.compensated == 0 && window_M >= 64);
     c->wpb = o.warps_per_block ? o.warps_per_block : 8;
+    c->wpb_auto = o.warps_per_block == 0;
     c->lb = o.max_registers == 0 || o.max_registers >= 128 ? 0 : (o.max_registers >= 80 ? 1 : 2);
     c->F = o.window_F ? o.window_F : 1;
     c->mixed = o.precision;
+    c->loader = o.loader;
+    c->tma_G = o.tma_stage_windows ? o.tma_stage_windows : 1;
+    c->tma_NS = o.tma_stages ? o.tma_stages : 2;
+    c->inject = o.debug_inject_wait_timeout;
     if (c->mixed) {
         if (o.compensated == 1 || c->lb != 0) {
             delete c;
@@ -477,9 +552,9 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     }
     cudaError_t e;
     if ((e = cudaMalloc(&c->carry, sizeof(float) * 9 * (size_t)c->P * c->R)) != cudaSuccess ||
-        (e = cudaMalloc(&c->counter, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&c->counter, 4 * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMemset(c->carry, 0, sizeof(float) * 9 * (size_t)c->P * c->R)) != cudaSuccess ||
-        (e = cudaMemset(c->counter, 0, 2 * sizeof(unsigned long long))) != cudaSuccess) {
+        (e = cudaMemset(c->counter, 0, 4 * sizeof(unsigned long long))) != cudaSuccess) {
         cudaGetLastError();
         free_ctx(c);
         return fail(e == cudaErrorMemoryAllocation ? RFI_ENOMEM : RFI_ECUDA,
@@ -562,6 +637,10 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->max_registers = ctx->lb == 0 ? 128 : (ctx->lb == 1 ? 80 : 64);
     opt->window_F = ctx->F;
     opt->precision = ctx->mixed;
+    opt->loader = ctx->loader;
+    opt->tma_stage_windows = ctx->tma_G;
+    opt->tma_stages = ctx->tma_NS;
+    opt->debug_inject_wait_timeout = ctx->inject;
     return RFI_OK;
 }
 
@@ -742,6 +821,24 @@ int rfi_batch_graph_destroy(rfi_batch_graph *g) {
     return RFI_OK;
 }
 
+int rfi_check(rfi_ctx *ctx, void *stream) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    int err = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&err, reinterpret_cast<int *>(ctx->counter + 2), sizeof(int),
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_check");
+    if (err) {
+        ctx->status = RFI_ETIMEOUT;
+        return fail(RFI_ETIMEOUT, "a bounded wait in the kernel gave up (error word %d); "
+                                  "results of that launch are incomplete; rfi_reset clears it",
+                    err);
+    }
+    return RFI_OK;
+}
+
 int rfi_reset(rfi_ctx *ctx) {
     if (!ctx || !is_live(ctx) || ctx->magic != CTX_MAGIC)
         return fail(RFI_ESTATE, "not a live context");
@@ -749,7 +846,7 @@ int rfi_reset(rfi_ctx *ctx) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
         e = cudaMemset(ctx->carry, 0, sizeof(float) * 9 * (size_t)ctx->P * ctx->R);
-    if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         ctx->status = RFI_ECUDA;
         return fail(RFI_ECUDA, "reset: %s", cudaGetErrorString(e));

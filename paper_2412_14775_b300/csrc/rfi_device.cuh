@@ -44,6 +44,13 @@ struct StreamArgs {
     float d;                // SK shape parameter (used by the mixed-precision mode)
     int pf_windows;         // windows per L2 prefetch group (>= 1)
     int pf_groups;          // prefetch distance in groups (0 = no prefetch)
+    // shared-memory staging (TMA loader)
+    int stage_windows;      // windows of every row per stage (G)
+    int stages;             // stages per warp (NS)
+    unsigned pitch;         // bytes per row in a stage (G*M*SB padded to an odd x 16)
+    unsigned tx_extra;      // extra bytes expected per stage (fault injection only)
+    long long wait_limit;   // cycles a stage wait may take before it gives up
+    int *err;               // device error word: 1 = a bounded wait gave up
     float c0;               // (W d + 1)/(W - 1), W = M F, Table 1 group 5
     float s_low, s_high, gamma, eps;
     float fM;               // W = M F as float (samples in one window)
@@ -79,6 +86,50 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// ---- TMA bulk copies into shared memory, completed on an mbarrier --------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for a barrier phase for at most `limit` cycles; false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ---- streaming loads of one 16- or 32-byte unit (read once: no L1 allocation) ---
 template <int UB> struct Unit;
 template <> struct Unit<32> { uint32_t r[8]; };
@@ -94,6 +145,18 @@ __device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
     asm("ld.global.nc.L1::no_allocate.v4.b32 {%0,%1,%2,%3}, [%4];"
         : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3])
         : "l"(p));
+}
+
+__device__ __forceinline__ void load_unit_smem(const unsigned char *p, Unit<32> &u) {
+    const unsigned a = smem_u32(p);
+    asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3]) : "r"(a));
+    asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(u.r[4]), "=r"(u.r[5]), "=r"(u.r[6]), "=r"(u.r[7]) : "r"(a + 16));
+}
+__device__ __forceinline__ void load_unit_smem(const unsigned char *p, Unit<16> &u) {
+    asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3]) : "r"(smem_u32(p)));
 }
 
 // Complex Stokes parameters (Sec. 2, Eq. IQUV) of sample k of a unit, each as a float2
@@ -255,9 +318,14 @@ __device__ __forceinline__ float rowsum(float v, int PF) {
 // (fewer registers, more resident warps).  The arithmetic is the same either way.
 // MIXED: the paper's trained mixed precision (Tables 3 and 4; one lane per row, no
 // footprint, no Kahan), else float32 arithmetic throughout.
-template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false>
+// TMA: every lane owns one row (P = 1) and reads it from shared memory, where the
+// warp's rows are staged a few windows at a time by cp.async.bulk copies (one per row,
+// issued by the row's lane) that complete on one mbarrier per stage.
+template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false,
+          bool TMA = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
     static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
+    static_assert(!TMA || P == 1, "the shared-memory loader runs one lane per row");
     constexpr int RW = 32 / P;
     constexpr int SB = (DT == DT_F32) ? 32 : 16;   // bytes per sample
     constexpr int UB = SB * SPU;                   // bytes per load unit
@@ -324,8 +392,10 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     for (int c = 0; c < 4; ++c) A.a[c] = zero2;
     int w = 0, cw = 0;
     Unit<UB> ua[CH], ub[DB ? CH : 1];
+    if constexpr (!TMA) {
 #pragma unroll
-    for (int c = 0; c < CH; ++c) load_unit(cp_ + c * (P * UB), ua[c]);
+        for (int c = 0; c < CH; ++c) load_unit(cp_ + c * (P * UB), ua[c]);
+    }
 
     auto consume = [&](const Unit<UB>(&u)[CH]) {
 #pragma unroll
@@ -441,7 +511,65 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         }
     };
 
-    if constexpr (DB) {
+    if constexpr (TMA) {
+        // stages of G windows for the warp's 32 rows: [stage][lane][pitch] bytes
+        extern __shared__ __align__(128) unsigned char smem_raw[];
+        const int warp = threadIdx.x >> 5;
+        const int NS = a.stages, G = a.stage_windows;
+        uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + warp * NS;
+        const unsigned bar_bytes = (8u * NS * (blockDim.x >> 5) + 127u) & ~127u;
+        unsigned char *wbuf = smem_raw + bar_bytes + (size_t)warp * NS * 32 * a.pitch;
+        const int ngroups = (a.nwin + G - 1) / G;
+        const unsigned n_active = __popc(__ballot_sync(FULL, active));
+        if (lane == 0) {
+            for (int st = 0; st < NS; ++st) mbar_init(&bars[st], 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+        auto issue = [&](int g) {
+            const int st = g % NS;
+            const int w0 = g * G;
+            const unsigned bytes = (unsigned)(min(G, a.nwin - w0) * a.M * SB);
+            if (lane == 0) mbar_arrive_expect_tx(&bars[st], bytes * n_active + a.tx_extra);
+            __syncwarp();
+            if (active)
+                tma_load_1d(wbuf + ((size_t)st * 32 + lane) * a.pitch, rp + (size_t)w0 * a.M * SB,
+                            bytes, &bars[st]);
+        };
+        for (int g = 0; g < min(NS, ngroups); ++g) issue(g);
+        int g = 0;
+        for (; g < ngroups; ++g) {
+            const int st = g % NS;
+            bool ok = mbar_wait_bounded(&bars[st], (unsigned)((g / NS) & 1), a.wait_limit);
+            ok = __all_sync(FULL, ok);
+            if (!ok) {
+                if (lane == 0) atomicOr(a.err, 1);
+                break;
+            }
+            const unsigned char *sp = wbuf + ((size_t)st * 32 + lane) * a.pitch;
+            const int nw = min(G, a.nwin - g * G);
+            for (int wi = 0; wi < nw; ++wi) {
+                for (int q = 0; q < nch; ++q) {
+                    Unit<UB> u[CH];
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) load_unit_smem(sp + (q * CH + c) * UB, u[c]);
+                    consume(u);
+                }
+                end_window();
+                sp += wbytes;
+            }
+            __syncwarp();
+            fence_proxy_async();           // our reads of this stage precede its refill
+            if (g + NS < ngroups) issue(g + NS);
+        }
+        if (g < ngroups) {
+            // a wait gave up: let the copies still in flight land (again bounded)
+            // before the warp leaves, so no copy targets shared memory of an exited CTA
+            for (int h = g; h < min(ngroups, g + NS); ++h)
+                mbar_wait_bounded(&bars[h % NS], (unsigned)((h / NS) & 1), a.wait_limit);
+            return;
+        }
+    } else if constexpr (DB) {
         for (int q = 0; q < Q; q += 2) {
             if (q + 1 < Q) {
 #pragma unroll
@@ -500,6 +628,15 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     // the 128-register budget keeps two chunks in flight; tighter budgets load one
     // chunk at a time and rely on more resident warps instead
     process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED>(a, group);
+}
+
+// One lane per row, rows staged in shared memory by TMA bulk copies; dynamic shared
+// memory = round_up(8 * warps * stages, 128) + warps * stages * 32 * pitch bytes.
+template <int DT, int SPU, int CH, bool KAHAN>
+__global__ void __launch_bounds__(512, 1) k_tma(const __grid_constant__ StreamArgs a) {
+    const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (group * 32 >= a.R) return;     // whole warp leaves together
+    process_group<DT, SPU, 1, CH, KAHAN, false, false, true>(a, group);
 }
 
 // Persistent batch: every warp takes (stream, row group) tasks from a device counter

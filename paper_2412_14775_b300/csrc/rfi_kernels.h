@@ -22,6 +22,18 @@ struct InstanceTable {
 InstanceTable instances_f32();
 InstanceTable instances_f16();
 
+// The shared-memory (TMA) loader: one lane per row, direct-load twin for batches.
+struct TmaInstance {
+    int dt, spu, ch, kahan;
+    const void *fn;         // k_tma<...>
+};
+struct TmaTable {
+    const TmaInstance *items;
+    int n;
+};
+TmaTable tma_instances_f32();
+TmaTable tma_instances_f16();
+
 }  // namespace rfi
 
 // Entries for one (DT, SPU, P, CH, K): LB = 0 with its own batch kernel.
@@ -50,3 +62,6 @@ InstanceTable instances_f16();
 #define RFI_INSTB_P(DT, SPU, LB)                                                            \
     RFI_INSTB_CH(DT, SPU, 1, LB), RFI_INSTB_CH(DT, SPU, 2, LB), RFI_INSTB_CH(DT, SPU, 4, LB), \
         RFI_INSTB_CH(DT, SPU, 8, LB)
+#define RFI_TMA(DT, SPU, CH, K) {DT, SPU, CH, K, (const void *)&rfi::k_tma<DT, SPU, CH, (bool)K>}
+#define RFI_TMA_CH(DT, SPU, K)                                                              \
+    RFI_TMA(DT, SPU, 1, K), RFI_TMA(DT, SPU, 2, K), RFI_TMA(DT, SPU, 4, K), RFI_TMA(DT, SPU, 5, K)

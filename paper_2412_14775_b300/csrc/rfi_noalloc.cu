@@ -144,7 +144,7 @@ extern "C" int rfi_process_block_noalloc(int stations, int channels, int window_
     // The kernel reads the carry only when this block continues an open bin
     // (n_seen % K != 0); that carry was written by the previous call for the same
     // stream.  Nothing in the scratch has to start at zero.
-    StreamArgs a;
+    StreamArgs a = {};
     a.vis = vis;
     a.flags = flags;
     a.avg = avg;

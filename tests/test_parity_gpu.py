@@ -111,6 +111,13 @@ SHAPES = [
     ("f32", 3, 16, 16, 32, [48, 16], {"window_F": 8, "lanes_per_row": 4}),
     ("f16", 3, 16, 8, 16, [32, 32], {"window_F": 16, "lanes_per_row": 2}),
     ("f32", 3, 4, 1, 4, [8, 4], {"window_F": 4}),
+    # rows staged in shared memory by TMA bulk copies (one lane per row)
+    ("f32", 5, 4, 16, 64, [256, 128], {"loader": 1}),
+    ("f16", 5, 4, 16, 32, [96, 64], {"loader": 1, "tma_stage_windows": 3, "tma_stages": 3}),
+    ("f16", 4, 5, 5, 10, [10, 20, 40], {"loader": 1, "tma_stage_windows": 2}),
+    ("f32", 6, 3, 20, 40, [40, 60, 100], {"loader": 1, "tma_stages": 1, "warps_per_block": 2}),
+    ("f16", 5, 4, 10, 20, [20, 40], {"loader": 1, "window_F": 2}),
+    ("f32", 5, 4, 64, 128, [128, 64, 192], {"loader": 1}),
 ]
 
 
@@ -372,3 +379,43 @@ def test_invalid_arguments():
         binding.rfi_destroy(ctx)
     assert ei.value.status == 5                                 # double destroy
     binding.rfi_destroy(None)                                   # no-op
+
+
+def test_tma_loader_bit_identical_to_direct_loads():
+    """The shared-memory loader and the direct loader with one lane per row perform
+    the same arithmetic in the same order."""
+    M, K, T = 16, 64, 256
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=31, stations=9, channels=11, T=T)["vis"]
+    for dtype in ("f32", "f16"):
+        v = to_device_rows(d, dtype)
+        a = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=1).process(v)
+        b = RfiStream(9, 11, M, K, thr, dtype, loader=1, tma_stage_windows=2).process(v)
+        torch.cuda.synchronize()
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(a[k], b[k]), (dtype, k)
+
+
+def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
+    """Failure detection without a GPU fault: with the injection option the staged
+    loader expects more bytes than it copies, so every stage wait gives up after about
+    1 ms; rfi_check reports RFI_ETIMEOUT, and the device keeps working."""
+    M, K, T = 16, 64, 128
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=32, stations=6, channels=4, T=T)["vis"]
+    v = to_device_rows(d, "f32")
+    bad = RfiStream(6, 4, M, K, thr, "f32", loader=1, debug_inject_wait_timeout=1)
+    bad.process(v)
+    with pytest.raises(RfiError) as ei:
+        binding.rfi_check(bad.ctx)
+    assert ei.value.status == 4                                   # RFI_ETIMEOUT
+    with pytest.raises(RfiError):                                 # sticky until reset
+        bad.process(v)
+    binding.rfi_reset(bad.ctx)
+    good = RfiStream(6, 4, M, K, thr, "f32", loader=1)
+    out = good.process(v)
+    binding.rfi_check(good.ctx)
+    want = RfiStream(6, 4, M, K, thr, "f32", lanes_per_row=1).process(v)
+    torch.cuda.synchronize()
+    for k in ("flags", "avg", "weight", "stats"):
+        assert torch.equal(out[k], want[k]), k
