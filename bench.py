@@ -220,7 +220,8 @@ def footprint_extras(torch, cs, peak, steps=500, warmup=10):
         sb = 32 if dtype == "f32" else 16
         for M, F in ((10, 2), (5, 4)):
             thr = default_thresholds(M * F)
-            best, _ = autotune.tune(62, 64, M, K, thr, dtype, vis, fixed={"window_F": F})
+            best, _ = autotune.tune(62, 64, M, K, thr, dtype, vis, fixed={"window_F": F},
+                                    cache_path=autotune.TUNED_PATH, write_cache=False)
             opts = autotune.options_of(best)
             st = RfiStream(62, 64, M, K, thr, dtype, **opts)
             out = st.alloc_outputs(T)
@@ -475,6 +476,7 @@ def main():
 
     import synth
     from paper_2412_14775_b300 import RfiStream, autotune, default_thresholds
+    from paper_2412_14775_b300.shard import aggregate
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -494,7 +496,8 @@ def main():
             f = [int(x) for x in args.tile.split(",")]
             keys = ["lanes_per_row", "warps_per_block", "prefetch_groups", "prefetch_bytes"]
             return dict(zip(keys, f))
-        best, _ = autotune.tune(62, 64, Mw, K, default_thresholds(Mw), dtype, vis)
+        best, _ = autotune.tune(62, 64, Mw, K, default_thresholds(Mw), dtype, vis,
+                                cache_path=autotune.TUNED_PATH, write_cache=False)
         return autotune.options_of(best)
 
     main_dt = args.dtype
@@ -509,12 +512,10 @@ def main():
         dist.barrier()
     total, per, clocks = time_kernel(st, vis_main, out, args.steps, args.warmup, torch, cs,
                                      sampler_index=local)
-    if ws > 1:
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
     samples = R * T
-    value = ws * samples * args.steps / total
+    # every rank processes its own block (weak scaling): total samples of all ranks over
+    # the slowest rank's time
+    _, total, value = aggregate(samples * args.steps, total)
     n_out = 1
     bytes_launch = algo_bytes(R, T, M, K, n_out, sbytes)
     kern = statistics.mean(per)

@@ -52,8 +52,11 @@ def time_options(stations, channels, M, K, thr, dtype, vis, reps=30, warmup=5, *
         st.close()
 
 
+TUNED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
 def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, verbose=False,
-         fixed=None):
+         fixed=None, write_cache=True):
     """Return (best_options, table) for this workload; coordinate search over the
     launch shape, then the prefetch distance and size.  `fixed` options (for example
     window_F) are part of every candidate."""
@@ -109,7 +112,7 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
                     best, best_t = o, t
     best = dict(best, seconds=best_t, **fixed)
     _MEM[key] = best
-    if cache_path:
+    if cache_path and write_cache:
         disk = {}
         if os.path.exists(cache_path):
             with open(cache_path) as f:
