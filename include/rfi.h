@@ -238,6 +238,17 @@ int rfi_process_block_noalloc(int stations, int channels, int window_M, int avg_
                               const void *vis, int T, uint32_t *flags, float *avg,
                               float *weight, float *stats, void *stream);
 
+/* Checkpoint and resume.  A stream's state is its sample count, thresholds and the
+ * per-lane running sums of every row's open averaging bin.  rfi_get_state
+ * synchronises `stream` and copies the state into a caller-owned host buffer of
+ * rfi_state_size bytes (a plain byte blob); rfi_set_state loads it into a context of
+ * the same geometry and launch shape (rows, lanes_per_row, M, K, window_F; else
+ * RFI_EINVAL), after which the stream continues exactly (bit for bit) where the saved
+ * one stopped. */
+int rfi_state_size(const rfi_ctx *ctx, size_t *bytes);
+int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream);
+int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes);
+
 /* Synchronise `stream` and report a device-side failure of work issued for the
  * context: RFI_ETIMEOUT when a bounded wait in the kernel gave up (the context then
  * stays failed until rfi_reset), RFI_OK otherwise. */

@@ -23,7 +23,8 @@ EXPORTED = ["rfi_create", "rfi_create_ex", "rfi_rows", "rfi_outputs_for", "rfi_g
             "rfi_set_thresholds", "rfi_process_block", "rfi_process_block_host",
             "rfi_process_batch", "rfi_batch_graph_create", "rfi_batch_graph_launch",
             "rfi_batch_graph_destroy", "rfi_reset", "rfi_destroy", "rfi_status_str",
-            "rfi_last_error", "rfi_process_block_noalloc", "rfi_check"]
+            "rfi_last_error", "rfi_process_block_noalloc", "rfi_check", "rfi_state_size",
+            "rfi_get_state", "rfi_set_state"]
 
 # Fixed size of the library's no-allocation scratch (RFI_NOALLOC_SCRATCH_BYTES).
 RFI_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -81,6 +82,9 @@ def load_library(path=None):
         "rfi_batch_graph_destroy": ([vp], ip),
         "rfi_reset": ([vp], ip),
         "rfi_check": ([vp, vp], ip),
+        "rfi_state_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ip),
+        "rfi_get_state": ([vp, vp, ctypes.c_size_t, vp], ip),
+        "rfi_set_state": ([vp, vp, ctypes.c_size_t], ip),
         "rfi_destroy": ([vp], ip),
         "rfi_process_block_noalloc": ([ip, ip, ip, ip, ctypes.POINTER(rfi_thresholds), ip,
                                        ctypes.c_longlong, vp, ip, vp, vp, vp, vp, vp], ip),
@@ -252,6 +256,25 @@ def rfi_process_block_noalloc(stations, channels, window_M, avg_K, thresholds, d
 
 def rfi_check(ctx, stream=None):
     _check(load_library().rfi_check(ctx, _stream(stream)), "rfi_check")
+
+
+def rfi_state_size(ctx):
+    n = ctypes.c_size_t()
+    _check(load_library().rfi_state_size(ctx, ctypes.byref(n)), "rfi_state_size")
+    return n.value
+
+
+def rfi_get_state(ctx, stream=None):
+    """The stream's state as bytes (synchronises the stream)."""
+    n = rfi_state_size(ctx)
+    buf = ctypes.create_string_buffer(n)
+    _check(load_library().rfi_get_state(ctx, buf, n, _stream(stream)), "rfi_get_state")
+    return buf.raw
+
+
+def rfi_set_state(ctx, state):
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    _check(load_library().rfi_set_state(ctx, buf, len(state)), "rfi_set_state")
 
 
 def rfi_reset(ctx):

@@ -821,6 +821,76 @@ int rfi_batch_graph_destroy(rfi_batch_graph *g) {
     return RFI_OK;
 }
 
+namespace {
+// Header of a saved stream state; followed by the carry, float[R][P][9].
+struct StateHeader {
+    unsigned int magic, version;
+    long long R, n_seen;
+    int P, M, K, F, dtype, pad;
+    rfi_thresholds thr;
+};
+constexpr unsigned int STATE_MAGIC = 0x52464953u;  // "RFIS"
+}  // namespace
+
+int rfi_state_size(const rfi_ctx *ctx, size_t *bytes) {
+    if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
+    if (!bytes) return fail(RFI_EINVAL, "null output");
+    *bytes = sizeof(StateHeader) + sizeof(float) * 9 * (size_t)ctx->P * ctx->R;
+    return RFI_OK;
+}
+
+int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    size_t need = 0;
+    rfi_state_size(ctx, &need);
+    if (!buf || bytes < need) return fail(RFI_EINVAL, "state buffer needs %zu bytes", need);
+    StateHeader h = {};
+    h.magic = STATE_MAGIC;
+    h.version = 1;
+    h.R = ctx->R;
+    h.n_seen = ctx->n_seen;
+    h.P = ctx->P;
+    h.M = ctx->M;
+    h.K = ctx->K;
+    h.F = ctx->F;
+    h.dtype = (int)ctx->dtype;
+    h.thr = ctx->thr;
+    std::memcpy(buf, &h, sizeof h);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(static_cast<char *>(buf) + sizeof h, ctx->carry, need - sizeof h,
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_get_state");
+    return RFI_OK;
+}
+
+int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    size_t need = 0;
+    rfi_state_size(ctx, &need);
+    if (!buf || bytes < need) return fail(RFI_EINVAL, "state buffer holds %zu of %zu bytes",
+                                          bytes, need);
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (h.magic != STATE_MAGIC || h.version != 1)
+        return fail(RFI_EINVAL, "not a saved stream state");
+    if (h.R != ctx->R || h.P != ctx->P || h.M != ctx->M || h.K != ctx->K || h.F != ctx->F)
+        return fail(RFI_EINVAL, "saved state is for another geometry or launch shape "
+                                "(rows %lld, lanes %d, M %d, K %d, F %d)",
+                    h.R, h.P, h.M, h.K, h.F);
+    if ((rc = check_thresholds(&h.thr))) return rc;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->carry, static_cast<const char *>(buf) + sizeof h, need - sizeof h,
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_set_state");
+    ctx->n_seen = h.n_seen;
+    ctx->thr = h.thr;
+    return RFI_OK;
+}
+
 int rfi_check(rfi_ctx *ctx, void *stream) {
     int rc;
     if ((rc = check_ctx(ctx))) return rc;

@@ -419,3 +419,56 @@ def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
     torch.cuda.synchronize()
     for k in ("flags", "avg", "weight", "stats"):
         assert torch.equal(out[k], want[k]), k
+
+
+def test_checkpoint_resume_bit_identical():
+    """Save a stream's state after a block whose last averaging bin is open, load it
+    into a new context, and continue: identical to the uninterrupted stream."""
+    M, K = 16, 96
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=50, stations=6, channels=5, T=256)["vis"]
+    blocks = [d[:, :, 0:64], d[:, :, 64:160], d[:, :, 160:256]]
+    ref = RfiStream(6, 5, M, K, thr, "f32")
+    want = [ref.process(to_device_rows(b, "f32")) for b in blocks]
+    a = RfiStream(6, 5, M, K, thr, "f32")
+    a.process(to_device_rows(blocks[0], "f32"))
+    state = binding.rfi_get_state(a.ctx)
+    assert len(state) == binding.rfi_state_size(a.ctx)
+    b = RfiStream(6, 5, M, K, dict(thr, s_low=-9.0), "f32")   # thresholds come with the state
+    binding.rfi_set_state(b.ctx, state)
+    assert binding.rfi_outputs_for(b.ctx, 96) == binding.rfi_outputs_for(a.ctx, 96)
+    for blk, w in zip(blocks[1:], want[1:]):
+        got = b.process(to_device_rows(blk, "f32"))
+        torch.cuda.synchronize()
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(got[k], w[k]), k
+    other = RfiStream(6, 5, M, 64, thr, "f32")                 # another K: refused
+    with pytest.raises(RfiError):
+        binding.rfi_set_state(other.ctx, state)
+    with pytest.raises(RfiError):
+        binding.rfi_set_state(other.ctx, state[:10])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_degenerate_thresholds_and_geometries(dtype):
+    """Every window flagged (averages 0, weight 0); nothing flagged (plain means); a
+    single-row stream; K spanning many blocks."""
+    M, K, T = 16, 64, 128
+    d = synth.tiny_block(seed=51, stations=3, channels=4, T=T)["vis"]
+    v = to_device_rows(d, dtype)
+    rows = d.reshape(-1, T, 8).astype(np.float16 if dtype == "f16" else np.float32)
+    every = dict(d=1.0, s_low=1e30, s_high=2e30, gamma=2.0, eps=2 ** -23)
+    o = RfiStream(3, 4, M, K, every, dtype).process(v)
+    torch.cuda.synchronize()
+    assert torch.all(o["flags"] == -1) and torch.all(o["weight"] == 0) and torch.all(o["avg"] == 0)
+    none = dict(d=1.0, s_low=-1e30, s_high=1e30, gamma=2.0, eps=2 ** -23)
+    o = RfiStream(3, 4, M, K, none, dtype).process(v)
+    torch.cuda.synchronize()
+    assert torch.all(o["flags"] == 0) and torch.all(o["weight"] == 1)
+    mean = rows.astype(np.float64).reshape(-1, T // K, K, 8).mean(axis=2)
+    got = o["avg"].cpu().numpy().reshape(-1, T // K, 8)
+    assert np.all(np.abs(got - mean) <= 1e-5 * np.maximum(np.abs(mean), 1.0))
+    # one station, one channel: a single row
+    _check_stream(1, 1, 16, 32, [64, 32], dtype)
+    # averaging bins of 512 samples over blocks of 48
+    _check_stream(2, 3, 16, 512, [48] * 12, dtype)
