@@ -41,13 +41,16 @@ def _peaks():
         return 6400.0, "fallback"
 
 
+KERNEL_SOURCES = ("rfi_device.cuh", "rfi_inst_f16.cu", "rfi_inst_f32.cu", "rfi_kernels.h")
+
+
 def kernel_source_hash():
-    """Hash of the CUDA sources; a profile's traffic figure is used only while the
-    sources it was taken from are unchanged."""
+    """Hash of the device code (kernel templates and their instances); a profile's
+    traffic figure is used only while the code it was taken from is unchanged."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2412_14775_b300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
