@@ -122,6 +122,14 @@ typedef enum {
  *   debug_inject_wait_timeout  1 = for testing failure detection only: the staged
  *                  loader expects 16 more bytes per stage than it copies, so every
  *                  stage wait gives up after about 1 ms and the error word is set.
+ *   buffered_stores  1 = each row keeps the statistics of 4 windows and 4 flag words
+ *                  in registers and writes them with one 16-byte store each (fewer
+ *                  store instructions for small windows).  Taken where T/M is a
+ *                  multiple of 4, the flag words of a row are too (M dividing 32) and
+ *                  the buffers are 16-byte aligned, else the plain stores run.  Needs
+ *                  the direct loader, float32 arithmetic, the 128-register budget, no
+ *                  Kahan, lanes_per_row <= 4 and 1, 2 or 4 load units per chunk.
+ *                  Results are identical.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -140,6 +148,7 @@ typedef struct {
     int tma_stage_windows;
     int tma_stages;
     int debug_inject_wait_timeout;
+    int buffered_stores;
 } rfi_options;
 
 /* Create a context for one stream of `stations` stations (B = N(N+1)/2 baselines)

@@ -1,8 +1,8 @@
 """Autotuner for the flagging kernel's launch shape.
 
 For one workload (dtype, M, K, T, rows) it times candidate options of rfi_create_ex
--- lanes per row P, warps per block, register budget, L2 prefetch group size and
-distance -- on the
+-- lanes per row P, warps per block, register budget, shared-memory staging,
+buffered output stores, L2 prefetch group size and distance -- on the
 caller's device data with CUDA events, and returns the fastest.  Results are cached
 in memory and, when `cache_path` is given, in a JSON file keyed by the workload.
 
@@ -101,6 +101,14 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
                 stage1.append((run(o), o))
             except B.RfiError:          # does not fit the shared memory
                 continue
+    stage1.sort(key=lambda x: x[0])
+    # the best direct-load shapes again with 16-byte buffered output stores
+    for _, base in [x for x in stage1 if x[1].get("loader", 0) == 0][:3]:
+        o = dict(base, buffered_stores=1)
+        try:
+            stage1.append((run(o), o))
+        except B.RfiError:              # no buffered variant of this shape
+            continue
     stage1.sort(key=lambda x: x[0])
     best_t, best = stage1[0]
     for _, base in stage1[:3]:

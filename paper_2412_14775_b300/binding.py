@@ -48,7 +48,8 @@ class rfi_options(ctypes.Structure):
                 ("prefetch_groups", ctypes.c_int), ("max_registers", ctypes.c_int),
                 ("window_F", ctypes.c_int), ("precision", ctypes.c_int),
                 ("loader", ctypes.c_int), ("tma_stage_windows", ctypes.c_int),
-                ("tma_stages", ctypes.c_int), ("debug_inject_wait_timeout", ctypes.c_int)]
+                ("tma_stages", ctypes.c_int), ("debug_inject_wait_timeout", ctypes.c_int),
+                ("buffered_stores", ctypes.c_int)]
 
 
 _lib = None

@@ -38,13 +38,14 @@ int fail(int status, const char *fmt, ...) {
 }
 
 // ---- kernel instances (rfi_inst_f32.cu, rfi_inst_f16.cu) ----------------------
-const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb, int mixed) {
+const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb, int mixed,
+                              int vs) {
     const InstanceTable tabs[] = {instances_f32(), instances_f16()};
     for (const InstanceTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const Instance &in = t.items[i];
             if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan &&
-                in.lb == lb && in.mixed == mixed)
+                in.lb == lb && in.mixed == mixed && in.vs == vs)
                 return &in;
         }
     return nullptr;
@@ -111,6 +112,7 @@ struct rfi_ctx {
     unsigned tma_pitch;
     size_t tma_smem;                    // dynamic shared memory per block
     int inject;                         // fault injection: stage waits cannot complete
+    int vs;                             // buffered 16-byte statistic and flag stores
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     const Instance *inst;
     long long n_seen;
@@ -232,7 +234,11 @@ int choose_shape(rfi_ctx *c, int P_req) {
     c->spu = spu;
     c->S = c->M / (P * spu);
     c->ch = largest_chunk(c->S);
-    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed);
+    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs);
+    if (c->vs && (!c->inst || c->loader != 0))
+        return fail(RFI_EUNSUPPORTED, "buffered_stores needs the direct loader, float32 "
+                                      "arithmetic, the 128-register budget, no Kahan, "
+                                      "lanes_per_row <= 4 and 1, 2 or 4 load units per chunk");
     if (c->loader == 1) {
         c->tma_fn = find_tma(dt, spu, c->ch, c->kahan);
         if (!c->tma_fn || c->mixed || c->lb != 0)
@@ -527,6 +533,7 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->tma_G = o.tma_stage_windows ? o.tma_stage_windows : 1;
     c->tma_NS = o.tma_stages ? o.tma_stages : 2;
     c->inject = o.debug_inject_wait_timeout;
+    c->vs = o.buffered_stores != 0;
     if (c->mixed) {
         if (o.compensated == 1 || c->lb != 0) {
             delete c;
@@ -641,6 +648,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->tma_stage_windows = ctx->tma_G;
     opt->tma_stages = ctx->tma_NS;
     opt->debug_inject_wait_timeout = ctx->inject;
+    opt->buffered_stores = ctx->vs;
     return RFI_OK;
 }
 

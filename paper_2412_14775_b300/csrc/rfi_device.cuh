@@ -321,8 +321,11 @@ __device__ __forceinline__ float rowsum(float v, int PF) {
 // TMA: every lane owns one row (P = 1) and reads it from shared memory, where the
 // warp's rows are staged a few windows at a time by cp.async.bulk copies (one per row,
 // issued by the row's lane) that complete on one mbarrier per stage.
+// VS: statistics and flag words buffered in registers and written 16 bytes at a time
+// (4 windows / 4 words) where the row layout allows; fewer, larger stores for small
+// windows at the price of 16 live registers.
 template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false,
-          bool TMA = false>
+          bool TMA = false, bool VS = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
     static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
     static_assert(!TMA || P == 1, "the shared-memory loader runs one lane per row");
@@ -367,6 +370,12 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     const int words_per_window = a.M >> 5;
     uint32_t fword = 0;
     int fbit = 0, fwi = 0;
+    const bool vec_stats = VS && (a.nwin & 3) == 0 && (a.stats_plane & 3) == 0 &&
+                           (reinterpret_cast<uintptr_t>(a.stats) & 15) == 0;
+    const bool vec_flags = VS && fmode == 0 && (a.Wpr & 3) == 0 && (a.T & 31) == 0 &&
+                           (reinterpret_cast<uintptr_t>(a.flags) & 15) == 0;
+    float4 tq = make_float4(0.f, 0.f, 0.f, 0.f), rq = tq, iq = tq;
+    uint4 fq = make_uint4(0u, 0u, 0u, 0u);
     // L2 prefetch: lane 0 of each row keeps pf_groups groups of pf_windows windows
     // requested ahead of the window being loaded.
     const bool pf = a.pf_groups > 0 && lead;
@@ -435,7 +444,16 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
                 !(r_im <= a.gamma);
         }
-        if (st_lead) {
+        if (vec_stats) {
+            tq = make_float4(tq.y, tq.z, tq.w, tau);
+            rq = make_float4(rq.y, rq.z, rq.w, r_re);
+            iq = make_float4(iq.y, iq.z, iq.w, r_im);
+            if ((w & 3) == 3 && st_lead) {
+                *reinterpret_cast<float4 *>(st_row + w - 3) = tq;
+                *reinterpret_cast<float4 *>(st_row + w - 3 + plane) = rq;
+                *reinterpret_cast<float4 *>(st_row + w - 3 + 2 * plane) = iq;
+            }
+        } else if (st_lead) {
             st_row[w] = tau;
             st_row[w + plane] = r_re;
             st_row[w + 2 * plane] = r_im;
@@ -445,7 +463,12 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             if (f) fword |= wmask << fbit;
             fbit += a.M;
             if (fbit == 32) {
-                if (lead) fl_row[fwi] = fword;
+                if (vec_flags) {
+                    fq = make_uint4(fq.y, fq.z, fq.w, fword);
+                    if ((fwi & 3) == 3 && lead) *reinterpret_cast<uint4 *>(fl_row + fwi - 3) = fq;
+                } else if (lead) {
+                    fl_row[fwi] = fword;
+                }
                 ++fwi;
                 fword = 0;
                 fbit = 0;
@@ -620,14 +643,15 @@ template <> struct Bounds<0> { static constexpr int threads = 512, blocks = 1; }
 template <> struct Bounds<1> { static constexpr int threads = 256, blocks = 3; };
 template <> struct Bounds<2> { static constexpr int threads = 256, blocks = 4; };
 
-template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, bool MIXED = false>
+template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, bool MIXED = false,
+          bool VS = false>
 __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_block(const __grid_constant__ StreamArgs a) {
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     // the 128-register budget keeps two chunks in flight; tighter budgets load one
     // chunk at a time and rely on more resident warps instead
-    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED>(a, group);
+    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS>(a, group);
 }
 
 // One lane per row, rows staged in shared memory by TMA bulk copies; dynamic shared

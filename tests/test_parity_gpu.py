@@ -118,6 +118,13 @@ SHAPES = [
     ("f32", 6, 3, 20, 40, [40, 60, 100], {"loader": 1, "tma_stages": 1, "warps_per_block": 2}),
     ("f16", 5, 4, 10, 20, [20, 40], {"loader": 1, "window_F": 2}),
     ("f32", 5, 4, 64, 128, [128, 64, 192], {"loader": 1}),
+    # statistics and flag words written 16 bytes at a time (falls back to plain
+    # stores where T/M or the flag words per row are not multiples of 4)
+    ("f16", 5, 4, 8, 32, [128, 64, 32], {"buffered_stores": 1, "lanes_per_row": 2}),
+    ("f32", 4, 5, 8, 16, [64, 40], {"buffered_stores": 1, "lanes_per_row": 4}),
+    ("f16", 4, 6, 16, 64, [512, 192], {"buffered_stores": 1}),
+    ("f32", 5, 4, 4, 8, [128, 8, 256], {"buffered_stores": 1, "lanes_per_row": 1}),
+    ("f32", 5, 4, 8, 16, [64, 32], {"buffered_stores": 1, "window_F": 2}),
 ]
 
 
@@ -394,6 +401,25 @@ def test_tma_loader_bit_identical_to_direct_loads():
         torch.cuda.synchronize()
         for k in ("flags", "avg", "weight", "stats"):
             assert torch.equal(a[k], b[k]), (dtype, k)
+
+
+def test_buffered_stores_bit_identical_to_plain_stores():
+    """Buffering four windows' outputs per store changes only how they are written."""
+    thr8 = default_thresholds(8)
+    d = synth.tiny_block(seed=37, stations=10, channels=13, T=512)["vis"]
+    for dtype, P in (("f32", 2), ("f32", 4), ("f16", 2), ("f16", 1)):
+        v = to_device_rows(d, dtype)
+        a = RfiStream(10, 13, 8, 64, thr8, dtype, lanes_per_row=P).process(v)
+        st = RfiStream(10, 13, 8, 64, thr8, dtype, lanes_per_row=P, buffered_stores=1)
+        assert st.options["buffered_stores"] == 1
+        b = st.process(v)
+        torch.cuda.synchronize()
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(a[k], b[k]), (dtype, P, k)
+    with pytest.raises(binding.RfiError):      # no buffered variant of the staged loader
+        RfiStream(4, 4, 8, 64, thr8, "f32", loader=1, buffered_stores=1)
+    with pytest.raises(binding.RfiError):      # nor of the reduced register budgets
+        RfiStream(4, 4, 8, 64, thr8, "f32", max_registers=64, buffered_stores=1)
 
 
 def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
