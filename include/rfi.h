@@ -130,6 +130,17 @@ typedef enum {
  *                  the direct loader, float32 arithmetic, the 128-register budget, no
  *                  Kahan, lanes_per_row <= 4 and 1, 2 or 4 load units per chunk.
  *                  Results are identical.
+ *   partial_windows  1 = blocks of any length T (even T for binary16 input with even
+ *                  M): a window that a block leaves open is completed by the next
+ *                  block(s).  Its raw samples wait in a device buffer of the context
+ *                  (R M samples, allocated here), and its flags, statistics and the
+ *                  averages it completes are returned by the call that completes it,
+ *                  so a call's outputs cover the windows it completes (rfi_windows_for)
+ *                  and may start up to M-1 samples before its block.  Results are bit
+ *                  identical to any other split of the stream, including one block.
+ *                  Needs the direct loader, float32 arithmetic, the 128-register
+ *                  budget and plain stores (kernel instances of their own, so the
+ *                  others carry no cost).  0 = T must be a multiple of M (default).
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -149,6 +160,7 @@ typedef struct {
     int tma_stages;
     int debug_inject_wait_timeout;
     int buffered_stores;
+    int partial_windows;
 } rfi_options;
 
 /* Create a context for one stream of `stations` stations (B = N(N+1)/2 baselines)
@@ -168,24 +180,36 @@ int rfi_rows(const rfi_ctx *ctx, long long *rows);
  * the number of samples already processed. */
 int rfi_outputs_for(const rfi_ctx *ctx, int T, int *n_out);
 
+/* Windows the next rfi_process_block with T samples will complete, n_win: the call
+ * returns n_win statistics per row (footprint) and n_win M flag bits per row, bit i
+ * for stream sample *first_sample + i (first_sample may be NULL).  Without
+ * partial_windows, n_win = T/M and first_sample = n_seen.  With it, a window left
+ * open by earlier blocks is completed first: n_win = (n_seen mod M + T) / M and
+ * first_sample = n_seen - n_seen mod M (Sec. 2: windows of consecutive samples of a
+ * stream, whatever the correlator's block length). */
+int rfi_windows_for(const rfi_ctx *ctx, int T, int *n_win, long long *first_sample);
+
 /* The launch shape the context uses (after automatic choice). */
 int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt);
 
 /* Replace the thresholds (takes effect for work issued afterwards). */
 int rfi_set_thresholds(rfi_ctx *ctx, const rfi_thresholds *thr);
 
-/* Process one block of T samples (T a positive multiple of M) of every row.
+/* Process one block of T samples (T a positive multiple of M, or any T with
+ * partial_windows) of every row.  n_win = rfi_windows_for(T) windows complete.
  *   vis    [R][T][4 correlations][re, im] in the context's dtype; 32-byte aligned.
- *   flags  [R][ceil(T/32)] uint32: bit (t mod 32) of word t/32 is 1 when sample t
- *          of the row lies in a flagged window (the flag applies to all 4
- *          correlations).  Bits at t >= T are 0.  4-byte aligned.
+ *   flags  [R][ceil(n_win M/32)] uint32: bit (t mod 32) of word t/32 is 1 when sample
+ *          t of the completed windows (t = 0 at first_sample; the block's own sample 0
+ *          unless a window was open) lies in a flagged window (the flag applies to
+ *          all 4 correlations).  Bits at t >= n_win M are 0.  4-byte aligned.
  *   avg    [R][n_out][4][re, im] float32: mean of the unflagged samples of every
  *          averaging bin that completes in this call (n_out = rfi_outputs_for);
  *          0 where every sample of the bin was flagged.  16-byte aligned.
  *   weight [R][n_out] float32: unflagged samples of the bin / K.
- *   stats  [3][R/F][T/M] float32: tau, r_Re, r_Im of every window (SoA; F = 1
- *          unless the context has a T x F footprint).
- * avg and weight may be NULL only when n_out == 0.  Asynchronous on `stream`. */
+ *   stats  [3][R/F][n_win] float32: tau, r_Re, r_Im of every completed window (SoA;
+ *          F = 1 unless the context has a T x F footprint).
+ * avg and weight may be NULL only when n_out == 0, flags and stats only when n_win ==
+ * 0.  Asynchronous on `stream`. */
 int rfi_process_block(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags, float *avg,
                       float *weight, float *stats, void *stream);
 
@@ -248,10 +272,12 @@ int rfi_process_block_noalloc(int stations, int channels, int window_M, int avg_
                               float *weight, float *stats, void *stream);
 
 /* Checkpoint and resume.  A stream's state is its sample count, thresholds and the
- * per-lane running sums of every row's open averaging bin.  rfi_get_state
+ * per-lane running sums of every row's open averaging bin (and, with
+ * partial_windows, the raw samples of every row's open window).  rfi_get_state
  * synchronises `stream` and copies the state into a caller-owned host buffer of
  * rfi_state_size bytes (a plain byte blob); rfi_set_state loads it into a context of
- * the same geometry and launch shape (rows, lanes_per_row, M, K, window_F; else
+ * the same geometry and launch shape (rows, lanes_per_row, M, K, window_F, dtype,
+ * partial_windows; else
  * RFI_EINVAL), after which the stream continues exactly (bit for bit) where the saved
  * one stopped. */
 int rfi_state_size(const rfi_ctx *ctx, size_t *bytes);

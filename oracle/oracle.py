@@ -122,10 +122,14 @@ class OracleStream:
 
     Holds the open averaging bin of every row between blocks, exactly (float64),
     so that any split of the stream at multiples of the window gives the same
-    results as one long block.
+    results as one long block.  With `partial`, blocks may have any length: the
+    samples after a block's last whole window are kept and put in front of the next
+    block, so every window is evaluated whole, on consecutive samples of the stream
+    (Sec. 2), and a call reports the windows it completes.
     """
 
-    def __init__(self, R, M, K, d, s_low, s_high, gamma, eps, compensated=False, F=1):
+    def __init__(self, R, M, K, d, s_low, s_high, gamma, eps, compensated=False, F=1,
+                 partial=False):
         """M: samples per row in a window; F: adjacent rows (channels) per window, so
         a window holds W = M * F samples; R must be a multiple of F."""
         if M * F < 2 or K % M != 0 or R % F != 0:
@@ -136,22 +140,40 @@ class OracleStream:
         self.n_seen = 0
         self.carry_sum = np.zeros((self.R, 8))
         self.carry_cnt = np.zeros(self.R)
+        self.partial = bool(partial)
+        self.pending = np.zeros((self.R, 0, 8))     # samples of the open window
 
     def outputs_for(self, T):
-        return outputs_for(self.n_seen, T, self.K)
+        """Averaging bins completed by the next block of T samples (bins end at window
+        ends, so the samples of an open window do not change this count)."""
+        return outputs_for(self.n_seen + self.pending.shape[1], T, self.K)
+
+    def windows_for(self, T):
+        """(windows completed, stream index of their first sample) for T samples."""
+        return (self.pending.shape[1] + T) // self.M, self.n_seen
 
     def process(self, vis):
         """Process one block; vis is any layout accepted by to_f64_rows with R rows."""
         v = to_f64_rows(vis)
-        R, T = v.shape[0], v.shape[1]
+        R = v.shape[0]
         if R != self.R:
             raise ValueError(f"expected {self.R} rows, got {R}")
+        if self.partial:
+            v = np.concatenate([self.pending, v], axis=1)
+            whole = (v.shape[1] // self.M) * self.M
+            v, self.pending = np.ascontiguousarray(v[:, :whole]), v[:, whole:].copy()
+        T = v.shape[1]
         if T % self.M != 0:
             raise ValueError("T must be a multiple of M")
         nw = T // self.M
         nwords = (T + 31) // 32
         n_out = self.outputs_for(T)
         G = R // self.F
+        if T == 0:          # the block only extends the open window
+            return dict(tau=np.zeros((G, 0)), r_re=np.zeros((G, 0)), r_im=np.zeros((G, 0)),
+                        wflag=np.zeros((G, 0), dtype=np.uint8),
+                        flagbits=np.zeros((R, 0), dtype=np.uint32),
+                        avg=np.zeros((R, 0, 8)), weight=np.zeros((R, 0)))
         out = dict(
             tau=np.zeros((G, nw)), r_re=np.zeros((G, nw)), r_im=np.zeros((G, nw)),
             wflag=np.zeros((G, nw), dtype=np.uint8),

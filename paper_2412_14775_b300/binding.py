@@ -24,7 +24,7 @@ EXPORTED = ["rfi_create", "rfi_create_ex", "rfi_rows", "rfi_outputs_for", "rfi_g
             "rfi_process_batch", "rfi_batch_graph_create", "rfi_batch_graph_launch",
             "rfi_batch_graph_destroy", "rfi_reset", "rfi_destroy", "rfi_status_str",
             "rfi_last_error", "rfi_process_block_noalloc", "rfi_check", "rfi_state_size",
-            "rfi_get_state", "rfi_set_state"]
+            "rfi_get_state", "rfi_set_state", "rfi_windows_for"]
 
 # Fixed size of the library's no-allocation scratch (RFI_NOALLOC_SCRATCH_BYTES).
 RFI_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -49,7 +49,7 @@ class rfi_options(ctypes.Structure):
                 ("window_F", ctypes.c_int), ("precision", ctypes.c_int),
                 ("loader", ctypes.c_int), ("tma_stage_windows", ctypes.c_int),
                 ("tma_stages", ctypes.c_int), ("debug_inject_wait_timeout", ctypes.c_int),
-                ("buffered_stores", ctypes.c_int)]
+                ("buffered_stores", ctypes.c_int), ("partial_windows", ctypes.c_int)]
 
 
 _lib = None
@@ -73,6 +73,7 @@ def load_library(path=None):
                            ctypes.POINTER(rfi_options)], ip),
         "rfi_rows": ([vp, ctypes.POINTER(ctypes.c_longlong)], ip),
         "rfi_outputs_for": ([vp, ip, ctypes.POINTER(ip)], ip),
+        "rfi_windows_for": ([vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_longlong)], ip),
         "rfi_get_options": ([vp, ctypes.POINTER(rfi_options)], ip),
         "rfi_set_thresholds": ([vp, ctypes.POINTER(rfi_thresholds)], ip),
         "rfi_process_block": ([vp, vp, ip, vp, vp, vp, vp, vp], ip),
@@ -181,6 +182,16 @@ def rfi_outputs_for(ctx, T):
     n = ctypes.c_int()
     _check(load_library().rfi_outputs_for(ctx, T, ctypes.byref(n)), "rfi_outputs_for")
     return n.value
+
+
+def rfi_windows_for(ctx, T):
+    """(n_win, first_sample): windows the next block of T samples completes and the
+    stream index of the first sample they cover."""
+    n = ctypes.c_int()
+    first = ctypes.c_longlong()
+    _check(load_library().rfi_windows_for(ctx, T, ctypes.byref(n), ctypes.byref(first)),
+           "rfi_windows_for")
+    return n.value, first.value
 
 
 def rfi_get_options(ctx):

@@ -39,13 +39,14 @@ int fail(int status, const char *fmt, ...) {
 
 // ---- kernel instances (rfi_inst_f32.cu, rfi_inst_f16.cu) ----------------------
 const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb, int mixed,
-                              int vs) {
-    const InstanceTable tabs[] = {instances_f32(), instances_f16()};
+                              int vs, int pw) {
+    const InstanceTable tabs[] = {instances_f32(), instances_f16(), instances_f32_pw(),
+                                  instances_f16_pw()};
     for (const InstanceTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const Instance &in = t.items[i];
             if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan &&
-                in.lb == lb && in.mixed == mixed && in.vs == vs)
+                in.lb == lb && in.mixed == mixed && in.vs == vs && in.pw == pw)
                 return &in;
         }
     return nullptr;
@@ -113,6 +114,8 @@ struct rfi_ctx {
     size_t tma_smem;                    // dynamic shared memory per block
     int inject;                         // fault injection: stage waits cannot complete
     int vs;                             // buffered 16-byte statistic and flag stores
+    int pw;                             // partial windows: any T, open window carried
+    char *hw;                           // [R][M] raw samples of each row's open window
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     const Instance *inst;
     long long n_seen;
@@ -234,7 +237,10 @@ int choose_shape(rfi_ctx *c, int P_req) {
     c->spu = spu;
     c->S = c->M / (P * spu);
     c->ch = largest_chunk(c->S);
-    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs);
+    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs, c->pw);
+    if (c->pw && !c->inst)
+        return fail(RFI_EUNSUPPORTED, "partial_windows needs the 128-register budget and "
+                                      "float32 arithmetic, without buffered_stores");
     if (c->vs && (!c->inst || c->loader != 0))
         return fail(RFI_EUNSUPPORTED, "buffered_stores needs the direct loader, float32 "
                                       "arithmetic, the 128-register budget, no Kahan, "
@@ -265,11 +271,16 @@ int choose_shape(rfi_ctx *c, int P_req) {
     return RFI_OK;
 }
 
+// Samples of the open window carried into the next block, and the windows (hence
+// statistics columns and M nwin flag bits) a block of T samples completes.
+int phase_of(const rfi_ctx *c) { return c->pw ? (int)(c->n_seen % c->M) : 0; }
+int windows_for(const rfi_ctx *c, int T) { return (phase_of(c) + T) / c->M; }
+
 StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, float *avg,
                      float *weight, float *stats, long long r0, long long nrows) {
-    StreamArgs a;
-    const int nwin = T / c->M;
-    const int Wpr = (T + 31) / 32;
+    StreamArgs a = {};
+    const int nwin = windows_for(c, T);
+    const int Wpr = (nwin * c->M + 31) / 32;
     const long long n_out = (c->n_seen + T) / c->K - c->n_seen / c->K;
     a.vis = static_cast<const char *>(vis) + r0 * (long long)T * sample_bytes(c->dtype);
     a.flags = flags + r0 * Wpr;
@@ -277,6 +288,8 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.weight = weight ? weight + r0 * n_out : nullptr;
     a.stats = stats + (r0 / c->F) * nwin;     // r0 is a multiple of F
     a.carry = c->carry + r0 * c->P * 9;
+    a.hw = c->hw ? c->hw + r0 * c->M * sample_bytes(c->dtype) : nullptr;
+    a.phase = phase_of(c);
     a.R = nrows;
     a.stats_plane = (c->R / c->F) * nwin;
     a.F = c->F;
@@ -293,7 +306,8 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.Wpr = Wpr;
     a.nwin = nwin;
     a.n_out = (int)n_out;
-    a.bin_pos0 = (int)(c->n_seen % c->K);
+    // samples of the open bin before window 0 (which may itself start in an earlier block)
+    a.bin_pos0 = (int)((c->n_seen - a.phase) % c->K);
     const double Md = (double)c->M * c->F;     // W = M F samples per window
     a.c0 = (float)((Md * c->thr.d + 1.0) / (Md - 1.0));
     a.s_low = (float)c->thr.s_low;
@@ -309,18 +323,31 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     return a;
 }
 
+int check_T(const rfi_ctx *c, int T) {
+    if (c->pw) {
+        if (T <= 0) return fail(RFI_EINVAL, "T=%d must be positive", T);
+        if (T % c->spu != 0)
+            return fail(RFI_EINVAL, "T=%d must be even (binary16 samples are loaded in pairs)", T);
+        return RFI_OK;
+    }
+    if (T <= 0 || T % c->M != 0)
+        return fail(RFI_EINVAL, "T=%d must be a positive multiple of M=%d (or create the "
+                                "context with partial_windows = 1)", T, c->M);
+    return RFI_OK;
+}
+
 int check_block_args(const rfi_ctx *c, const void *vis, int T, const uint32_t *flags,
                      const float *avg, const float *weight, const float *stats, bool device) {
-    if (T <= 0 || T % c->M != 0)
-        return fail(RFI_EINVAL, "T=%d must be a positive multiple of M=%d", T, c->M);
+    int rc0;
+    if ((rc0 = check_T(c, T))) return rc0;
     if ((long long)T * c->R > (1ll << 40)) return fail(RFI_EINVAL, "block too large");
     const long long n_out = (c->n_seen + T) / c->K - c->n_seen / c->K;
     const size_t sb = sample_bytes(c->dtype);
     const size_t vis_align = (size_t)sb * c->spu;
     const size_t R = (size_t)c->R;
-    const size_t nw = T / c->M, wpr = (T + 31) / 32;
+    const size_t nw = windows_for(c, T), wpr = (nw * c->M + 31) / 32;
     if (!device) {
-        if (!vis || !flags || !stats || (n_out > 0 && (!avg || !weight)))
+        if (!vis || (nw > 0 && (!flags || !stats)) || (n_out > 0 && (!avg || !weight)))
             return fail(RFI_EINVAL, "null host buffer");
         return RFI_OK;
     }
@@ -421,8 +448,7 @@ int build_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *
                 return rc;
             b->s[i] = make_args(c, vis[i], T[i], flags[i], avg[i], weight[i], stats[i], 0, c->R);
         } else {
-            if (T[i] <= 0 || T[i] % c->M != 0)
-                return fail(RFI_EINVAL, "T[%d]=%d must be a positive multiple of M", i, T[i]);
+            if ((rc = check_T(c, T[i]))) return rc;
             b->s[i] = make_args(c, nullptr, T[i], nullptr, nullptr, nullptr, nullptr, 0, c->R);
         }
         b->prefix[i] = tot;
@@ -438,6 +464,7 @@ void free_ctx(rfi_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->carry) cudaFree(c->carry);
+    if (c->hw) cudaFree(c->hw);
     if (c->counter) cudaFree(c->counter);
     if (c->h_vis) cudaFree(c->h_vis);
     if (c->h_flags) cudaFree(c->h_flags);
@@ -534,6 +561,11 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->tma_NS = o.tma_stages ? o.tma_stages : 2;
     c->inject = o.debug_inject_wait_timeout;
     c->vs = o.buffered_stores != 0;
+    c->pw = o.partial_windows != 0;
+    if (c->pw && c->loader != 0) {
+        delete c;
+        return fail(RFI_EUNSUPPORTED, "partial_windows needs the direct loader (loader = 0)");
+    }
     if (c->mixed) {
         if (o.compensated == 1 || c->lb != 0) {
             delete c;
@@ -561,7 +593,9 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     if ((e = cudaMalloc(&c->carry, sizeof(float) * 9 * (size_t)c->P * c->R)) != cudaSuccess ||
         (e = cudaMalloc(&c->counter, 4 * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMemset(c->carry, 0, sizeof(float) * 9 * (size_t)c->P * c->R)) != cudaSuccess ||
-        (e = cudaMemset(c->counter, 0, 4 * sizeof(unsigned long long))) != cudaSuccess) {
+        (e = cudaMemset(c->counter, 0, 4 * sizeof(unsigned long long))) != cudaSuccess ||
+        (c->pw && (e = cudaMalloc(&c->hw, (size_t)c->R * c->M * sample_bytes(dtype))) !=
+                      cudaSuccess)) {
         cudaGetLastError();
         free_ctx(c);
         return fail(e == cudaErrorMemoryAllocation ? RFI_ENOMEM : RFI_ECUDA,
@@ -570,19 +604,21 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->host_max_T = o.host_max_T;
     c->host_chunks = o.host_chunks ? o.host_chunks : 4;
     if (c->host_max_T > 0) {
-        const int T = c->host_max_T - c->host_max_T % c->M;
-        if (T < c->M) {
+        const int T = c->pw ? c->host_max_T : c->host_max_T - c->host_max_T % c->M;
+        if (T < (c->pw ? 1 : c->M)) {
             free_ctx(c);
             return fail(RFI_EINVAL, "host_max_T smaller than M");
         }
         c->host_max_T = T;
         const size_t R = (size_t)c->R;
         const size_t n_out_max = (size_t)T / c->K + 1;
+        // a carried partial window adds at most one completed window per block
+        const size_t nw_max = (size_t)(T + (c->pw ? c->M - 1 : 0)) / c->M;
         bool ok = cudaMalloc(&c->h_vis, R * T * sample_bytes(dtype)) == cudaSuccess &&
-                  cudaMalloc(&c->h_flags, R * ((T + 31) / 32) * 4) == cudaSuccess &&
+                  cudaMalloc(&c->h_flags, R * ((nw_max * c->M + 31) / 32) * 4) == cudaSuccess &&
                   cudaMalloc(&c->h_avg, R * n_out_max * 32) == cudaSuccess &&
                   cudaMalloc(&c->h_weight, R * n_out_max * 4) == cudaSuccess &&
-                  cudaMalloc(&c->h_stats, 3 * R * (T / c->M) * 4) == cudaSuccess &&
+                  cudaMalloc(&c->h_stats, 3 * R * nw_max * 4) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&c->s_run, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking) == cudaSuccess &&
@@ -626,8 +662,19 @@ int rfi_rows(const rfi_ctx *ctx, long long *rows) {
 int rfi_outputs_for(const rfi_ctx *ctx, int T, int *n_out) {
     if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
     if (!n_out) return fail(RFI_EINVAL, "null output");
-    if (T < 0 || T % ctx->M != 0) return fail(RFI_EINVAL, "T must be a multiple of M");
+    if (T < 0 || (!ctx->pw && T % ctx->M != 0))
+        return fail(RFI_EINVAL, "T must be a multiple of M");
     *n_out = (int)((ctx->n_seen + T) / ctx->K - ctx->n_seen / ctx->K);
+    return RFI_OK;
+}
+
+int rfi_windows_for(const rfi_ctx *ctx, int T, int *n_win, long long *first_sample) {
+    if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
+    if (!n_win) return fail(RFI_EINVAL, "null output");
+    if (T < 0 || (!ctx->pw && T % ctx->M != 0))
+        return fail(RFI_EINVAL, "T must be a multiple of M");
+    *n_win = windows_for(ctx, T);
+    if (first_sample) *first_sample = ctx->n_seen - phase_of(ctx);
     return RFI_OK;
 }
 
@@ -649,6 +696,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->tma_stages = ctx->tma_NS;
     opt->debug_inject_wait_timeout = ctx->inject;
     opt->buffered_stores = ctx->vs;
+    opt->partial_windows = ctx->pw;
     return RFI_OK;
 }
 
@@ -681,7 +729,7 @@ int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     const long long R = ctx->R;
     const int nch = (int)std::min<long long>(ctx->host_chunks, R);
-    const int nwin = T / ctx->M, wpr = (T + 31) / 32;
+    const int nwin = windows_for(ctx, T), wpr = (nwin * ctx->M + 31) / 32;
     const long long n_out = (ctx->n_seen + T) / ctx->K - ctx->n_seen / ctx->K;
     const size_t sb = sample_bytes(ctx->dtype);
     cudaError_t e;
@@ -705,10 +753,10 @@ int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags
         if ((rc = launch_block(ctx, a, ctx->s_run))) return rc;
         e = cudaEventRecord(ctx->ev_run[k], ctx->s_run);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_run[k], 0);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && nwin > 0)
             e = cudaMemcpyAsync(flags + r0 * wpr, ctx->h_flags + r0 * wpr, nr * wpr * 4,
                                 cudaMemcpyDeviceToHost, ctx->s_out);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && nwin > 0)
             e = cudaMemcpy2DAsync(stats + (r0 / F) * nwin, (size_t)(R / F) * nwin * 4,
                                   ctx->h_stats + (r0 / F) * nwin, (size_t)(R / F) * nwin * 4,
                                   (nr / F) * nwin * 4, 3, cudaMemcpyDeviceToHost, ctx->s_out);
@@ -830,20 +878,25 @@ int rfi_batch_graph_destroy(rfi_batch_graph *g) {
 }
 
 namespace {
-// Header of a saved stream state; followed by the carry, float[R][P][9].
+// Header of a saved stream state; followed by the carry, float[R][P][9], and, for
+// contexts with partial windows, the raw samples of the open windows, [R][M] samples.
 struct StateHeader {
     unsigned int magic, version;
     long long R, n_seen;
-    int P, M, K, F, dtype, pad;
+    int P, M, K, F, dtype, pw;
     rfi_thresholds thr;
 };
+size_t carry_bytes(const rfi_ctx *c) { return sizeof(float) * 9 * (size_t)c->P * c->R; }
+size_t hw_bytes(const rfi_ctx *c) {
+    return c->pw ? (size_t)c->R * c->M * sample_bytes(c->dtype) : 0;
+}
 constexpr unsigned int STATE_MAGIC = 0x52464953u;  // "RFIS"
 }  // namespace
 
 int rfi_state_size(const rfi_ctx *ctx, size_t *bytes) {
     if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
     if (!bytes) return fail(RFI_EINVAL, "null output");
-    *bytes = sizeof(StateHeader) + sizeof(float) * 9 * (size_t)ctx->P * ctx->R;
+    *bytes = sizeof(StateHeader) + carry_bytes(ctx) + hw_bytes(ctx);
     return RFI_OK;
 }
 
@@ -855,7 +908,8 @@ int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream) {
     if (!buf || bytes < need) return fail(RFI_EINVAL, "state buffer needs %zu bytes", need);
     StateHeader h = {};
     h.magic = STATE_MAGIC;
-    h.version = 1;
+    h.version = 2;
+    h.pw = ctx->pw;
     h.R = ctx->R;
     h.n_seen = ctx->n_seen;
     h.P = ctx->P;
@@ -866,9 +920,11 @@ int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream) {
     h.thr = ctx->thr;
     std::memcpy(buf, &h, sizeof h);
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    char *dst = static_cast<char *>(buf) + sizeof h;
     if (e == cudaSuccess)
-        e = cudaMemcpy(static_cast<char *>(buf) + sizeof h, ctx->carry, need - sizeof h,
-                       cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(dst, ctx->carry, carry_bytes(ctx), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ctx->pw)
+        e = cudaMemcpy(dst + carry_bytes(ctx), ctx->hw, hw_bytes(ctx), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_get_state");
     return RFI_OK;
 }
@@ -882,17 +938,20 @@ int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes) {
                                           bytes, need);
     StateHeader h;
     std::memcpy(&h, buf, sizeof h);
-    if (h.magic != STATE_MAGIC || h.version != 1)
+    if (h.magic != STATE_MAGIC || h.version != 2)
         return fail(RFI_EINVAL, "not a saved stream state");
-    if (h.R != ctx->R || h.P != ctx->P || h.M != ctx->M || h.K != ctx->K || h.F != ctx->F)
+    if (h.R != ctx->R || h.P != ctx->P || h.M != ctx->M || h.K != ctx->K || h.F != ctx->F ||
+        h.pw != ctx->pw || h.dtype != (int)ctx->dtype)
         return fail(RFI_EINVAL, "saved state is for another geometry or launch shape "
-                                "(rows %lld, lanes %d, M %d, K %d, F %d)",
-                    h.R, h.P, h.M, h.K, h.F);
+                                "(rows %lld, lanes %d, M %d, K %d, F %d, partial windows %d)",
+                    h.R, h.P, h.M, h.K, h.F, h.pw);
     if ((rc = check_thresholds(&h.thr))) return rc;
     cudaError_t e = cudaDeviceSynchronize();
+    const char *src = static_cast<const char *>(buf) + sizeof h;
     if (e == cudaSuccess)
-        e = cudaMemcpy(ctx->carry, static_cast<const char *>(buf) + sizeof h, need - sizeof h,
-                       cudaMemcpyHostToDevice);
+        e = cudaMemcpy(ctx->carry, src, carry_bytes(ctx), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ctx->pw)
+        e = cudaMemcpy(ctx->hw, src + carry_bytes(ctx), hw_bytes(ctx), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_set_state");
     ctx->n_seen = h.n_seen;
     ctx->thr = h.thr;

@@ -39,7 +39,7 @@ struct StreamArgs {
     long long R;            // rows in this launch
     long long stats_plane;  // floats between the tau, r_Re and r_Im planes
     int T, M, K, Wpr, nwin, n_out;
-    int bin_pos0;           // samples of the open bin consumed before this block
+    int bin_pos0;           // samples of the open bin before window 0 of this launch
     int F;                  // adjacent rows (channels) per window footprint (power of 2)
     float d;                // SK shape parameter (used by the mixed-precision mode)
     int pf_windows;         // windows per L2 prefetch group (>= 1)
@@ -56,6 +56,10 @@ struct StreamArgs {
     float fM;               // W = M F as float (samples in one window)
     float fK;
     float invM;             // 1/W (exact when W is a power of two)
+    // partial windows: a window may begin in an earlier block; its first `phase`
+    // samples wait in hw, and the samples after this block's last whole window go there
+    char *hw;               // [R][M] raw samples of each row's open window (or null)
+    int phase;              // samples of window 0 already in hw (0 <= phase < M)
 };
 
 struct BatchArgs {
@@ -145,6 +149,20 @@ __device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
     asm("ld.global.nc.L1::no_allocate.v4.b32 {%0,%1,%2,%3}, [%4];"
         : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3])
         : "l"(p));
+}
+
+// The raw-sample carry of partial windows is read, then rewritten, by the same launch:
+// coherent loads, ordered before the later stores.
+__device__ __forceinline__ void load_unit_rw(const char *p, Unit<32> &u) {
+    asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3]),
+                   "=r"(u.r[4]), "=r"(u.r[5]), "=r"(u.r[6]), "=r"(u.r[7])
+                 : "l"(p) : "memory");
+}
+__device__ __forceinline__ void load_unit_rw(const char *p, Unit<16> &u) {
+    asm volatile("ld.global.v4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3])
+                 : "l"(p) : "memory");
 }
 
 __device__ __forceinline__ void load_unit_smem(const unsigned char *p, Unit<32> &u) {
@@ -324,8 +342,12 @@ __device__ __forceinline__ float rowsum(float v, int PF) {
 // VS: statistics and flag words buffered in registers and written 16 bytes at a time
 // (4 windows / 4 words) where the row layout allows; fewer, larger stores for small
 // windows at the price of 16 live registers.
+// PW: partial windows.  Window 0 may have begun in an earlier block (its first
+// `phase` samples wait in the raw-sample carry), and the samples after the last whole
+// window are put there for the next block.  A separate instance, so that the code of
+// the head window and the tail copy does not cost the kernels that need neither.
 template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false,
-          bool TMA = false, bool VS = false>
+          bool TMA = false, bool VS = false, bool PW = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
     static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
     static_assert(!TMA || P == 1, "the shared-memory loader runs one lane per row");
@@ -339,6 +361,11 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     const long long rowc = active ? row : a.R - 1;  // inactive lanes re-read a valid row
     const int S = a.M / (P * SPU);                  // load units per lane per window
     const char *rp = static_cast<const char *>(a.vis) + rowc * (long long)a.T * SB;
+    // window frame: sample 0 of window 0, `phase` samples before the block's first
+    const char *fp = PW ? rp - (long long)a.phase * SB : rp;
+    const bool head = PW && a.phase > 0 && a.nwin > 0;  // window 0 starts in the carry
+    char *const hwp = PW ? a.hw + rowc * (long long)a.M * SB : nullptr;
+    const int nbits = PW ? a.nwin * a.M : a.T;          // flagged samples of this call
     const bool lead = active && j == 0;     // writes the row's outputs
 
     float acc[8];            // running bin sums of (I, Q, U, V), re and im
@@ -372,7 +399,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     int fbit = 0, fwi = 0;
     const bool vec_stats = VS && (a.nwin & 3) == 0 && (a.stats_plane & 3) == 0 &&
                            (reinterpret_cast<uintptr_t>(a.stats) & 15) == 0;
-    const bool vec_flags = VS && fmode == 0 && (a.Wpr & 3) == 0 && (a.T & 31) == 0 &&
+    const bool vec_flags = VS && fmode == 0 && (a.Wpr & 3) == 0 && (nbits & 31) == 0 &&
                            (reinterpret_cast<uintptr_t>(a.flags) & 15) == 0;
     float4 tq = make_float4(0.f, 0.f, 0.f, 0.f), rq = tq, iq = tq;
     uint4 fq = make_uint4(0u, 0u, 0u, 0u);
@@ -382,7 +409,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     const unsigned wbytes = (unsigned)a.M * SB;
     if (pf) {
         const int hi = min(a.nwin, (1 + a.pf_groups) * a.pf_windows);
-        if (hi > 1) prefetch_l2(rp + wbytes, (unsigned)(hi - 1) * wbytes);
+        if (hi > 1) prefetch_l2(fp + wbytes, (unsigned)(hi - 1) * wbytes);
     }
     int pf_next = a.pf_windows;
 
@@ -393,7 +420,11 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     constexpr int CHB = CH * P * UB;
     const int nch = S / CH;                       // chunks per window
     const int Q = a.nwin * nch;                   // chunks per lane in this block
-    const char *cp_ = rp + j * UB;
+    const char *cp_ = fp + j * UB;
+    auto load_chunk = [&](int q, Unit<UB>(&u)[CH]) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) load_unit(cp_ + (long long)q * CHB + c * (P * UB), u[c]);
+    };
     WinAcc A;
     const float2 zero2 = make_float2(0.f, 0.f);
     A.s = A.c = A.q = A.u = A.v = zero2;
@@ -401,10 +432,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     for (int c = 0; c < 4; ++c) A.a[c] = zero2;
     int w = 0, cw = 0;
     Unit<UB> ua[CH], ub[DB ? CH : 1];
-    if constexpr (!TMA) {
-#pragma unroll
-        for (int c = 0; c < CH; ++c) load_unit(cp_ + c * (P * UB), ua[c]);
-    }
+    if constexpr (!TMA && !PW) load_chunk(0, ua);
 
     auto consume = [&](const Unit<UB>(&u)[CH]) {
 #pragma unroll
@@ -529,10 +557,31 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         if (pf && w == pf_next) {
             const int g0 = w + a.pf_groups * a.pf_windows;
             const int g1 = min(a.nwin, g0 + a.pf_windows);
-            if (g0 < g1) prefetch_l2(rp + (long long)g0 * wbytes, (unsigned)(g1 - g0) * wbytes);
+            if (g0 < g1) prefetch_l2(fp + (long long)g0 * wbytes, (unsigned)(g1 - g0) * wbytes);
             pf_next += a.pf_windows;
         }
     };
+
+    int q0 = 0;                                   // first chunk of the pipelined loop
+    if constexpr (!TMA && PW) {
+        if (head) {
+            // window 0 began in an earlier block: its units before the block come from
+            // the raw-sample carry; loaded chunk by chunk, outside the pipelined loop
+            for (int q = 0; q < nch; ++q) {
+                Unit<UB> u[CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int off = q * CHB + c * (P * UB) + j * UB;
+                    if (off < a.phase * SB) load_unit_rw(hwp + off, u[c]);
+                    else load_unit(fp + off, u[c]);
+                }
+                consume(u);
+            }
+            end_window();
+            q0 = nch;
+        }
+        if (q0 < Q) load_chunk(q0, ua);
+    }
 
     if constexpr (TMA) {
         // stages of G windows for the warp's 32 rows: [stage][lane][pitch] bytes
@@ -593,37 +642,37 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             return;
         }
     } else if constexpr (DB) {
-        for (int q = 0; q < Q; q += 2) {
-            if (q + 1 < Q) {
-#pragma unroll
-                for (int c = 0; c < CH; ++c)
-                    load_unit(cp_ + (long long)(q + 1) * CHB + c * (P * UB), ub[c]);
-            }
+        for (int q = q0; q < Q; q += 2) {
+            if (q + 1 < Q) load_chunk(q + 1, ub);
             consume(ua);
             if (++cw == nch) { cw = 0; end_window(); }
             if (q + 1 >= Q) break;
-            if (q + 2 < Q) {
-#pragma unroll
-                for (int c = 0; c < CH; ++c)
-                    load_unit(cp_ + (long long)(q + 2) * CHB + c * (P * UB), ua[c]);
-            }
+            if (q + 2 < Q) load_chunk(q + 2, ua);
             consume(ub);
             if (++cw == nch) { cw = 0; end_window(); }
         }
     } else {
-        for (int q = 0; q < Q; ++q) {
-            if (q > 0) {
-#pragma unroll
-                for (int c = 0; c < CH; ++c)
-                    load_unit(cp_ + (long long)q * CHB + c * (P * UB), ua[c]);
-            }
+        for (int q = q0; q < Q; ++q) {
+            if (q > q0) load_chunk(q, ua);
             consume(ua);
             if (++cw == nch) { cw = 0; end_window(); }
         }
     }
-    // a last, partly filled flag word (T not a multiple of 32)
-    if (a.T & 31) {
-        if (lead) fl_row[a.T >> 5] = fword;
+    // a last, partly filled flag word (nwin M not a multiple of 32)
+    if (nbits & 31) {
+        if (lead) fl_row[nbits >> 5] = fword;
+    }
+    // samples after the last whole window (window frame [max(nbits, phase), phase + T))
+    // wait in the raw-sample carry for the next block; the window-0 loads above were
+    // consumed before the row's lanes synchronised in end_window
+    if (PW && !TMA && a.phase + a.T > nbits) {
+        __syncwarp();
+        const int s0 = max(nbits, a.phase);
+        const uint4 *src = reinterpret_cast<const uint4 *>(fp + (long long)s0 * SB);
+        uint4 *dst = reinterpret_cast<uint4 *>(hwp + (long long)(s0 - nbits) * SB);
+        const int n16 = (a.phase + a.T - s0) * (SB / 16);
+        if (active)
+            for (int k = j; k < n16; k += P) dst[k] = src[k];
     }
     if (wib != 0 && active) {
         float *cp = a.carry + (row * P + j) * 9;
@@ -644,14 +693,14 @@ template <> struct Bounds<1> { static constexpr int threads = 256, blocks = 3; }
 template <> struct Bounds<2> { static constexpr int threads = 256, blocks = 4; };
 
 template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, bool MIXED = false,
-          bool VS = false>
+          bool VS = false, bool PW = false>
 __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_block(const __grid_constant__ StreamArgs a) {
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     // the 128-register budget keeps two chunks in flight; tighter budgets load one
     // chunk at a time and rely on more resident warps instead
-    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS>(a, group);
+    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS, PW>(a, group);
 }
 
 // One lane per row, rows staged in shared memory by TMA bulk copies; dynamic shared
@@ -666,7 +715,7 @@ __global__ void __launch_bounds__(512, 1) k_tma(const __grid_constant__ StreamAr
 // Persistent batch: every warp takes (stream, row group) tasks from a device counter
 // until none is left; the last block to finish resets the counter for the next
 // launch in stream order.
-template <int DT, int SPU, int P, int CH, bool KAHAN, bool MIXED = false>
+template <int DT, int SPU, int P, int CH, bool KAHAN, bool MIXED = false, bool PW = false>
 __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchArgs b) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -681,7 +730,8 @@ __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchA
             const bool le = k < b.n && b.prefix[k + 1] <= (long long)t;
             i += __popc(__ballot_sync(FULL, le));
         }
-        process_group<DT, SPU, P, CH, KAHAN, true, MIXED>(b.s[i], (long long)t - b.prefix[i]);
+        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW>(
+            b.s[i], (long long)t - b.prefix[i]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

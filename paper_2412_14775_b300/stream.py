@@ -22,15 +22,22 @@ class RfiStream:
     def outputs_for(self, T):
         return B.rfi_outputs_for(self.ctx, T)
 
+    def windows_for(self, T):
+        """(n_win, first_sample) of the next block of T samples."""
+        return B.rfi_windows_for(self.ctx, T)
+
     def alloc_outputs(self, T, device="cuda", pin_memory=False):
+        """Outputs of the NEXT block of T samples (their sizes depend on the stream's
+        position when windows or bins straddle blocks)."""
         import torch
         n_out = self.outputs_for(T)
+        n_win = self.windows_for(T)[0]
         kw = dict(device=device) if device != "cpu" else dict(pin_memory=pin_memory)
         return dict(
-            flags=torch.empty((self.R, (T + 31) // 32), dtype=torch.int32, **kw),
+            flags=torch.empty((self.R, (n_win * self.M + 31) // 32), dtype=torch.int32, **kw),
             avg=torch.empty((self.R, n_out, 4, 2), dtype=torch.float32, **kw),
             weight=torch.empty((self.R, n_out), dtype=torch.float32, **kw),
-            stats=torch.empty((3, self.R // self.F, T // self.M), dtype=torch.float32, **kw))
+            stats=torch.empty((3, self.R // self.F, n_win), dtype=torch.float32, **kw))
 
     def _T(self, vis):
         if vis.shape[-2:] != (4, 2):

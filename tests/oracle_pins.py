@@ -23,6 +23,9 @@ Facts used (paper: arXiv 2412.14775, Sections 2.1, 2.2, Tables 1-2):
   P7  Exact evaluation on a small integer grid (50-digit arithmetic, Stokes taken as
       traces against the Pauli matrices instead of the sums of Eq. IQUV).
   P8  Splitting a stream into blocks at multiples of W changes nothing.
+  P10 Windows are runs of consecutive samples of a stream (Sec. 2), whatever the
+      correlator's block length: with partial windows, blocks of any length give the
+      windows, flags and averages of the unsplit stream, each reported once.
 """
 import itertools
 import math
@@ -402,3 +405,49 @@ def pin_p9_tf_footprints(seed=10):
 
 
 ALL_PINS.append(pin_p9_tf_footprints)
+
+
+def _bits(words, n):
+    """The first n flag bits of a row's words, bit t of word t // 32 at t mod 32."""
+    w = np.asarray(words, dtype=np.uint64)
+    return [(int(w[t >> 5]) >> (t & 31)) & 1 for t in range(n)]
+
+
+def pin_p10_partial_windows(seed=11):
+    """P10: blocks of any length (partial windows carried between blocks) give, per
+    completed window, exactly the unsplit stream's statistics, flag bits and averages;
+    samples of a window still open at the end are not reported."""
+    rng = np.random.default_rng(seed)
+    for R, M, K, F, T in ((6, 5, 20, 1, 203), (8, 4, 24, 2, 150), (5, 16, 16, 1, 100)):
+        vis = rng.standard_normal((R, T, 4)) + 1j * rng.standard_normal((R, T, 4))
+        vis[:, 30:41] *= 6.0
+        vis[1, 60:95, :] = 4.0 * (1 - 1j)
+        thr = (1.0, 0.3, 2.0, 0.7, EPS32)
+        whole_T = (T // M) * M
+        whole = OracleStream(R, M, K, *thr, F=F).process(vis[:, :whole_T])
+        for cuts in ((1, 2, 3, 50, 51, 130), (7, 77), tuple(range(3, T, 13)), (M + 1,)):
+            st = OracleStream(R, M, K, *thr, F=F, partial=True)
+            edges = (0,) + tuple(c for c in cuts if c < T) + (T,)
+            parts = []
+            for a, b in zip(edges[:-1], edges[1:]):
+                nwin, f0 = st.windows_for(b - a)
+                n_out = st.outputs_for(b - a)
+                out = st.process(vis[:, a:b])
+                assert out["tau"].shape[1] == nwin and out["avg"].shape[1] == n_out
+                assert f0 == (a // M) * M if nwin else True
+                parts.append(out)
+            for key in ("tau", "r_re", "r_im", "wflag"):
+                got = np.concatenate([p[key] for p in parts], axis=1)
+                assert np.array_equal(got, whole[key]), (M, cuts, key)
+            for key in ("avg", "weight"):
+                got = np.concatenate([p[key] for p in parts], axis=1)
+                assert np.array_equal(got, whole[key]), (M, cuts, key)
+            for r in range(R):
+                bits = []
+                for p in parts:
+                    bits += _bits(p["flagbits"][r], p["tau"].shape[1] * M)
+                assert bits == _bits(whole["flagbits"][r], whole_T), (M, cuts, r)
+            assert st.pending.shape[1] == T - whole_T
+
+
+ALL_PINS.append(pin_p10_partial_windows)

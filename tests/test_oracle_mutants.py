@@ -78,3 +78,26 @@ def test_pins_catch_mutant(name, src, tmp_path):
     finally:
         oracle.oracle.use_library(None)
     assert os.path.exists(lib)
+
+
+# Partial windows live in the Python wrapper (oracle/oracle.py), which buffers the
+# samples of a window left open by a block; mistakes there must fail pin P10.
+PY_MUTANTS = {
+    "partial_pending_dropped": ("v = np.concatenate([self.pending, v], axis=1)", "v = v"),
+    "partial_pending_not_kept": ("v[:, whole:].copy()", "v[:, :0].copy()"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_partial_window_pin_catches_mutant(name, monkeypatch):
+    import types
+    old, new = PY_MUTANTS[name]
+    with open(oracle.oracle.__file__) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mod = types.ModuleType("oracle._mutant")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(text.replace(old, new), "oracle_mutant.py", "exec"), mod.__dict__)
+    monkeypatch.setattr(oracle_pins, "OracleStream", mod.OracleStream)
+    with pytest.raises((AssertionError, ValueError)):
+        oracle_pins.pin_p10_partial_windows()

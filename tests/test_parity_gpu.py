@@ -31,7 +31,7 @@ def _check_stream(stations, channels, M, K, Ts, dtype, thr=None, seed=3, **opts)
                             duty=0.08)["vis"]
     R = data.shape[0] * data.shape[1]
     st = RfiStream(stations, channels, M, K, thr, dtype, **opts)
-    orc = oracle.OracleStream(R, M, K, **thr, F=F)
+    orc = oracle.OracleStream(R, M, K, **thr, F=F, partial=bool(opts.get("partial_windows")))
     t0 = 0
     reps = []
     for T in Ts:
@@ -125,6 +125,16 @@ SHAPES = [
     ("f16", 4, 6, 16, 64, [512, 192], {"buffered_stores": 1}),
     ("f32", 5, 4, 4, 8, [128, 8, 256], {"buffered_stores": 1, "lanes_per_row": 1}),
     ("f32", 5, 4, 8, 16, [64, 32], {"buffered_stores": 1, "window_F": 2}),
+    # blocks of any length: windows left open by a block are completed by the next
+    ("f32", 5, 4, 16, 64, [250, 7, 1, 100, 300], {"partial_windows": 1, "lanes_per_row": 4}),
+    ("f16", 4, 5, 8, 32, [50, 6, 2, 100], {"partial_windows": 1, "lanes_per_row": 2}),
+    ("f16", 4, 5, 5, 10, [7, 3, 11, 20], {"partial_windows": 1}),
+    ("f32", 5, 4, 10, 20, [33, 17, 50], {"partial_windows": 1, "window_F": 2}),
+    ("f32", 4, 6, 16, 32, [40, 24, 100], {"partial_windows": 1, "lanes_per_row": 2}),
+    ("f16", 5, 4, 16, 64, [90, 38], {"partial_windows": 1, "compensated": 1,
+                                     "lanes_per_row": 1}),
+    ("f32", 4, 5, 8, 16, [20, 12, 64], {"partial_windows": 1, "lanes_per_row": 4}),
+    ("f32", 4, 5, 64, 128, [100, 60, 200], {"partial_windows": 1, "lanes_per_row": 8}),
 ]
 
 
@@ -420,6 +430,100 @@ def test_buffered_stores_bit_identical_to_plain_stores():
         RfiStream(4, 4, 8, 64, thr8, "f32", loader=1, buffered_stores=1)
     with pytest.raises(binding.RfiError):      # nor of the reduced register budgets
         RfiStream(4, 4, 8, 64, thr8, "f32", max_registers=64, buffered_stores=1)
+
+
+def _bit_stream(flags, n):
+    """The first n flag bits of every row, [R, n] uint8."""
+    f = flags.cpu().numpy().view(np.uint32).astype(np.uint64)
+    t = np.arange(n)
+    return ((f[:, t // 32] >> (t % 32).astype(np.uint64)) & 1).astype(np.uint8)
+
+
+@pytest.mark.parametrize("dtype,M,P,F", [("f32", 16, 4, 1), ("f16", 8, 2, 1), ("f16", 5, 1, 1),
+                                         ("f32", 10, 2, 2)])
+def test_partial_windows_bit_identical_to_one_block(dtype, M, P, F):
+    """A stream cut into blocks of any length gives, bit for bit, the outputs of the
+    unsplit stream (every window is evaluated whole, in the same lane order)."""
+    N, C, K, T = 7, 8, 4 * M, 40 * M
+    thr = default_thresholds(M * F)
+    d = synth.tiny_block(seed=41, stations=N, channels=C, T=T, duty=0.08)["vis"]
+    v = to_device_rows(d, dtype)
+    opts = dict(lanes_per_row=P, window_F=F)
+    one = RfiStream(N, C, M, K, thr, dtype, **opts).process(v)
+    rng = np.random.default_rng(5)
+    st = RfiStream(N, C, M, K, thr, dtype, partial_windows=1, **opts)
+    cuts = sorted(set(int(x) for x in rng.integers(1, T, size=12)))
+    if dtype == "f16" and M % 2 == 0:
+        cuts = sorted(set(c - c % 2 for c in cuts) - {0})
+    edges = [0] + cuts + [T]
+    parts = [st.process(v[:, a:b].contiguous()) for a, b in zip(edges[:-1], edges[1:])]
+    torch.cuda.synchronize()
+    for k in ("stats", "avg", "weight"):
+        assert torch.equal(torch.cat([p[k] for p in parts], dim=-1 if k == "stats" else 1),
+                           one[k]), k
+    bits = np.concatenate([_bit_stream(p["flags"], p["stats"].shape[-1] * M) for p in parts],
+                          axis=1)
+    assert np.array_equal(bits, _bit_stream(one["flags"], T))
+
+
+def test_partial_windows_batch_host_and_checkpoint():
+    """Partial windows through the persistent batch (contexts at different phases),
+    the host-buffer path and a checkpoint taken while a window is open."""
+    M, K = 16, 64
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=43, stations=6, channels=8, T=512)["vis"]
+    v = to_device_rows(d, "f32")
+    solo = [RfiStream(6, 8, M, K, thr, "f32", partial_windows=1, lanes_per_row=2)
+            for _ in range(2)]
+    bat = [RfiStream(6, 8, M, K, thr, "f32", partial_windows=1, lanes_per_row=2)
+           for _ in range(2)]
+    # phases: stream 0 advanced by 5 samples, stream 1 by 22
+    for ss in (solo, bat):
+        ss[0].process(v[:, :5].contiguous())
+        ss[1].process(v[:, :22].contiguous())
+    Ts = [37, 90]
+    blocks = [v[:, 5:42].contiguous(), v[:, 22:112].contiguous()]
+    exp = [s.process(b) for s, b in zip(solo, blocks)]
+    outs = [s.alloc_outputs(T) for s, T in zip(bat, Ts)]
+    binding.rfi_process_batch([s.ctx for s in bat], blocks, Ts,
+                              [o["flags"] for o in outs], [o["avg"] for o in outs],
+                              [o["weight"] for o in outs], [o["stats"] for o in outs])
+    torch.cuda.synchronize()
+    for e, o in zip(exp, outs):
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(e[k], o[k]), k
+    # host path: the same stream, block by block, in host memory
+    a = RfiStream(6, 8, M, K, thr, "f32", partial_windows=1, host_max_T=200)
+    b = RfiStream(6, 8, M, K, thr, "f32", partial_windows=1)
+    h = v.cpu()
+    t0 = 0
+    for T in (13, 200, 51, 3):
+        ga = a.process_host(h[:, t0:t0 + T].contiguous())
+        gb = b.process(v[:, t0:t0 + T].contiguous())
+        torch.cuda.synchronize()
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(ga[k], gb[k].cpu()), (T, k)
+        t0 += T
+    # checkpoint with a window open, resume in a new context
+    blob = binding.rfi_get_state(b.ctx)
+    c = RfiStream(6, 8, M, K, thr, "f32", partial_windows=1)
+    binding.rfi_set_state(c.ctx, blob)
+    x = b.process(v[:, t0:t0 + 77].contiguous())
+    y = c.process(v[:, t0:t0 + 77].contiguous())
+    torch.cuda.synchronize()
+    for k in ("flags", "avg", "weight", "stats"):
+        assert torch.equal(x[k], y[k]), k
+    # argument checks
+    with pytest.raises(RfiError):        # pairs of binary16 samples: T must be even
+        RfiStream(4, 4, 8, 32, default_thresholds(8), "f16", partial_windows=1).process(
+            torch.zeros(10, 7, 4, 2, dtype=torch.float16, device="cuda"))
+    for bad in (dict(loader=1), dict(max_registers=64), dict(precision=1),
+                dict(buffered_stores=1)):      # instances exist for the default kernel only
+        with pytest.raises(RfiError):
+            RfiStream(4, 4, 16, 64, thr, "f32", partial_windows=1, **bad)
+    with pytest.raises(RfiError):        # without the option, T must be a multiple of M
+        RfiStream(4, 4, 16, 64, thr, "f32").process(
+            torch.zeros(10, 24, 4, 2, device="cuda"))
 
 
 def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
