@@ -363,6 +363,51 @@ def mixed_extras(vis32, torch, cs, peak, steps=300, warmup=10):
     return res
 
 
+def variant_extras(vis32, opts, torch, cs, peak, steps=300, warmup=10):
+    """The LOFAR-scale complex64 block through the kernel variants with their own
+    instances: online per-stream SK thresholds (T = 256) and partial windows (blocks
+    of T = 250 samples, so windows straddle blocks), each against the plain kernel."""
+    from paper_2412_14775_b300 import RfiStream, default_thresholds
+    M, K = 16, 256
+    thr = default_thresholds(M)
+    R = vis32.shape[0]
+    res = {}
+    ad = RfiStream(62, 64, M, K, thr, "f32", adaptive=1, **opts)
+    o = ad.alloc_outputs(256)
+    _, per, _ = time_kernel(ad, vis32, o, steps, warmup, torch, cs)
+    k = statistics.mean(per)
+    nbytes = algo_bytes(R, 256, M, K, 1, 32) + R * 16 * 2     # + state read and write
+    rate = float(o["weight"].lt(1.0).float().mean())
+    res["online_thresholds"] = {"kernel_us": k * 1e6, "achieved_gbs": nbytes / k / 1e9,
+                                "frac": nbytes / k / 1e9 / peak,
+                                "bins_with_flagged_samples": rate}
+    ad.close()
+    v250 = vis32[:, :250].contiguous()
+    pw = RfiStream(62, 64, M, K, thr, "f32", partial_windows=1, **opts)
+    times = []
+    for step in range(warmup + steps):
+        out = pw.alloc_outputs(250)
+        n_win = out["stats"].shape[-1]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cs)
+        pw.process(v250, out=out, stream=cs)
+        e1.record(cs)
+        if step >= warmup:
+            times.append((e0, e1, n_win))
+    torch.cuda.synchronize()
+    us = statistics.mean(a.elapsed_time(b) for a, b, _ in times) * 1e3
+    nw = statistics.mean(n for _, _, n in times)
+    # input, flags and statistics of the completed windows, the samples carried
+    nbytes = R * (250 * 32 + 4 * math.ceil(nw * M / 32) + 12 * nw + 32 * (M - 1))
+    res["partial_windows_T250"] = {"kernel_us": us, "achieved_gbs": nbytes / (us * 1e-6) / 1e9,
+                                   "frac": nbytes / (us * 1e-6) / 1e9 / peak,
+                                   "samples_per_s": R * 250 / (us * 1e-6)}
+    pw.close()
+    del v250
+    torch.cuda.empty_cache()
+    return res
+
+
 def batched_extras(options, torch, steps=300, warmup=10):
     """8 uneven binary16 subbands (stations 24..76, channels 16..128, T = 256) in one
     persistent launch replayed from a CUDA graph, against the same 8 streams launched
@@ -557,6 +602,7 @@ def main():
     extras = {}
     if not args.no_extras and rank == 0:
         extras["mixed_precision"] = mixed_extras(vis32, torch, cs, peak)
+        extras["variants"] = variant_extras(vis32, opts, torch, cs, peak)
         if args.detection:
             extras["detection"] = detection_experiment(torch)
         # FP16 storage (same geometry), window sweep

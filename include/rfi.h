@@ -141,6 +141,18 @@ typedef enum {
  *                  Needs the direct loader, float32 arithmetic, the 128-register
  *                  budget and plain stores (kernel instances of their own, so the
  *                  others carry no cost).  0 = T must be a multiple of M (default).
+ *   adaptive       1 = online per-stream SK thresholds (the paper's Sec. 5 names online
+ *                  threshold adaptation as future work; this is the build's form of
+ *                  it): every footprint row keeps, on the device, a running estimate
+ *                  of the mean and second moment of tau over its unflagged windows
+ *                  (the n-th such window weighted max(alpha, 1/n)); once n >= n_warm
+ *                  the row's SK test uses [mean - k_sigma sd, mean + k_sigma sd]
+ *                  instead of [s_low, s_high].  A launch uses the thresholds of the
+ *                  state at its start and advances the state window by window.  gamma
+ *                  stays fixed.  Parameters: rfi_set_adaptation (defaults alpha =
+ *                  1/64, k_sigma = 3, n_warm = 32).  Needs the direct loader, float32
+ *                  arithmetic, the 128-register budget, plain stores and whole
+ *                  windows.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -161,7 +173,15 @@ typedef struct {
     int debug_inject_wait_timeout;
     int buffered_stores;
     int partial_windows;
+    int adaptive;
 } rfi_options;
+
+/* Parameters of the online SK thresholds (option `adaptive`). */
+typedef struct {
+    double alpha;     /* weight of a new clean window once n >= 1/alpha; 0 = plain mean */
+    double k_sigma;   /* half width of the accepted interval in standard deviations */
+    int n_warm;       /* clean windows a row needs before its own thresholds apply */
+} rfi_adaptation;
 
 /* Create a context for one stream of `stations` stations (B = N(N+1)/2 baselines)
  * and `channels` channels, window M = window_M >= 2 samples and output averaging
@@ -194,6 +214,14 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt);
 
 /* Replace the thresholds (takes effect for work issued afterwards). */
 int rfi_set_thresholds(rfi_ctx *ctx, const rfi_thresholds *thr);
+
+/* Adaptive contexts only (else RFI_EINVAL): set the parameters of the online SK
+ * thresholds (0 <= alpha <= 1, finite k_sigma >= 0, n_warm >= 1), effective for work
+ * issued afterwards; and copy the per-row state, float[R/F][4] = {n, mean of tau,
+ * mean of tau^2, unused}, to (write = 0) or from (write = 1) a host buffer of at least
+ * 4 R/F floats, after synchronising `stream`. */
+int rfi_set_adaptation(rfi_ctx *ctx, const rfi_adaptation *p);
+int rfi_adaptive_state(rfi_ctx *ctx, float *host, size_t n_floats, int write, void *stream);
 
 /* Process one block of T samples (T a positive multiple of M, or any T with
  * partial_windows) of every row.  n_win = rfi_windows_for(T) windows complete.
@@ -273,11 +301,12 @@ int rfi_process_block_noalloc(int stations, int channels, int window_M, int avg_
 
 /* Checkpoint and resume.  A stream's state is its sample count, thresholds and the
  * per-lane running sums of every row's open averaging bin (and, with
- * partial_windows, the raw samples of every row's open window).  rfi_get_state
+ * partial_windows, the raw samples of every row's open window; with adaptive, the
+ * running moments of tau and their parameters).  rfi_get_state
  * synchronises `stream` and copies the state into a caller-owned host buffer of
  * rfi_state_size bytes (a plain byte blob); rfi_set_state loads it into a context of
  * the same geometry and launch shape (rows, lanes_per_row, M, K, window_F, dtype,
- * partial_windows; else
+ * partial_windows, adaptive; else
  * RFI_EINVAL), after which the stream continues exactly (bit for bit) where the saved
  * one stopped. */
 int rfi_state_size(const rfi_ctx *ctx, size_t *bytes);

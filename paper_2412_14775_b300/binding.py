@@ -24,7 +24,8 @@ EXPORTED = ["rfi_create", "rfi_create_ex", "rfi_rows", "rfi_outputs_for", "rfi_g
             "rfi_process_batch", "rfi_batch_graph_create", "rfi_batch_graph_launch",
             "rfi_batch_graph_destroy", "rfi_reset", "rfi_destroy", "rfi_status_str",
             "rfi_last_error", "rfi_process_block_noalloc", "rfi_check", "rfi_state_size",
-            "rfi_get_state", "rfi_set_state", "rfi_windows_for"]
+            "rfi_get_state", "rfi_set_state", "rfi_windows_for", "rfi_set_adaptation",
+            "rfi_adaptive_state"]
 
 # Fixed size of the library's no-allocation scratch (RFI_NOALLOC_SCRATCH_BYTES).
 RFI_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -41,6 +42,11 @@ class rfi_thresholds(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
+class rfi_adaptation(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("k_sigma", ctypes.c_double),
+                ("n_warm", ctypes.c_int)]
+
+
 class rfi_options(ctypes.Structure):
     _fields_ = [("lanes_per_row", ctypes.c_int), ("warps_per_block", ctypes.c_int),
                 ("host_max_T", ctypes.c_int), ("host_chunks", ctypes.c_int),
@@ -49,7 +55,8 @@ class rfi_options(ctypes.Structure):
                 ("window_F", ctypes.c_int), ("precision", ctypes.c_int),
                 ("loader", ctypes.c_int), ("tma_stage_windows", ctypes.c_int),
                 ("tma_stages", ctypes.c_int), ("debug_inject_wait_timeout", ctypes.c_int),
-                ("buffered_stores", ctypes.c_int), ("partial_windows", ctypes.c_int)]
+                ("buffered_stores", ctypes.c_int), ("partial_windows", ctypes.c_int),
+                ("adaptive", ctypes.c_int)]
 
 
 _lib = None
@@ -76,6 +83,8 @@ def load_library(path=None):
         "rfi_windows_for": ([vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_longlong)], ip),
         "rfi_get_options": ([vp, ctypes.POINTER(rfi_options)], ip),
         "rfi_set_thresholds": ([vp, ctypes.POINTER(rfi_thresholds)], ip),
+        "rfi_set_adaptation": ([vp, ctypes.POINTER(rfi_adaptation)], ip),
+        "rfi_adaptive_state": ([vp, vp, ctypes.c_size_t, ip, vp], ip),
         "rfi_process_block": ([vp, vp, ip, vp, vp, vp, vp, vp], ip),
         "rfi_process_block_host": ([vp, vp, ip, vp, vp, vp, vp, vp], ip),
         "rfi_process_batch": ([pp, ip, pp, ctypes.POINTER(ip), pp, pp, pp, pp, vp], ip),
@@ -203,6 +212,28 @@ def rfi_get_options(ctx):
 def rfi_set_thresholds(ctx, thresholds):
     t = _thr(thresholds)
     _check(load_library().rfi_set_thresholds(ctx, ctypes.byref(t)), "rfi_set_thresholds")
+
+
+def rfi_set_adaptation(ctx, alpha=1.0 / 64, k_sigma=3.0, n_warm=32):
+    p = rfi_adaptation(float(alpha), float(k_sigma), int(n_warm))
+    _check(load_library().rfi_set_adaptation(ctx, ctypes.byref(p)), "rfi_set_adaptation")
+
+
+def rfi_adaptive_state(ctx, state=None, stream=None):
+    """Read (state None) or write the per-row online-threshold state, float32 [R/F, 4]
+    = (n, mean of tau, mean of tau^2, unused); returns it as a numpy array."""
+    import numpy as np
+    if state is None:
+        R = rfi_rows(ctx)
+        F = rfi_get_options(ctx)["window_F"]
+        buf = np.zeros((R // F, 4), np.float32)
+        write = 0
+    else:
+        buf = np.ascontiguousarray(state, dtype=np.float32)
+        write = 1
+    _check(load_library().rfi_adaptive_state(ctx, buf.ctypes.data, buf.size, write,
+                                             _stream(stream)), "rfi_adaptive_state")
+    return buf
 
 
 def rfi_process_block(ctx, vis, T, flags, avg, weight, stats, stream=None):

@@ -39,14 +39,14 @@ int fail(int status, const char *fmt, ...) {
 
 // ---- kernel instances (rfi_inst_f32.cu, rfi_inst_f16.cu) ----------------------
 const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb, int mixed,
-                              int vs, int pw) {
-    const InstanceTable tabs[] = {instances_f32(), instances_f16(), instances_f32_pw(),
-                                  instances_f16_pw()};
+                              int vs, int pw, int ad) {
+    const InstanceTable tabs[] = {instances_f32(),    instances_f16(),    instances_f32_pw(),
+                                  instances_f16_pw(), instances_f32_ad(), instances_f16_ad()};
     for (const InstanceTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const Instance &in = t.items[i];
             if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan &&
-                in.lb == lb && in.mixed == mixed && in.vs == vs && in.pw == pw)
+                in.lb == lb && in.mixed == mixed && in.vs == vs && in.pw == pw && in.ad == ad)
                 return &in;
         }
     return nullptr;
@@ -116,6 +116,9 @@ struct rfi_ctx {
     int vs;                             // buffered 16-byte statistic and flag stores
     int pw;                             // partial windows: any T, open window carried
     char *hw;                           // [R][M] raw samples of each row's open window
+    int ad;                             // online per-stream SK thresholds
+    float *adapt;                       // [R/F][4]: n, mean, second moment of tau, unused
+    rfi_adaptation adp;
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     const Instance *inst;
     long long n_seen;
@@ -147,6 +150,7 @@ struct rfi_batch_graph {
 namespace {
 
 int sample_bytes(rfi_dtype dt) { return dt == RFI_C64 ? 32 : 16; }
+size_t adapt_bytes(const rfi_ctx *c) { return sizeof(float) * 4 * (size_t)(c->R / c->F); }
 
 int check_ctx(const rfi_ctx *ctx) {
     if (!ctx) return fail(RFI_EINVAL, "null context");
@@ -237,7 +241,11 @@ int choose_shape(rfi_ctx *c, int P_req) {
     c->spu = spu;
     c->S = c->M / (P * spu);
     c->ch = largest_chunk(c->S);
-    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs, c->pw);
+    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs, c->pw, c->ad);
+    if (c->ad && (!c->inst || c->loader != 0))
+        return fail(RFI_EUNSUPPORTED, "adaptive needs the direct loader, the 128-register "
+                                      "budget and float32 arithmetic, without buffered_stores "
+                                      "or partial_windows");
     if (c->pw && !c->inst)
         return fail(RFI_EUNSUPPORTED, "partial_windows needs the 128-register budget and "
                                       "float32 arithmetic, without buffered_stores");
@@ -289,6 +297,10 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.stats = stats + (r0 / c->F) * nwin;     // r0 is a multiple of F
     a.carry = c->carry + r0 * c->P * 9;
     a.hw = c->hw ? c->hw + r0 * c->M * sample_bytes(c->dtype) : nullptr;
+    a.adapt = c->adapt ? c->adapt + (r0 / c->F) * 4 : nullptr;
+    a.alpha = (float)c->adp.alpha;
+    a.k_sigma = (float)c->adp.k_sigma;
+    a.n_warm = (float)c->adp.n_warm;
     a.phase = phase_of(c);
     a.R = nrows;
     a.stats_plane = (c->R / c->F) * nwin;
@@ -465,6 +477,7 @@ void free_ctx(rfi_ctx *c) {
     cudaSetDevice(c->device);
     if (c->carry) cudaFree(c->carry);
     if (c->hw) cudaFree(c->hw);
+    if (c->adapt) cudaFree(c->adapt);
     if (c->counter) cudaFree(c->counter);
     if (c->h_vis) cudaFree(c->h_vis);
     if (c->h_flags) cudaFree(c->h_flags);
@@ -562,6 +575,10 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->inject = o.debug_inject_wait_timeout;
     c->vs = o.buffered_stores != 0;
     c->pw = o.partial_windows != 0;
+    c->ad = o.adaptive != 0;
+    c->adp.alpha = 1.0 / 64;
+    c->adp.k_sigma = 3.0;
+    c->adp.n_warm = 32;
     if (c->pw && c->loader != 0) {
         delete c;
         return fail(RFI_EUNSUPPORTED, "partial_windows needs the direct loader (loader = 0)");
@@ -595,7 +612,9 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
         (e = cudaMemset(c->carry, 0, sizeof(float) * 9 * (size_t)c->P * c->R)) != cudaSuccess ||
         (e = cudaMemset(c->counter, 0, 4 * sizeof(unsigned long long))) != cudaSuccess ||
         (c->pw && (e = cudaMalloc(&c->hw, (size_t)c->R * c->M * sample_bytes(dtype))) !=
-                      cudaSuccess)) {
+                      cudaSuccess) ||
+        (c->ad && (e = cudaMalloc(&c->adapt, adapt_bytes(c))) != cudaSuccess) ||
+        (c->ad && (e = cudaMemset(c->adapt, 0, adapt_bytes(c))) != cudaSuccess)) {
         cudaGetLastError();
         free_ctx(c);
         return fail(e == cudaErrorMemoryAllocation ? RFI_ENOMEM : RFI_ECUDA,
@@ -697,6 +716,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->debug_inject_wait_timeout = ctx->inject;
     opt->buffered_stores = ctx->vs;
     opt->partial_windows = ctx->pw;
+    opt->adaptive = ctx->ad;
     return RFI_OK;
 }
 
@@ -705,6 +725,32 @@ int rfi_set_thresholds(rfi_ctx *ctx, const rfi_thresholds *thr) {
     if ((rc = check_ctx(ctx))) return rc;
     if ((rc = check_thresholds(thr))) return rc;
     ctx->thr = *thr;
+    return RFI_OK;
+}
+
+int rfi_set_adaptation(rfi_ctx *ctx, const rfi_adaptation *p) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!ctx->ad) return fail(RFI_EINVAL, "context was created without adaptive = 1");
+    if (!p || !(p->alpha >= 0.0 && p->alpha <= 1.0) || !(p->k_sigma >= 0.0) ||
+        !std::isfinite(p->k_sigma) || p->n_warm < 1)
+        return fail(RFI_EINVAL, "need 0 <= alpha <= 1, finite k_sigma >= 0, n_warm >= 1");
+    ctx->adp = *p;
+    return RFI_OK;
+}
+
+int rfi_adaptive_state(rfi_ctx *ctx, float *host, size_t n_floats, int write, void *stream) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!ctx->ad) return fail(RFI_EINVAL, "context was created without adaptive = 1");
+    const size_t need = adapt_bytes(ctx) / sizeof(float);
+    if (!host || n_floats < need)
+        return fail(RFI_EINVAL, "adaptive state needs %zu floats ([R/F][4])", need);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess)
+        e = write ? cudaMemcpy(ctx->adapt, host, adapt_bytes(ctx), cudaMemcpyHostToDevice)
+                  : cudaMemcpy(host, ctx->adapt, adapt_bytes(ctx), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_adaptive_state");
     return RFI_OK;
 }
 
@@ -878,13 +924,15 @@ int rfi_batch_graph_destroy(rfi_batch_graph *g) {
 }
 
 namespace {
-// Header of a saved stream state; followed by the carry, float[R][P][9], and, for
-// contexts with partial windows, the raw samples of the open windows, [R][M] samples.
+// Header of a saved stream state; followed by the carry, float[R][P][9], for contexts
+// with partial windows the raw samples of the open windows, [R][M] samples, and for
+// adaptive contexts the running moments of tau, float[R/F][4].
 struct StateHeader {
     unsigned int magic, version;
     long long R, n_seen;
-    int P, M, K, F, dtype, pw;
+    int P, M, K, F, dtype, pw, ad, pad;
     rfi_thresholds thr;
+    rfi_adaptation adp;
 };
 size_t carry_bytes(const rfi_ctx *c) { return sizeof(float) * 9 * (size_t)c->P * c->R; }
 size_t hw_bytes(const rfi_ctx *c) {
@@ -896,7 +944,8 @@ constexpr unsigned int STATE_MAGIC = 0x52464953u;  // "RFIS"
 int rfi_state_size(const rfi_ctx *ctx, size_t *bytes) {
     if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
     if (!bytes) return fail(RFI_EINVAL, "null output");
-    *bytes = sizeof(StateHeader) + carry_bytes(ctx) + hw_bytes(ctx);
+    *bytes = sizeof(StateHeader) + carry_bytes(ctx) + hw_bytes(ctx) +
+             (ctx->ad ? adapt_bytes(ctx) : 0);
     return RFI_OK;
 }
 
@@ -908,8 +957,10 @@ int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream) {
     if (!buf || bytes < need) return fail(RFI_EINVAL, "state buffer needs %zu bytes", need);
     StateHeader h = {};
     h.magic = STATE_MAGIC;
-    h.version = 2;
+    h.version = 3;
     h.pw = ctx->pw;
+    h.ad = ctx->ad;
+    h.adp = ctx->adp;
     h.R = ctx->R;
     h.n_seen = ctx->n_seen;
     h.P = ctx->P;
@@ -925,6 +976,9 @@ int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream) {
         e = cudaMemcpy(dst, ctx->carry, carry_bytes(ctx), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && ctx->pw)
         e = cudaMemcpy(dst + carry_bytes(ctx), ctx->hw, hw_bytes(ctx), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ctx->ad)
+        e = cudaMemcpy(dst + carry_bytes(ctx) + hw_bytes(ctx), ctx->adapt, adapt_bytes(ctx),
+                       cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_get_state");
     return RFI_OK;
 }
@@ -938,13 +992,14 @@ int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes) {
                                           bytes, need);
     StateHeader h;
     std::memcpy(&h, buf, sizeof h);
-    if (h.magic != STATE_MAGIC || h.version != 2)
+    if (h.magic != STATE_MAGIC || h.version != 3)
         return fail(RFI_EINVAL, "not a saved stream state");
     if (h.R != ctx->R || h.P != ctx->P || h.M != ctx->M || h.K != ctx->K || h.F != ctx->F ||
-        h.pw != ctx->pw || h.dtype != (int)ctx->dtype)
+        h.pw != ctx->pw || h.ad != ctx->ad || h.dtype != (int)ctx->dtype)
         return fail(RFI_EINVAL, "saved state is for another geometry or launch shape "
-                                "(rows %lld, lanes %d, M %d, K %d, F %d, partial windows %d)",
-                    h.R, h.P, h.M, h.K, h.F, h.pw);
+                                "(rows %lld, lanes %d, M %d, K %d, F %d, partial windows %d, "
+                                "adaptive %d)",
+                    h.R, h.P, h.M, h.K, h.F, h.pw, h.ad);
     if ((rc = check_thresholds(&h.thr))) return rc;
     cudaError_t e = cudaDeviceSynchronize();
     const char *src = static_cast<const char *>(buf) + sizeof h;
@@ -952,9 +1007,13 @@ int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes) {
         e = cudaMemcpy(ctx->carry, src, carry_bytes(ctx), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && ctx->pw)
         e = cudaMemcpy(ctx->hw, src + carry_bytes(ctx), hw_bytes(ctx), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ctx->ad)
+        e = cudaMemcpy(ctx->adapt, src + carry_bytes(ctx) + hw_bytes(ctx), adapt_bytes(ctx),
+                       cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_set_state");
     ctx->n_seen = h.n_seen;
     ctx->thr = h.thr;
+    if (ctx->ad) ctx->adp = h.adp;
     return RFI_OK;
 }
 
@@ -984,6 +1043,7 @@ int rfi_reset(rfi_ctx *ctx) {
     if (e == cudaSuccess)
         e = cudaMemset(ctx->carry, 0, sizeof(float) * 9 * (size_t)ctx->P * ctx->R);
     if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess && ctx->ad) e = cudaMemset(ctx->adapt, 0, adapt_bytes(ctx));
     if (e != cudaSuccess) {
         ctx->status = RFI_ECUDA;
         return fail(RFI_ECUDA, "reset: %s", cudaGetErrorString(e));

@@ -60,6 +60,12 @@ struct StreamArgs {
     // samples wait in hw, and the samples after this block's last whole window go there
     char *hw;               // [R][M] raw samples of each row's open window (or null)
     int phase;              // samples of window 0 already in hw (0 <= phase < M)
+    // online SK thresholds: per footprint row {n, mean, second moment} of tau over the
+    // unflagged windows seen so far (exponentially weighted), updated window by window
+    float *adapt;           // [R/F][4] (or null)
+    float alpha;            // weight of a new window once n >= 1/alpha
+    float k_sigma;          // thresholds mean -/+ k_sigma * sd once n >= n_warm
+    float n_warm;
 };
 
 struct BatchArgs {
@@ -346,8 +352,15 @@ __device__ __forceinline__ float rowsum(float v, int PF) {
 // `phase` samples wait in the raw-sample carry), and the samples after the last whole
 // window are put there for the next block.  A separate instance, so that the code of
 // the head window and the tail copy does not cost the kernels that need neither.
+// AD: online per-stream SK thresholds.  Each footprint row keeps a running estimate of
+// the mean and second moment of tau over its unflagged windows (weight max(alpha, 1/n)
+// for the n-th, so the first 1/alpha windows give the plain mean).  Once n >= n_warm
+// the row's SK test uses [mean - k sd, mean + k sd] instead of [s_low, s_high]; the
+// thresholds are those of the state at the start of the launch, and the state advances
+// window by window.  The DS threshold gamma stays fixed (its null, E r^2 = 1/W, does
+// not depend on the data).
 template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false,
-          bool TMA = false, bool VS = false, bool PW = false>
+          bool TMA = false, bool VS = false, bool PW = false, bool AD = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
     static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
     static_assert(!TMA || P == 1, "the shared-memory loader runs one lane per row");
@@ -367,6 +380,20 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     char *const hwp = PW ? a.hw + rowc * (long long)a.M * SB : nullptr;
     const int nbits = PW ? a.nwin * a.M : a.T;          // flagged samples of this call
     const bool lead = active && j == 0;     // writes the row's outputs
+    float ad_n = 0.f, ad_mu = 0.f, ad_m2 = 0.f, slo = 0.f, shi = 0.f;
+    float *const ad_row = AD ? a.adapt + (rowc / a.F) * 4 : nullptr;
+    if constexpr (AD) {
+        ad_n = ad_row[0];
+        ad_mu = ad_row[1];
+        ad_m2 = ad_row[2];
+        slo = a.s_low;
+        shi = a.s_high;
+        if (ad_n >= a.n_warm) {
+            const float sd = __fsqrt_rn(fmaxf(ad_m2 - ad_mu * ad_mu, 0.f));
+            slo = ad_mu - a.k_sigma * sd;
+            shi = ad_mu + a.k_sigma * sd;
+        }
+    }
 
     float acc[8];            // running bin sums of (I, Q, U, V), re and im
     float cnt = 0.f;
@@ -469,8 +496,19 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             r_re = sqrt_approx(qr * qr + ur * ur + vr * vr) * a.invM;
             r_im = sqrt_approx(qi * qi + ui * ui + vi * vi) * a.invM;
             // SK flag OR (DS Re OR DS Im); a NaN statistic fails its "inside" test
-            f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
-                !(r_im <= a.gamma);
+            if constexpr (AD)
+                f = !(tau >= slo && tau <= shi) || !(r_re <= a.gamma) || !(r_im <= a.gamma);
+            else
+                f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
+                    !(r_im <= a.gamma);
+        }
+        if constexpr (AD) {
+            if (!f) {       // the running moments follow the windows judged clean
+                ad_n += 1.f;
+                const float wgt = fmaxf(a.alpha, __frcp_rn(ad_n));
+                ad_mu = ad_mu + wgt * (tau - ad_mu);
+                ad_m2 = ad_m2 + wgt * (tau * tau - ad_m2);
+            }
         }
         if (vec_stats) {
             tq = make_float4(tq.y, tq.z, tq.w, tau);
@@ -674,6 +712,13 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         if (active)
             for (int k = j; k < n16; k += P) dst[k] = src[k];
     }
+    if constexpr (AD) {
+        if (st_lead) {
+            ad_row[0] = ad_n;
+            ad_row[1] = ad_mu;
+            ad_row[2] = ad_m2;
+        }
+    }
     if (wib != 0 && active) {
         float *cp = a.carry + (row * P + j) * 9;
 #pragma unroll
@@ -693,14 +738,14 @@ template <> struct Bounds<1> { static constexpr int threads = 256, blocks = 3; }
 template <> struct Bounds<2> { static constexpr int threads = 256, blocks = 4; };
 
 template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, bool MIXED = false,
-          bool VS = false, bool PW = false>
+          bool VS = false, bool PW = false, bool AD = false>
 __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_block(const __grid_constant__ StreamArgs a) {
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     // the 128-register budget keeps two chunks in flight; tighter budgets load one
     // chunk at a time and rely on more resident warps instead
-    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS, PW>(a, group);
+    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS, PW, AD>(a, group);
 }
 
 // One lane per row, rows staged in shared memory by TMA bulk copies; dynamic shared
@@ -715,7 +760,8 @@ __global__ void __launch_bounds__(512, 1) k_tma(const __grid_constant__ StreamAr
 // Persistent batch: every warp takes (stream, row group) tasks from a device counter
 // until none is left; the last block to finish resets the counter for the next
 // launch in stream order.
-template <int DT, int SPU, int P, int CH, bool KAHAN, bool MIXED = false, bool PW = false>
+template <int DT, int SPU, int P, int CH, bool KAHAN, bool MIXED = false, bool PW = false,
+          bool AD = false>
 __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchArgs b) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -730,7 +776,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchA
             const bool le = k < b.n && b.prefix[k + 1] <= (long long)t;
             i += __popc(__ballot_sync(FULL, le));
         }
-        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW>(
+        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW, AD>(
             b.s[i], (long long)t - b.prefix[i]);
     }
     __syncthreads();

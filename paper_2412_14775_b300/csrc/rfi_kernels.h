@@ -8,7 +8,7 @@
 namespace rfi {
 
 struct Instance {
-    int dt, spu, P, ch, kahan, lb, mixed, vs, pw;
+    int dt, spu, P, ch, kahan, lb, mixed, vs, pw, ad;
     const void *block_fn;   // k_block<...>
     const void *batch_fn;   // k_batch<...>; the register budget does not change results,
                             // so every budget shares the LB = 0 batch kernel
@@ -23,6 +23,8 @@ InstanceTable instances_f32();
 InstanceTable instances_f16();
 InstanceTable instances_f32_pw();     // partial windows (rfi_inst_pw_f32.cu)
 InstanceTable instances_f16_pw();     // partial windows (rfi_inst_pw_f16.cu)
+InstanceTable instances_f32_ad();     // online SK thresholds (rfi_inst_ad_f32.cu)
+InstanceTable instances_f16_ad();     // online SK thresholds (rfi_inst_ad_f16.cu)
 
 // The shared-memory (TMA) loader: one lane per row, direct-load twin for batches.
 struct TmaInstance {
@@ -40,22 +42,22 @@ TmaTable tma_instances_f16();
 
 // Entries for one (DT, SPU, P, CH, K): LB = 0 with its own batch kernel.
 #define RFI_INST0(DT, SPU, P, CH, K)                                                        \
-    {DT, SPU, P, CH, K, 0, 0, 0, 0,                                                         \
+    {DT, SPU, P, CH, K, 0, 0, 0, 0, 0,                                                      \
      (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0>,                               \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K>}
 // A tighter register budget LB for the single-stream kernel.
 #define RFI_INSTB(DT, SPU, P, CH, LB)                                                       \
-    {DT, SPU, P, CH, 0, LB, 0, 0, 0,                                                        \
+    {DT, SPU, P, CH, 0, LB, 0, 0, 0, 0,                                                     \
      (const void *)&rfi::k_block<DT, SPU, P, CH, false, LB>,                                \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
 // The paper-mixed precision mode (one lane per row).
 #define RFI_INSTM(DT, SPU, CH)                                                              \
-    {DT, SPU, 1, CH, 0, 0, 1, 0, 0,                                                         \
+    {DT, SPU, 1, CH, 0, 0, 1, 0, 0, 0,                                                      \
      (const void *)&rfi::k_block<DT, SPU, 1, CH, false, 0, true>,                           \
      (const void *)&rfi::k_batch<DT, SPU, 1, CH, false, true>}
 // Buffered 16-byte output stores (for small windows); shares the batch kernel.
 #define RFI_INSTV(DT, SPU, P, CH)                                                           \
-    {DT, SPU, P, CH, 0, 0, 0, 1, 0,                                                         \
+    {DT, SPU, P, CH, 0, 0, 0, 1, 0, 0,                                                      \
      (const void *)&rfi::k_block<DT, SPU, P, CH, false, 0, false, true>,                   \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
 #define RFI_INSTV_P(DT, SPU)                                                                \
@@ -64,7 +66,7 @@ TmaTable tma_instances_f16();
         RFI_INSTV(DT, SPU, 4, 1), RFI_INSTV(DT, SPU, 4, 2), RFI_INSTV(DT, SPU, 4, 4)
 // Partial windows (blocks of any length), 128-register budget.
 #define RFI_INSTP(DT, SPU, P, CH, K)                                                        \
-    {DT, SPU, P, CH, K, 0, 0, 0, 1,                                                         \
+    {DT, SPU, P, CH, K, 0, 0, 0, 1, 0,                                                      \
      (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, true>,          \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, true>}
 #define RFI_INSTP_CH(DT, SPU, P, K)                                                         \
@@ -74,6 +76,18 @@ TmaTable tma_instances_f16();
     RFI_INSTP_CH(DT, SPU, 1, K), RFI_INSTP_CH(DT, SPU, 2, K), RFI_INSTP_CH(DT, SPU, 4, K),  \
         RFI_INSTP_CH(DT, SPU, 8, K), RFI_INSTP_CH(DT, SPU, 16, K),                         \
         RFI_INSTP_CH(DT, SPU, 32, K)
+// Online per-stream SK thresholds, 128-register budget.
+#define RFI_INSTA(DT, SPU, P, CH, K)                                                        \
+    {DT, SPU, P, CH, K, 0, 0, 0, 0, 1,                                                      \
+     (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, false, true>,   \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, false, true>}
+#define RFI_INSTA_CH(DT, SPU, P, K)                                                         \
+    RFI_INSTA(DT, SPU, P, 1, K), RFI_INSTA(DT, SPU, P, 2, K), RFI_INSTA(DT, SPU, P, 4, K),  \
+        RFI_INSTA(DT, SPU, P, 5, K)
+#define RFI_INSTA_P(DT, SPU, K)                                                             \
+    RFI_INSTA_CH(DT, SPU, 1, K), RFI_INSTA_CH(DT, SPU, 2, K), RFI_INSTA_CH(DT, SPU, 4, K),  \
+        RFI_INSTA_CH(DT, SPU, 8, K), RFI_INSTA_CH(DT, SPU, 16, K),                         \
+        RFI_INSTA_CH(DT, SPU, 32, K)
 #define RFI_INSTM_CH(DT, SPU)                                                               \
     RFI_INSTM(DT, SPU, 1), RFI_INSTM(DT, SPU, 2), RFI_INSTM(DT, SPU, 4), RFI_INSTM(DT, SPU, 5)
 #define RFI_INST0_CH(DT, SPU, P, K)                                                         \

@@ -65,6 +65,14 @@ class RfiStream:
                                  out["weight"] if n_out else None, out["stats"], stream)
         return out
 
+    def set_adaptation(self, alpha=1.0 / 64, k_sigma=3.0, n_warm=32):
+        """Parameters of the online SK thresholds (contexts created with adaptive=1)."""
+        B.rfi_set_adaptation(self.ctx, alpha, k_sigma, n_warm)
+
+    def adaptive_state(self, state=None):
+        """Read, or with `state` write, the per-row (n, mean tau, mean tau^2, 0)."""
+        return B.rfi_adaptive_state(self.ctx, state)
+
     def reset(self):
         B.rfi_reset(self.ctx)
 

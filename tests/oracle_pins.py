@@ -451,3 +451,88 @@ def pin_p10_partial_windows(seed=11):
 
 
 ALL_PINS.append(pin_p10_partial_windows)
+
+
+def _level_windows(levels, M):
+    """Rows of windows whose tau is fixed by construction: xx = yy = s/2 real, xy = yx
+    = 0, so I = s and Q = U = V = 0 (r = 0, the DS test never flags).  A window of
+    constant s has W S2/S1^2 = 1; one alternating s = 1, 3 has W S2/S1^2 = 5/4."""
+    out = []
+    for lev in levels:
+        s = np.ones(M) if lev == "A" else np.tile([1.0, 3.0], M // 2)
+        out.append(s)
+    s = np.concatenate(out)
+    vis = np.zeros((1, s.size, 4), np.complex128)
+    vis[0, :, 0] = vis[0, :, 3] = s / 2
+    return vis
+
+
+def pin_p11_online_thresholds(seed=12):
+    """P11: online per-stream SK thresholds (the build's rule for the paper's future
+    work, see oracle/adaptive.py).
+
+    (a) before n_warm clean windows nothing changes: outputs equal the fixed-threshold
+        oracle's exactly;
+    (b) with alpha = 0 the state is (count, mean tau, mean tau^2) over the windows the
+        row did not flag -- the definition of a running mean, computed with numpy;
+    (c) after warm-up a window is flagged iff tau leaves mean -/+ k sd of the earlier
+        clean windows (numpy mean and population sd) or r exceeds gamma;
+    (d) with alpha > 0, once n >= 1/alpha the mean relaxes geometrically: after N0
+        windows at level A and k at level B, mean = tau_B + (1 - alpha)^k (mu0 - tau_B)."""
+    from oracle import AdaptiveOracleStream
+    rng = np.random.default_rng(seed)
+    R, M, K, T, nblk = 12, 8, 32, 64, 6
+    vis = (rng.standard_normal((R, T * nblk, 4)) + 1j * rng.standard_normal((R, T * nblk, 4))) / math.sqrt(2)
+    vis[:, 100:120] *= 7.0
+    vis[3, 200:260, :] = 3.0 * (1 + 1j)
+    thr = dict(d=1.0, s_low=0.2, s_high=2.2, gamma=0.75, eps=EPS32)
+    # (a)
+    a = AdaptiveOracleStream(R, M, K, **thr, n_warm=10 ** 6)
+    b = OracleStream(R, M, K, **thr)
+    for k in range(nblk):
+        oa, ob = a.process(vis[:, k * T:(k + 1) * T]), b.process(vis[:, k * T:(k + 1) * T])
+        for key in ob:
+            assert np.array_equal(oa[key], ob[key]), key
+    # (b) and (c)
+    st = AdaptiveOracleStream(R, M, K, **thr, alpha=0.0, k_sigma=2.5, n_warm=12)
+    hist_tau = [[] for _ in range(R)]
+    for k in range(nblk):
+        lo_exp = np.full(R, thr["s_low"])
+        hi_exp = np.full(R, thr["s_high"])
+        for g in range(R):
+            h = np.array(hist_tau[g])
+            if h.size >= 12:
+                lo_exp[g] = h.mean() - 2.5 * h.std()
+                hi_exp[g] = h.mean() + 2.5 * h.std()
+        out = st.process(vis[:, k * T:(k + 1) * T])
+        assert np.allclose(out["s_low_used"], lo_exp, rtol=1e-12, atol=1e-12)
+        assert np.allclose(out["s_high_used"], hi_exp, rtol=1e-12, atol=1e-12)
+        exp = ~((out["tau"] >= lo_exp[:, None]) & (out["tau"] <= hi_exp[:, None])) | \
+            (out["r_re"] > thr["gamma"]) | (out["r_im"] > thr["gamma"])
+        assert np.array_equal(out["wflag"].astype(bool), exp)
+        for g in range(R):
+            hist_tau[g] += list(out["tau"][g][~out["wflag"][g].astype(bool)])
+            h = np.array(hist_tau[g])
+            n, mu, m2 = st.state[g]
+            assert n == h.size
+            if h.size:
+                assert abs(mu - h.mean()) <= 1e-12 * max(1.0, abs(h.mean()))
+                assert abs(m2 - (h * h).mean()) <= 1e-12 * max(1.0, (h * h).mean())
+    assert any(f.any() for f in [st.thresholds()[0] != thr["s_low"]])   # warm-up was reached
+    # (d)
+    alpha, N0, kB = 1.0 / 8, 16, 11
+    lead = (M * 1.0 + 1.0) / (M - 1.0)
+    tau_B = lead * (M * 5.0 * M / ((2.0 * M) ** 2 + EPS32) - 1.0)
+    v = _level_windows(["A"] * N0 + ["B"] * kB, M)
+    st = AdaptiveOracleStream(1, M, M, 1.0, -1e300, 1e300, 2.0, EPS32, alpha=alpha,
+                              n_warm=10 ** 6)
+    st.process(v[:, :N0 * M])
+    mu0, m20 = st.state[0, 1], st.state[0, 2]
+    st.process(v[:, N0 * M:])
+    q = (1.0 - alpha) ** kB
+    assert abs(st.state[0, 1] - (tau_B + q * (mu0 - tau_B))) <= 1e-13
+    assert abs(st.state[0, 2] - (tau_B ** 2 + q * (m20 - tau_B ** 2))) <= 1e-13
+    assert abs(tau_B - lead * (0.25 - EPS32 / (4.0 * M * M) * 1.25)) <= 1e-9
+
+
+ALL_PINS.append(pin_p11_online_thresholds)

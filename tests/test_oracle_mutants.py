@@ -9,6 +9,7 @@ import os
 
 import pytest
 
+import oracle
 import oracle.build
 import oracle.oracle
 import oracle_pins
@@ -101,3 +102,29 @@ def test_partial_window_pin_catches_mutant(name, monkeypatch):
     monkeypatch.setattr(oracle_pins, "OracleStream", mod.OracleStream)
     with pytest.raises((AssertionError, ValueError)):
         oracle_pins.pin_p10_partial_windows()
+
+
+# The online thresholds (oracle/adaptive.py): mistakes there must fail pin P11.
+ADAPTIVE_MUTANTS = {
+    "adaptive_updates_flagged_windows": ("                if f:\n                    continue\n", ""),
+    "adaptive_sd_without_mean": ("np.maximum(m2 - mu * mu, 0.0)", "np.maximum(m2, 0.0)"),
+    "adaptive_ignores_alpha": ("w = max(self.alpha, 1.0 / n)", "w = 1.0 / n"),
+    "adaptive_weight_alpha_only": ("w = max(self.alpha, 1.0 / n)", "w = self.alpha"),
+    "adaptive_warm_never": ("warm = n >= self.n_warm", "warm = n > 1e300"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ADAPTIVE_MUTANTS))
+def test_online_threshold_pin_catches_mutant(name, monkeypatch):
+    import types
+    import oracle.adaptive
+    old, new = ADAPTIVE_MUTANTS[name]
+    with open(oracle.adaptive.__file__) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mod = types.ModuleType("oracle._adaptive_mutant")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(text.replace(old, new), "adaptive_mutant.py", "exec"), mod.__dict__)
+    monkeypatch.setattr(oracle, "AdaptiveOracleStream", mod.AdaptiveOracleStream)
+    with pytest.raises((AssertionError, ValueError, ZeroDivisionError)):
+        oracle_pins.pin_p11_online_thresholds()
