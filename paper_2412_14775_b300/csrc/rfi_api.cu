@@ -143,6 +143,7 @@ struct rfi_batch_graph {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     cudaGraphNode_t node;
+    cudaGraphNode_t adapt_node;         // state update of adaptive contexts, or null
     const Instance *inst;
     int grid, block;
 };
@@ -408,8 +409,20 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
         e = cudaLaunchKernel(c->inst->block_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args,
                              0, st);
     }
+    if (e == cudaSuccess && c->ad && a.nwin > 0) {     // advance the online thresholds
+        const long long G = a.R / c->F;
+        e = cudaLaunchKernel(adapt_fn(), dim3((unsigned)((G + 255) / 256)), dim3(256), args, 0,
+                             st);
+    }
     if (e != cudaSuccess) return set_cuda_error(c, e, "kernel launch");
     return RFI_OK;
+}
+
+// Blocks of the batched state update of adaptive contexts: a grid-stride loop.
+int adapt_batch_grid(int device) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return std::max(sms, 1) * 4;
 }
 
 // Resident blocks of a batch kernel on the whole GPU (cached per kernel, block size
@@ -834,6 +847,9 @@ int rfi_process_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const
     void *args[] = {b};
     cudaError_t e = cudaLaunchKernel(c0->inst->batch_fn, dim3(grid), dim3(32 * c0->wpb), args, 0,
                                      static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess && c0->ad)
+        e = cudaLaunchKernel(adapt_batch_fn(), dim3(adapt_batch_grid(c0->device)), dim3(256),
+                             args, 0, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         for (int i = 0; i < n; ++i) ctxs[i]->status = RFI_ECUDA;
         return fail(RFI_ECUDA, "batch launch: %s", cudaGetErrorString(e));
@@ -871,6 +887,13 @@ int rfi_batch_graph_create(rfi_batch_graph **out, rfi_ctx *const *ctxs, int n, c
     kp.kernelParams = args;
     cudaError_t e = cudaGraphCreate(&g->graph, 0);
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&g->node, g->graph, nullptr, 0, &kp);
+    if (e == cudaSuccess && ctxs[0]->ad) {
+        cudaKernelNodeParams ka = kp;
+        ka.func = const_cast<void *>(adapt_batch_fn());
+        ka.gridDim = dim3(adapt_batch_grid(ctxs[0]->device));
+        ka.blockDim = dim3(256);
+        e = cudaGraphAddKernelNode(&g->adapt_node, g->graph, &g->node, 1, &ka);
+    }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
     delete b;
     if (e != cudaSuccess) {
@@ -902,6 +925,13 @@ int rfi_batch_graph_launch(rfi_batch_graph *g, const void *const *vis, uint32_t 
     kp.blockDim = dim3(g->block);
     kp.kernelParams = args;
     cudaError_t e = cudaGraphExecKernelNodeSetParams(g->exec, g->node, &kp);
+    if (e == cudaSuccess && g->adapt_node) {
+        cudaKernelNodeParams ka = kp;
+        ka.func = const_cast<void *>(adapt_batch_fn());
+        ka.gridDim = dim3(adapt_batch_grid(g->ctxs[0]->device));
+        ka.blockDim = dim3(256);
+        e = cudaGraphExecKernelNodeSetParams(g->exec, g->adapt_node, &ka);
+    }
     if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         for (rfi_ctx *c : g->ctxs) c->status = RFI_ECUDA;

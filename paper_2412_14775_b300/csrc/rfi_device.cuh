@@ -355,10 +355,11 @@ __device__ __forceinline__ float rowsum(float v, int PF) {
 // AD: online per-stream SK thresholds.  Each footprint row keeps a running estimate of
 // the mean and second moment of tau over its unflagged windows (weight max(alpha, 1/n)
 // for the n-th, so the first 1/alpha windows give the plain mean).  Once n >= n_warm
-// the row's SK test uses [mean - k sd, mean + k sd] instead of [s_low, s_high]; the
-// thresholds are those of the state at the start of the launch, and the state advances
-// window by window.  The DS threshold gamma stays fixed (its null, E r^2 = 1/W, does
-// not depend on the data).
+// the row's SK test uses [mean - k sd, mean + k sd] instead of [s_low, s_high]: the
+// thresholds of the state at the start of the launch.  The state then advances window
+// by window in k_adapt (rfi_adapt.cu), a light pass over the stored tau and flag bits.
+// The DS threshold gamma stays fixed (its null, E r^2 = 1/W, does not depend on the
+// data).
 template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false,
           bool TMA = false, bool VS = false, bool PW = false, bool AD = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
@@ -380,20 +381,9 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     char *const hwp = PW ? a.hw + rowc * (long long)a.M * SB : nullptr;
     const int nbits = PW ? a.nwin * a.M : a.T;          // flagged samples of this call
     const bool lead = active && j == 0;     // writes the row's outputs
-    float ad_n = 0.f, ad_mu = 0.f, ad_m2 = 0.f, slo = 0.f, shi = 0.f;
-    float *const ad_row = AD ? a.adapt + (rowc / a.F) * 4 : nullptr;
-    if constexpr (AD) {
-        ad_n = ad_row[0];
-        ad_mu = ad_row[1];
-        ad_m2 = ad_row[2];
-        slo = a.s_low;
-        shi = a.s_high;
-        if (ad_n >= a.n_warm) {
-            const float sd = __fsqrt_rn(fmaxf(ad_m2 - ad_mu * ad_mu, 0.f));
-            slo = ad_mu - a.k_sigma * sd;
-            shi = ad_mu + a.k_sigma * sd;
-        }
-    }
+    // the row's SK interval (set below, from the state at the start of the launch; the
+    // state is advanced afterwards by k_adapt from the statistics and flags stored here)
+    float slo = 0.f, shi = 0.f;
 
     float acc[8];            // running bin sums of (I, Q, U, V), re and im
     float cnt = 0.f;
@@ -460,6 +450,17 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     int w = 0, cw = 0;
     Unit<UB> ua[CH], ub[DB ? CH : 1];
     if constexpr (!TMA && !PW) load_chunk(0, ua);
+    if constexpr (AD) {
+        // after the first loads are in flight, and without a branch, so that the wait
+        // for the state overlaps them (requesting the state before the data loads, or
+        // branching on it, measured 6-15 % slower)
+        const float *const ad_row = a.adapt + (rowc / a.F) * 4;
+        const float n0 = ad_row[0], mu0 = ad_row[1], m20 = ad_row[2];
+        const float sd = __fsqrt_rn(fmaxf(m20 - mu0 * mu0, 0.f));
+        const bool warm = n0 >= a.n_warm;
+        slo = warm ? mu0 - a.k_sigma * sd : a.s_low;
+        shi = warm ? mu0 + a.k_sigma * sd : a.s_high;
+    }
 
     auto consume = [&](const Unit<UB>(&u)[CH]) {
 #pragma unroll
@@ -502,14 +503,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
                 f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
                     !(r_im <= a.gamma);
         }
-        if constexpr (AD) {
-            if (!f) {       // the running moments follow the windows judged clean
-                ad_n += 1.f;
-                const float wgt = fmaxf(a.alpha, __frcp_rn(ad_n));
-                ad_mu = ad_mu + wgt * (tau - ad_mu);
-                ad_m2 = ad_m2 + wgt * (tau * tau - ad_m2);
-            }
-        }
+
         if (vec_stats) {
             tq = make_float4(tq.y, tq.z, tq.w, tau);
             rq = make_float4(rq.y, rq.z, rq.w, r_re);
@@ -711,13 +705,6 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         const int n16 = (a.phase + a.T - s0) * (SB / 16);
         if (active)
             for (int k = j; k < n16; k += P) dst[k] = src[k];
-    }
-    if constexpr (AD) {
-        if (st_lead) {
-            ad_row[0] = ad_n;
-            ad_row[1] = ad_mu;
-            ad_row[2] = ad_m2;
-        }
     }
     if (wib != 0 && active) {
         float *cp = a.carry + (row * P + j) * 9;

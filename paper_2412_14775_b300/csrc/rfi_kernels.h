@@ -25,6 +25,10 @@ InstanceTable instances_f32_pw();     // partial windows (rfi_inst_pw_f32.cu)
 InstanceTable instances_f16_pw();     // partial windows (rfi_inst_pw_f16.cu)
 InstanceTable instances_f32_ad();     // online SK thresholds (rfi_inst_ad_f32.cu)
 InstanceTable instances_f16_ad();     // online SK thresholds (rfi_inst_ad_f16.cu)
+// State update of adaptive contexts after a flagging launch (rfi_adapt.cu): one thread
+// per footprint row; k_adapt takes a StreamArgs, k_adapt_batch a BatchArgs.
+const void *adapt_fn();
+const void *adapt_batch_fn();
 
 // The shared-memory (TMA) loader: one lane per row, direct-load twin for batches.
 struct TmaInstance {
