@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import synth
-from paper_2412_14775_b300 import RfiStream, binding, default_thresholds
+from paper_2412_14775_b300 import RfiStream, autotune, binding, default_thresholds
 from paper_2412_14775_b300.binding import RfiError
 from parity import compare, gpu_to_numpy, run_gpu, to_device_rows
 
@@ -150,12 +150,15 @@ def test_shapes(dtype, N, C, M, K, Ts, opts):
                                      ("f16", 64)])
 def test_lofar_scale_sampled_rows(dtype, M):
     """62 stations (1953 baselines), 64 channels, T = 256, K = 256 in the launch shape
-    the bench times; the oracle checks a seeded sample of 2048 rows one by one."""
+    the bench times (the committed tuning table); the oracle checks a seeded sample of
+    2048 rows one by one."""
     K = 256
     thr = default_thresholds(M)
     d = synth.lofar_block(seed=2)
-    st = RfiStream(62, 64, M, K, thr, dtype)
     vis = to_device_rows(d["vis"], dtype)
+    best, _ = autotune.tune(62, 64, M, K, thr, dtype, vis, cache_path=autotune.TUNED_PATH,
+                            write_cache=False)
+    st = RfiStream(62, 64, M, K, thr, dtype, **autotune.options_of(best))
     g = run_gpu(st, vis)
     del vis
     rows = np.sort(np.random.default_rng(17).choice(st.R, size=2048, replace=False))
@@ -165,6 +168,48 @@ def test_lofar_scale_sampled_rows(dtype, M):
     rep = compare(gs, o, thr, M, K)
     print(f"lofar {dtype} M={M}", rep)
     st.close()
+
+
+def test_batched_uneven_full_size_sampled():
+    """The batched workload at full size: 8 binary16 subbands (stations 24..76,
+    channels 16..128, T = 256) in one persistent launch replayed from a CUDA graph, in
+    the launch shape the bench times; 256 seeded rows of every subband against the
+    oracle, and the second replay equal to the streams launched one by one."""
+    M, K, T = 16, 256, 256
+    thr = default_thresholds(M)
+    geo = list(zip(synth.BATCH_STATIONS, synth.BATCH_CHANNELS))
+    vis = [synth.generate.device_block(n, c, T, seed=300 + i) for i, (n, c) in enumerate(geo)]
+    best, _ = autotune.tune(62, 64, M, K, thr, "f16", vis[3], cache_path=autotune.TUNED_PATH,
+                            write_cache=False)
+    opts = {k: v for k, v in autotune.options_of(best).items() if k != "max_registers"}
+    streams = [RfiStream(n, c, M, K, thr, "f16", **opts) for n, c in geo]
+    solo = [RfiStream(n, c, M, K, thr, "f16", **opts) for n, c in geo]
+    outs = [s.alloc_outputs(T) for s in streams]
+    g = binding.rfi_batch_graph_create([s.ctx for s in streams], [T] * len(streams))
+    binding.rfi_batch_graph_launch(g, vis, [o["flags"] for o in outs], [o["avg"] for o in outs],
+                                   [o["weight"] for o in outs], [o["stats"] for o in outs])
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(23)
+    for i, (s, o) in enumerate(zip(streams, outs)):
+        rows = np.sort(rng.choice(s.R, size=256, replace=False))
+        gs = {k: v[rows] for k, v in gpu_to_numpy(o).items()}
+        host = vis[i][torch.from_numpy(rows).cuda()].cpu().numpy()       # float16 values
+        orc = oracle.OracleStream(len(rows), M, K, **thr).process(host)
+        compare(gs, orc, thr, M, K)
+    # a second replay (the blocks continue the streams) against one launch per stream
+    for st, v in zip(solo, vis):
+        st.process(v)
+    outs2 = [s.alloc_outputs(T) for s in streams]
+    binding.rfi_batch_graph_launch(g, vis, [o["flags"] for o in outs2], [o["avg"] for o in outs2],
+                                   [o["weight"] for o in outs2], [o["stats"] for o in outs2])
+    exp = [st.process(v) for st, v in zip(solo, vis)]
+    torch.cuda.synchronize()
+    for e, o in zip(exp, outs2):
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(e[k], o[k]), k
+    binding.rfi_batch_graph_destroy(g)
+    for s in streams + solo:
+        s.close()
 
 
 def test_block_split_bit_identical():
