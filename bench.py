@@ -179,11 +179,25 @@ def reference_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(WORKLOAD, dtype="complex64"),
             "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": f"{n_rows} of {R} rows x {T} samples per step, "
                                        f"row ranges on {cores} threads"},
             "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def cpu_model():
+    """The host CPU's model name (Linux), or the platform's processor string."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
 
 
 def host_threads():
@@ -232,7 +246,7 @@ def cpu_baseline(seconds_target=10.0):
     cores = host_threads()
     dtn = oracle_threads(rows[:n], M, K, thr, cores)
     return {"value": n * T / dtn, "unit": "samples/s", "cores": cores, "kind": "oracle",
-            "single_thread_value": n * T / dt1,
+            "single_thread_value": n * T / dt1, "cpu_model": cpu_model(),
             "sample": f"first {n} of {R} rows x {T} samples of the FP32 block: "
                       f"{dtn:.2f} s on {cores} threads (row ranges), "
                       f"{dt1:.1f} s single-threaded"}
