@@ -612,6 +612,13 @@ def main():
     bytes_launch = algo_bytes(R, T, M, K, n_out, sbytes)
     kern = statistics.mean(per)
     achieved = bytes_launch / kern / 1e9
+    # windows flagged by each test on the last timed block (from the kernel's statistics)
+    stt = out["stats"]
+    sk = ~((stt[0] >= thr["s_low"]) & (stt[0] <= thr["s_high"]))
+    dre, dim = ~(stt[1] <= thr["gamma"]), ~(stt[2] <= thr["gamma"])
+    flag_fractions = {"sk": sk.float().mean().item(), "ds_re": dre.float().mean().item(),
+                      "ds_im": dim.float().mean().item(),
+                      "any": (sk | dre | dim).float().mean().item()}
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -699,7 +706,7 @@ def main():
             "frac_of_8tbs": achieved / 8000.0,
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": args.steps,
-            "real_time_factor": BLOCK_SECONDS / kern,
+            "real_time_factor": BLOCK_SECONDS / kern, "flag_fractions": flag_fractions,
         }
         line.update(extras)
         print(json.dumps(line), flush=True)

@@ -11,7 +11,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "librfi.so")
+# RFI_LIBRARY selects another build of the library (the debug-bounds build, say)
+LIB_PATH = os.environ.get("RFI_LIBRARY") or os.path.join(HERE, "_lib", "librfi.so")
 
 RFI_C64 = 0
 RFI_C32H = 1

@@ -28,20 +28,27 @@ def _inputs():
     return files
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if stale) and return the path of librfi.so."""
-    if not force and os.path.exists(LIB):
+# The debug-bounds build: every global access of the kernels checked against its
+# buffer's extent (violations are skipped and reported by rfi_check).
+DEBUG_LIB = os.path.join(HERE, "_lib", "librfi_debug.so")
+
+
+def build(force: bool = False, verbose: bool = False, debug_bounds: bool = False) -> str:
+    """Compile (if stale) and return the path of librfi.so (or of librfi_debug.so)."""
+    lib = DEBUG_LIB if debug_bounds else LIB
+    if not force and os.path.exists(lib):
         newest = max(os.path.getmtime(f) for f in _inputs())
-        if os.path.getmtime(LIB) >= newest:
-            return LIB
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    objdir = os.path.join(HERE, "_lib", "obj")
+        if os.path.getmtime(lib) >= newest:
+            return lib
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    objdir = os.path.join(HERE, "_lib", "obj_debug" if debug_bounds else "obj")
     os.makedirs(objdir, exist_ok=True)
+    extra = ["-DRFI_DEBUG_BOUNDS"] if debug_bounds else []
     # translation units compile in parallel, then one link step
     procs, objs = [], []
     for src in SOURCES:
         obj = os.path.join(objdir, src.replace(".cu", f".{os.getpid()}.o"))
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", "-o", obj, os.path.join(CSRC, src)]
+        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", "-o", obj, os.path.join(CSRC, src)]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append(subprocess.Popen(cmd))
@@ -49,13 +56,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     failed = [p.wait() for p in procs]
     if any(failed):
         raise RuntimeError(f"nvcc failed for {[s for s, r in zip(SOURCES, failed) if r]}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([NVCC, *ARCH, "--cudart", "static", "-shared", "-o", tmp, *objs])
     for o in objs:
         os.remove(o)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose="-v" in sys.argv))
+    print(build(force=True, verbose="-v" in sys.argv, debug_bounds="--debug-bounds" in sys.argv))

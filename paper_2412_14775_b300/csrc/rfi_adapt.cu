@@ -15,6 +15,11 @@ __device__ void adapt_row(const StreamArgs &a, long long g) {
     float *st = a.adapt + g * 4;
     const float *tau_row = a.stats + g * a.nwin;                 // plane 0: tau
     const uint32_t *fl = a.flags + g * a.F * (long long)a.Wpr;   // first row of the footprint
+    // debug-bounds build: the row's state, statistics and flag words lie in their buffers
+    if (!rfi_in(st, 12, a.adapt, (a.R / a.F) * 16ll, a.err) ||
+        !rfi_in(tau_row, 4ll * a.nwin, a.stats, (a.R / a.F) * a.nwin * 4ll, a.err) ||
+        !rfi_in(fl, 4ll * a.Wpr, a.flags, a.R * a.Wpr * 4ll, a.err))
+        return;
     float n = st[0], mu = st[1], m2 = st[2];
     // windows in groups of 8: the group's loads are issued together, then the state
     // runs over the group in window order

@@ -12,6 +12,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -151,6 +152,15 @@ struct rfi_batch_graph {
 namespace {
 
 int sample_bytes(rfi_dtype dt) { return dt == RFI_C64 ? 32 : 16; }
+
+// An NVTX range over one entry point (visible in Nsight timelines; a no-op without a
+// tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 size_t adapt_bytes(const rfi_ctx *c) { return sizeof(float) * 4 * (size_t)(c->R / c->F); }
 
 int check_ctx(const rfi_ctx *ctx) {
@@ -536,6 +546,7 @@ const char *rfi_last_error(void) { return g_last_error; }
 
 int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int avg_K,
                   const rfi_thresholds *thr, rfi_dtype dtype, const rfi_options *opt) {
+    NvtxRange nvtx("rfi_create");
     if (!out) return fail(RFI_EINVAL, "null output handle");
     *out = nullptr;
     if (stations < 1 || channels < 1) return fail(RFI_EINVAL, "stations and channels must be >= 1");
@@ -769,6 +780,7 @@ int rfi_adaptive_state(rfi_ctx *ctx, float *host, size_t n_floats, int write, vo
 
 int rfi_process_block(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags, float *avg,
                       float *weight, float *stats, void *stream) {
+    NvtxRange nvtx("rfi_process_block");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if ((rc = check_block_args(ctx, vis, T, flags, avg, weight, stats, true))) return rc;
@@ -780,6 +792,7 @@ int rfi_process_block(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags, flo
 
 int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags, float *avg,
                            float *weight, float *stats, void *stream) {
+    NvtxRange nvtx("rfi_process_block_host");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if ((rc = check_block_args(ctx, vis, T, flags, avg, weight, stats, false))) return rc;
@@ -838,6 +851,7 @@ int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags
 int rfi_process_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *T,
                       uint32_t *const *flags, float *const *avg, float *const *weight,
                       float *const *stats, void *stream) {
+    NvtxRange nvtx("rfi_process_batch");
     static thread_local BatchArgs tb;
     BatchArgs *b = &tb;
     int rc = build_batch(ctxs, n, vis, T, flags, avg, weight, stats, true, b);
@@ -913,6 +927,7 @@ int rfi_batch_graph_create(rfi_batch_graph **out, rfi_ctx *const *ctxs, int n, c
 int rfi_batch_graph_launch(rfi_batch_graph *g, const void *const *vis, uint32_t *const *flags,
                            float *const *avg, float *const *weight, float *const *stats,
                            void *stream) {
+    NvtxRange nvtx("rfi_batch_graph_launch");
     if (!g || !is_live(g)) return fail(RFI_ESTATE, "not a live batch graph");
     static thread_local BatchArgs tb;
     BatchArgs *b = &tb;
@@ -1056,11 +1071,16 @@ int rfi_check(rfi_ctx *ctx, void *stream) {
         e = cudaMemcpy(&err, reinterpret_cast<int *>(ctx->counter + 2), sizeof(int),
                        cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_check");
-    if (err) {
+    if (err & 1) {
         ctx->status = RFI_ETIMEOUT;
         return fail(RFI_ETIMEOUT, "a bounded wait in the kernel gave up (error word %d); "
                                   "results of that launch are incomplete; rfi_reset clears it",
                     err);
+    }
+    if (err) {
+        ctx->status = RFI_ESTATE;
+        return fail(RFI_ESTATE, "the debug-bounds build caught an access outside its buffer "
+                                "(error word %d) and skipped it; rfi_reset clears it", err);
     }
     return RFI_OK;
 }

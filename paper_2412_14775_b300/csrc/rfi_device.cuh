@@ -157,6 +157,25 @@ __device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
         : "l"(p));
 }
 
+// ---- debug-bounds build (-DRFI_DEBUG_BOUNDS) -----------------------------------
+// Every global access of the kernels is checked against the extent that the launch's
+// own arguments give its buffer; an access outside it is skipped (a load reads zeros)
+// and bit 1 of the context's error word is set, read by rfi_check.  In the normal build
+// rfi_in is the constant true and the checks compile away.
+__device__ __forceinline__ bool rfi_in(const void *p, long long n, const void *base,
+                                       long long extent, int *err) {
+#ifdef RFI_DEBUG_BOUNDS
+    const char *c = static_cast<const char *>(p);
+    const char *b = static_cast<const char *>(base);
+    if (b != nullptr && c >= b && c + n <= b + extent) return true;
+    if (err) atomicOr(err, 2);
+    return false;
+#else
+    (void)p; (void)n; (void)base; (void)extent; (void)err;
+    return true;
+#endif
+}
+
 // The raw-sample carry of partial windows is read, then rewritten, by the same launch:
 // coherent loads, ordered before the later stores.
 __device__ __forceinline__ void load_unit_rw(const char *p, Unit<32> &u) {
@@ -381,6 +400,15 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     char *const hwp = PW ? a.hw + rowc * (long long)a.M * SB : nullptr;
     const int nbits = PW ? a.nwin * a.M : a.T;          // flagged samples of this call
     const bool lead = active && j == 0;     // writes the row's outputs
+    // extents (bytes) of the launch's buffers, for the debug-bounds build
+    const long long vis_ext = a.R * (long long)a.T * SB;
+    const long long hw_ext = a.R * (long long)a.M * SB;
+    const long long carry_ext = a.R * P * 9 * 4ll;
+    const long long stats_ext = (2 * a.stats_plane + (a.R / a.F) * a.nwin) * 4ll;
+    const long long flags_ext = a.R * a.Wpr * 4ll;
+    const long long avg_ext = a.R * a.n_out * 32ll;
+    const long long weight_ext = a.R * a.n_out * 4ll;
+    const long long adapt_ext = (a.R / a.F) * 16ll;
     // the row's SK interval (set below, from the state at the start of the launch; the
     // state is advanced afterwards by k_adapt from the statistics and flags stored here)
     float slo = 0.f, shi = 0.f;
@@ -391,9 +419,11 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     for (int c = 0; c < 8; ++c) acc[c] = 0.f;
     if (a.bin_pos0 != 0) {
         const float *cp = a.carry + (rowc * P + j) * 9;   // open-bin Stokes sums and count
+        if (rfi_in(cp, 36, a.carry, carry_ext, a.err)) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = cp[c];
-        cnt = cp[8];
+            for (int c = 0; c < 8; ++c) acc[c] = cp[c];
+            cnt = cp[8];
+        }
     }
     // Per-row cursors and counters, set up once per task so that the per-window
     // bookkeeping is a handful of integer operations.
@@ -426,7 +456,8 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     const unsigned wbytes = (unsigned)a.M * SB;
     if (pf) {
         const int hi = min(a.nwin, (1 + a.pf_groups) * a.pf_windows);
-        if (hi > 1) prefetch_l2(fp + wbytes, (unsigned)(hi - 1) * wbytes);
+        if (hi > 1 && rfi_in(fp + wbytes, (hi - 1) * (long long)wbytes, a.vis, vis_ext, a.err))
+            prefetch_l2(fp + wbytes, (unsigned)(hi - 1) * wbytes);
     }
     int pf_next = a.pf_windows;
 
@@ -440,7 +471,11 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     const char *cp_ = fp + j * UB;
     auto load_chunk = [&](int q, Unit<UB>(&u)[CH]) {
 #pragma unroll
-        for (int c = 0; c < CH; ++c) load_unit(cp_ + (long long)q * CHB + c * (P * UB), u[c]);
+        for (int c = 0; c < CH; ++c) {
+            const char *p = cp_ + (long long)q * CHB + c * (P * UB);
+            if (rfi_in(p, UB, a.vis, vis_ext, a.err)) load_unit(p, u[c]);
+            else u[c] = Unit<UB>{};
+        }
     };
     WinAcc A;
     const float2 zero2 = make_float2(0.f, 0.f);
@@ -455,7 +490,9 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         // for the state overlaps them (requesting the state before the data loads, or
         // branching on it, measured 6-15 % slower)
         const float *const ad_row = a.adapt + (rowc / a.F) * 4;
-        const float n0 = ad_row[0], mu0 = ad_row[1], m20 = ad_row[2];
+        const bool ad_ok = rfi_in(ad_row, 12, a.adapt, adapt_ext, a.err);
+        const float n0 = ad_ok ? ad_row[0] : 0.f, mu0 = ad_ok ? ad_row[1] : 0.f;
+        const float m20 = ad_ok ? ad_row[2] : 0.f;
         const float sd = __fsqrt_rn(fmaxf(m20 - mu0 * mu0, 0.f));
         const bool warm = n0 >= a.n_warm;
         slo = warm ? mu0 - a.k_sigma * sd : a.s_low;
@@ -508,12 +545,14 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             tq = make_float4(tq.y, tq.z, tq.w, tau);
             rq = make_float4(rq.y, rq.z, rq.w, r_re);
             iq = make_float4(iq.y, iq.z, iq.w, r_im);
-            if ((w & 3) == 3 && st_lead) {
+            if ((w & 3) == 3 && st_lead && rfi_in(st_row + w - 3, 16, a.stats, stats_ext, a.err) &&
+                rfi_in(st_row + w - 3 + 2 * plane, 16, a.stats, stats_ext, a.err)) {
                 *reinterpret_cast<float4 *>(st_row + w - 3) = tq;
                 *reinterpret_cast<float4 *>(st_row + w - 3 + plane) = rq;
                 *reinterpret_cast<float4 *>(st_row + w - 3 + 2 * plane) = iq;
             }
-        } else if (st_lead) {
+        } else if (st_lead && rfi_in(st_row + w, 4, a.stats, stats_ext, a.err) &&
+                   rfi_in(st_row + w + 2 * plane, 4, a.stats, stats_ext, a.err)) {
             st_row[w] = tau;
             st_row[w + plane] = r_re;
             st_row[w + 2 * plane] = r_im;
@@ -525,8 +564,10 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             if (fbit == 32) {
                 if (vec_flags) {
                     fq = make_uint4(fq.y, fq.z, fq.w, fword);
-                    if ((fwi & 3) == 3 && lead) *reinterpret_cast<uint4 *>(fl_row + fwi - 3) = fq;
-                } else if (lead) {
+                    if ((fwi & 3) == 3 && lead &&
+                        rfi_in(fl_row + fwi - 3, 16, a.flags, flags_ext, a.err))
+                        *reinterpret_cast<uint4 *>(fl_row + fwi - 3) = fq;
+                } else if (lead && rfi_in(fl_row + fwi, 4, a.flags, flags_ext, a.err)) {
                     fl_row[fwi] = fword;
                 }
                 ++fwi;
@@ -534,7 +575,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
                 fbit = 0;
             }
         } else if (fmode == 1) {
-            if (lead)
+            if (lead && rfi_in(fl_row + fwi, 4ll * words_per_window, a.flags, flags_ext, a.err))
                 for (int k = 0; k < words_per_window; ++k) fl_row[fwi + k] = f ? FULL : 0u;
             fwi += words_per_window;
         } else {
@@ -546,7 +587,8 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
                 if (f) fword |= (nb == 32 ? FULL : ((1u << nb) - 1u)) << b0;
                 lo += nb;
                 if ((lo & 31) == 0) {
-                    if (lead) fl_row[(lo - 1) >> 5] = fword;
+                    if (lead && rfi_in(fl_row + ((lo - 1) >> 5), 4, a.flags, flags_ext, a.err))
+                        fl_row[(lo - 1) >> 5] = fword;
                     fword = 0;
                 }
             }
@@ -565,7 +607,8 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
 #pragma unroll
             for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
             const float n = allsum<P>(cnt);
-            if (lead) {
+            if (lead && rfi_in(a.avg + (row * a.n_out + bin) * 8, 32, a.avg, avg_ext, a.err) &&
+                rfi_in(a.weight + row * a.n_out + bin, 4, a.weight, weight_ext, a.err)) {
                 // tot holds sums of (I, Q, U, V); the correlations are xx = (I + Q)/2,
                 // yy = (I - Q)/2, xy = (U - jV)/2, yx = (U + jV)/2
                 float4 *ap = reinterpret_cast<float4 *>(a.avg + (row * a.n_out + bin) * 8);
@@ -589,7 +632,10 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         if (pf && w == pf_next) {
             const int g0 = w + a.pf_groups * a.pf_windows;
             const int g1 = min(a.nwin, g0 + a.pf_windows);
-            if (g0 < g1) prefetch_l2(fp + (long long)g0 * wbytes, (unsigned)(g1 - g0) * wbytes);
+            if (g0 < g1 &&
+                rfi_in(fp + (long long)g0 * wbytes, (g1 - g0) * (long long)wbytes, a.vis, vis_ext,
+                       a.err))
+                prefetch_l2(fp + (long long)g0 * wbytes, (unsigned)(g1 - g0) * wbytes);
             pf_next += a.pf_windows;
         }
     };
@@ -604,8 +650,13 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
                     const int off = q * CHB + c * (P * UB) + j * UB;
-                    if (off < a.phase * SB) load_unit_rw(hwp + off, u[c]);
-                    else load_unit(fp + off, u[c]);
+                    if (off < a.phase * SB) {
+                        if (rfi_in(hwp + off, UB, a.hw, hw_ext, a.err)) load_unit_rw(hwp + off, u[c]);
+                        else u[c] = Unit<UB>{};
+                    } else {
+                        if (rfi_in(fp + off, UB, a.vis, vis_ext, a.err)) load_unit(fp + off, u[c]);
+                        else u[c] = Unit<UB>{};
+                    }
                 }
                 consume(u);
             }
@@ -636,7 +687,8 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             const unsigned bytes = (unsigned)(min(G, a.nwin - w0) * a.M * SB);
             if (lane == 0) mbar_arrive_expect_tx(&bars[st], bytes * n_active + a.tx_extra);
             __syncwarp();
-            if (active)
+            // (a copy skipped by the debug-bounds check leaves its stage wait to time out)
+            if (active && rfi_in(rp + (size_t)w0 * a.M * SB, bytes, a.vis, vis_ext, a.err))
                 tma_load_1d(wbuf + ((size_t)st * 32 + lane) * a.pitch, rp + (size_t)w0 * a.M * SB,
                             bytes, &bars[st]);
         };
@@ -692,7 +744,8 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     }
     // a last, partly filled flag word (nwin M not a multiple of 32)
     if (nbits & 31) {
-        if (lead) fl_row[nbits >> 5] = fword;
+        if (lead && rfi_in(fl_row + (nbits >> 5), 4, a.flags, flags_ext, a.err))
+            fl_row[nbits >> 5] = fword;
     }
     // samples after the last whole window (window frame [max(nbits, phase), phase + T))
     // wait in the raw-sample carry for the next block; the window-0 loads above were
@@ -703,10 +756,11 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         const uint4 *src = reinterpret_cast<const uint4 *>(fp + (long long)s0 * SB);
         uint4 *dst = reinterpret_cast<uint4 *>(hwp + (long long)(s0 - nbits) * SB);
         const int n16 = (a.phase + a.T - s0) * (SB / 16);
-        if (active)
+        if (active && rfi_in(src, 16ll * n16, a.vis, vis_ext, a.err) &&
+            rfi_in(dst, 16ll * n16, a.hw, hw_ext, a.err))
             for (int k = j; k < n16; k += P) dst[k] = src[k];
     }
-    if (wib != 0 && active) {
+    if (wib != 0 && active && rfi_in(a.carry + (row * P + j) * 9, 36, a.carry, carry_ext, a.err)) {
         float *cp = a.carry + (row * P + j) * 9;
 #pragma unroll
         for (int c = 0; c < 8; ++c) cp[c] = acc[c];

@@ -41,7 +41,8 @@ def _check_stream(stations, channels, M, K, Ts, dtype, thr=None, seed=3, **opts)
         o = orc.process(_oracle_input(blk, dtype))
         reps.append(compare(g, o, thr, M, K, n_seen=n_seen, F=F))
         t0 += T
-    st.close()
+    binding.rfi_check(st.ctx)           # no error word (in the debug-bounds build: no
+    st.close()                          # access outside its buffer)
     return reps
 
 
