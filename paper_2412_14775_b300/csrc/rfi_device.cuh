@@ -344,16 +344,6 @@ __device__ __forceinline__ float allsum(float v) {
     return v;
 }
 
-// Continue an allsum<P> over the F adjacent rows of a footprint (their lanes form one
-// aligned block of P*F lanes); PF = P * F is warp-uniform.
-template <int P>
-__device__ __forceinline__ float rowsum(float v, int PF) {
-#pragma unroll
-    for (int o = P; o < 32; o <<= 1)
-        if (o < PF) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-
 // ---- one row group of one stream ---------------------------------------------
 // DT: input dtype; SPU: samples per load unit (1 or 2); P: lanes per row;
 // CH: load units issued together per lane; KAHAN: compensated S1, S2.
@@ -518,9 +508,22 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         float qr = allsum<P>(A.q.x), ur = allsum<P>(A.u.x), vr = allsum<P>(A.v.x);
         float qi = allsum<P>(A.q.y), ui = allsum<P>(A.u.y), vi = allsum<P>(A.v.y);
         if (PF > P) {
-            S1 = rowsum<P>(S1, PF); S2 = rowsum<P>(S2, PF);
-            qr = rowsum<P>(qr, PF); ur = rowsum<P>(ur, PF); vr = rowsum<P>(vr, PF);
-            qi = rowsum<P>(qi, PF); ui = rowsum<P>(ui, PF); vi = rowsum<P>(vi, PF);
+            // continue the butterfly over the F adjacent rows of the footprint (their
+            // lanes form one aligned block of P*F lanes): one uniform test per step for
+            // all eight sums
+#pragma unroll
+            for (int o = P; o < 32; o <<= 1) {
+                if (o < PF) {
+                    S1 += __shfl_xor_sync(FULL, S1, o);
+                    S2 += __shfl_xor_sync(FULL, S2, o);
+                    qr += __shfl_xor_sync(FULL, qr, o);
+                    ur += __shfl_xor_sync(FULL, ur, o);
+                    vr += __shfl_xor_sync(FULL, vr, o);
+                    qi += __shfl_xor_sync(FULL, qi, o);
+                    ui += __shfl_xor_sync(FULL, ui, o);
+                    vi += __shfl_xor_sync(FULL, vi, o);
+                }
+            }
         }
         float tau, r_re, r_im;
         bool f;
