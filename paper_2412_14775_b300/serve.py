@@ -37,30 +37,38 @@ class _Stream:
         self.queue = collections.deque()          # (arrival_time, seq)
         self.busy = False
         self.done = 0
-        # outputs: flags and stats have a fixed shape; a block completes between
-        # floor(T/K) and floor(T/K) + 1 averaging bins, so avg/weight storage is sized
-        # for the larger count and viewed at this block's exact count
+        # outputs: a block completes between floor(T/K) and floor(T/K) + 1 averaging
+        # bins and, with partial windows, between floor(T/M) and floor((T + M - 1)/M)
+        # windows; the storage is sized for the larger counts and viewed at this
+        # block's exact ones
         import torch
-        R = self.st.R
+        R, F = self.st.R, self.st.F
         self.n_out_max = T // K + 1
+        self.n_win_max = (T + M - 1) // M
+        words_max = (self.n_win_max * M + 31) // 32
+        dev = blocks[0].device
         self.out_pool = []
         for _ in range(2):
-            o = self.st.alloc_outputs(T)
-            o["avg_store"] = torch.empty(R * self.n_out_max * 8, device=o["flags"].device)
-            o["weight_store"] = torch.empty(R * self.n_out_max, device=o["flags"].device)
-            self.out_pool.append(o)
+            self.out_pool.append(dict(
+                flags_store=torch.empty(R * words_max, dtype=torch.int32, device=dev),
+                stats_store=torch.empty(3 * (R // F) * self.n_win_max, device=dev),
+                avg_store=torch.empty(R * self.n_out_max * 8, device=dev),
+                weight_store=torch.empty(R * self.n_out_max, device=dev)))
         self.out_next = 0
         self.bytes_in = blocks[0].numel() * blocks[0].element_size()
-        o = self.out_pool[0]
-        self.bytes_out = sum(o[k].numel() * o[k].element_size()
-                             for k in ("flags", "stats", "avg_store", "weight_store"))
+        self.bytes_out = sum(v.numel() * v.element_size() for v in self.out_pool[0].values())
 
     def outputs(self):
-        """Output buffers for the next block, shaped for its number of completed bins."""
+        """Output buffers for the next block, shaped for its numbers of completed
+        windows and bins."""
         o = self.out_pool[self.out_next]
         self.out_next = (self.out_next + 1) % len(self.out_pool)
-        R, n = self.st.R, self.st.outputs_for(self.T)
-        return dict(flags=o["flags"], stats=o["stats"],
+        R, F, M = self.st.R, self.st.F, self.st.M
+        n = self.st.outputs_for(self.T)
+        nw = self.st.windows_for(self.T)[0]
+        words = (nw * M + 31) // 32
+        return dict(flags=o["flags_store"][:R * words].view(R, words),
+                    stats=o["stats_store"][:3 * (R // F) * nw].view(3, R // F, nw),
                     avg=o["avg_store"][:R * n * 8].view(R, n, 4, 2),
                     weight=o["weight_store"][:R * n].view(R, n))
 

@@ -11,8 +11,14 @@ from paper_2412_14775_b300.serve import ServingLoop
 pytestmark = pytest.mark.gpu
 
 
-def test_serving_mix_equals_solo():
-    M, K, T = 16, 32, 48          # bins of 32 straddle blocks of 48: the carry is exercised
+@pytest.mark.parametrize("options,T", [({}, 48), ({"adaptive": 1}, 48),
+                                       ({"partial_windows": 1}, 40)],
+                         ids=["fixed", "online_thresholds", "partial_windows"])
+def test_serving_mix_equals_solo(options, T):
+    """With online thresholds the per-stream threshold state lives on the device too and
+    advances with every block; with partial windows blocks of 40 samples leave windows
+    of 16 open between blocks.  In the mix exactly as alone."""
+    M, K = 16, 32                 # bins of 32 straddle the blocks: the carry is exercised
     cfgs = [dict(stations=n, channels=c, rho=r) for n, c, r in
             ((5, 4, 3.0), (9, 8, 2.0), (7, 16, 4.0), (12, 4, 1.5), (4, 8, 3.5), (8, 16, 2.5))]
     thr = default_thresholds(M)
@@ -20,7 +26,10 @@ def test_serving_mix_equals_solo():
                for k in range(3)] for i, c in enumerate(cfgs)]
     loop = ServingLoop(cfgs, M=M, K=K, T=T, thresholds=thr, dtype="f16", block_seconds=0.01,
                        max_batch=4, cuda_streams=3, record_outputs=True, blocks=blocks,
-                       hbm_budget_bytes=1 << 30)
+                       hbm_budget_bytes=1 << 30, options=options)
+    if options.get("adaptive"):
+        for s in loop.streams:
+            s.st.set_adaptation(alpha=1.0 / 16, k_sigma=3.0, n_warm=4)
     stats = loop.run(1.0, seed=3)
     assert stats["blocks"] > 200
     assert stats["mean_batch"] > 1.0, stats          # blocks were batched together
@@ -30,9 +39,11 @@ def test_serving_mix_equals_solo():
         assert [k for k, _ in got] == list(range(len(got)))
         solo = RfiStream(cfg["stations"], cfg["channels"], M, K, thr, "f16",
                          lanes_per_row=opts["lanes_per_row"],
-                         warps_per_block=opts["warps_per_block"])
+                         warps_per_block=opts["warps_per_block"], **options)
+        if options.get("adaptive"):
+            solo.set_adaptation(alpha=1.0 / 16, k_sigma=3.0, n_warm=4)
         for k, mixed in got:
-            o = solo.process(blocks[i][k % 3])
+            o = solo.process(blocks[i][k % 3].contiguous())
             torch.cuda.synchronize()
             for name in ("flags", "avg", "weight", "stats"):
                 assert np.array_equal(o[name].cpu().numpy(), mixed[name]), (i, k, name)
