@@ -89,7 +89,8 @@ typedef enum {
  *                  compute and copy out overlap across chunks); 0 = 4.
  *   compensated    Kahan-compensated S1 and S2 (the SK moments): 1 = on, -1 = off,
  *                  0 = on for windows of M >= 64 samples.
- *   prefetch_bytes   size of one L2 bulk prefetch per row, rounded down to whole
+ *   prefetch_bytes   size of one L2 prefetch group per row (128-byte lines split over
+ *                  the row's lanes), rounded down to whole
  *                  windows (at least one); a multiple of 16; 0 = 1024.
  *   prefetch_groups  how many such groups each row keeps requested ahead of the
  *                  window being loaded; 0 or -1 = no prefetch (default).

@@ -40,14 +40,16 @@ int fail(int status, const char *fmt, ...) {
 
 // ---- kernel instances (rfi_inst_f32.cu, rfi_inst_f16.cu) ----------------------
 const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb, int mixed,
-                              int vs, int pw, int ad) {
+                              int vs, int pw, int ad, int pf) {
     const InstanceTable tabs[] = {instances_f32(),    instances_f16(),    instances_f32_pw(),
-                                  instances_f16_pw(), instances_f32_ad(), instances_f16_ad()};
+                                  instances_f16_pw(), instances_f32_ad(), instances_f16_ad(),
+                                  instances_f32_pf(), instances_f16_pf()};
     for (const InstanceTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const Instance &in = t.items[i];
             if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan &&
-                in.lb == lb && in.mixed == mixed && in.vs == vs && in.pw == pw && in.ad == ad)
+                in.lb == lb && in.mixed == mixed && in.vs == vs && in.pw == pw && in.ad == ad &&
+                in.pf == pf)
                 return &in;
         }
     return nullptr;
@@ -252,7 +254,12 @@ int choose_shape(rfi_ctx *c, int P_req) {
     c->spu = spu;
     c->S = c->M / (P * spu);
     c->ch = largest_chunk(c->S);
-    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs, c->pw, c->ad);
+    // the plain 128-register kernels exist with and without the prefetch code; the
+    // other kinds always hold it
+    const bool plain = c->lb == 0 && !c->mixed && !c->vs && !c->pw && !c->ad;
+    const int pf = plain ? (c->pf_groups > 0 ? 1 : 0) : 1;
+    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs, c->pw, c->ad,
+                            pf);
     if (c->ad && (!c->inst || c->loader != 0))
         return fail(RFI_EUNSUPPORTED, "adaptive needs the direct loader, the 128-register "
                                       "budget and float32 arithmetic, without buffered_stores "

@@ -90,10 +90,20 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// Bulk prefetch of [p, p + bytes) into L2 by the TMA engine (no registers, no wait);
-// p 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+// L2 prefetch of the 128-byte line holding p: a per-thread hint (no register, no wait,
+// no memory clobber).  The bulk form (cp.async.bulk.prefetch.L2) takes warp-uniform
+// operands, so with one address per row it was issued once per distinct address, about
+// 100 instructions per prefetch and warp; the P lanes of a row instead split the range
+// into lines.
+__device__ __forceinline__ void prefetch_line(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+template <int P>
+__device__ __forceinline__ void prefetch_rows(const char *p, long long bytes, int j) {
+    const uintptr_t end = reinterpret_cast<uintptr_t>(p) + bytes;
+    for (uintptr_t q = (reinterpret_cast<uintptr_t>(p) & ~uintptr_t(127)) + 128u * j; q < end;
+         q += 128u * P)
+        prefetch_line(reinterpret_cast<const void *>(q));
 }
 
 // ---- TMA bulk copies into shared memory, completed on an mbarrier --------------
@@ -369,8 +379,12 @@ __device__ __forceinline__ float allsum(float v) {
 // by window in k_adapt (rfi_adapt.cu), a light pass over the stored tau and flag bits.
 // The DS threshold gamma stays fixed (its null, E r^2 = 1/W, does not depend on the
 // data).
+// PFT: the L2 prefetch code is compiled in (taken when the launch asks for it); the
+// plain kernels come with and without it, since its mere presence changes how the
+// compiler schedules the window loop.
 template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false,
-          bool TMA = false, bool VS = false, bool PW = false, bool AD = false>
+          bool TMA = false, bool VS = false, bool PW = false, bool AD = false,
+          bool PFT = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
     static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
     static_assert(!TMA || P == 1, "the shared-memory loader runs one lane per row");
@@ -440,14 +454,14 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
                            (reinterpret_cast<uintptr_t>(a.flags) & 15) == 0;
     float4 tq = make_float4(0.f, 0.f, 0.f, 0.f), rq = tq, iq = tq;
     uint4 fq = make_uint4(0u, 0u, 0u, 0u);
-    // L2 prefetch: lane 0 of each row keeps pf_groups groups of pf_windows windows
+    // L2 prefetch: the lanes of each row keep pf_groups groups of pf_windows windows
     // requested ahead of the window being loaded.
-    const bool pf = a.pf_groups > 0 && lead;
+    const bool pf = PFT && a.pf_groups > 0 && active;
     const unsigned wbytes = (unsigned)a.M * SB;
     if (pf) {
         const int hi = min(a.nwin, (1 + a.pf_groups) * a.pf_windows);
         if (hi > 1 && rfi_in(fp + wbytes, (hi - 1) * (long long)wbytes, a.vis, vis_ext, a.err))
-            prefetch_l2(fp + wbytes, (unsigned)(hi - 1) * wbytes);
+            prefetch_rows<P>(fp + wbytes, (hi - 1) * (long long)wbytes, j);
     }
     int pf_next = a.pf_windows;
 
@@ -638,7 +652,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             if (g0 < g1 &&
                 rfi_in(fp + (long long)g0 * wbytes, (g1 - g0) * (long long)wbytes, a.vis, vis_ext,
                        a.err))
-                prefetch_l2(fp + (long long)g0 * wbytes, (unsigned)(g1 - g0) * wbytes);
+                prefetch_rows<P>(fp + (long long)g0 * wbytes, (g1 - g0) * (long long)wbytes, j);
             pf_next += a.pf_windows;
         }
     };
@@ -782,14 +796,14 @@ template <> struct Bounds<1> { static constexpr int threads = 256, blocks = 3; }
 template <> struct Bounds<2> { static constexpr int threads = 256, blocks = 4; };
 
 template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, bool MIXED = false,
-          bool VS = false, bool PW = false, bool AD = false>
+          bool VS = false, bool PW = false, bool AD = false, bool PFT = false>
 __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_block(const __grid_constant__ StreamArgs a) {
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     // the 128-register budget keeps two chunks in flight; tighter budgets load one
     // chunk at a time and rely on more resident warps instead
-    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS, PW, AD>(a, group);
+    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS, PW, AD, PFT>(a, group);
 }
 
 // One lane per row, rows staged in shared memory by TMA bulk copies; dynamic shared
@@ -805,7 +819,7 @@ __global__ void __launch_bounds__(512, 1) k_tma(const __grid_constant__ StreamAr
 // until none is left; the last block to finish resets the counter for the next
 // launch in stream order.
 template <int DT, int SPU, int P, int CH, bool KAHAN, bool MIXED = false, bool PW = false,
-          bool AD = false>
+          bool AD = false, bool PFT = false>
 __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchArgs b) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -820,7 +834,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchA
             const bool le = k < b.n && b.prefix[k + 1] <= (long long)t;
             i += __popc(__ballot_sync(FULL, le));
         }
-        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW, AD>(
+        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW, AD, PFT>(
             b.s[i], (long long)t - b.prefix[i]);
     }
     __syncthreads();

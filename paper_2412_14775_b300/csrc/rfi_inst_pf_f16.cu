@@ -1,0 +1,19 @@
+// rfi_inst_pf_f16.cu -- the plain 128-register kernels for binary16 input with
+// the L2 prefetch code compiled in.
+#include "rfi_device.cuh"
+#include "rfi_kernels.h"
+
+namespace rfi {
+
+static const Instance k_table[] = {
+    RFI_INSTF_P(DT_F16, 2, 0),
+    RFI_INSTF_P(DT_F16, 2, 1),
+    RFI_INSTF_CH(DT_F16, 1, 1, 0),
+    RFI_INSTF_CH(DT_F16, 1, 1, 1),
+};
+
+InstanceTable instances_f16_pf() {
+    return {k_table, (int)(sizeof(k_table) / sizeof(k_table[0]))};
+}
+
+}  // namespace rfi

@@ -8,7 +8,7 @@
 namespace rfi {
 
 struct Instance {
-    int dt, spu, P, ch, kahan, lb, mixed, vs, pw, ad;
+    int dt, spu, P, ch, kahan, lb, mixed, vs, pw, ad, pf;
     const void *block_fn;   // k_block<...>
     const void *batch_fn;   // k_batch<...>; the register budget does not change results,
                             // so every budget shares the LB = 0 batch kernel
@@ -25,6 +25,8 @@ InstanceTable instances_f32_pw();     // partial windows (rfi_inst_pw_f32.cu)
 InstanceTable instances_f16_pw();     // partial windows (rfi_inst_pw_f16.cu)
 InstanceTable instances_f32_ad();     // online SK thresholds (rfi_inst_ad_f32.cu)
 InstanceTable instances_f16_ad();     // online SK thresholds (rfi_inst_ad_f16.cu)
+InstanceTable instances_f32_pf();     // plain kernels with L2 prefetch (rfi_inst_pf_f32.cu)
+InstanceTable instances_f16_pf();     // plain kernels with L2 prefetch (rfi_inst_pf_f16.cu)
 // State update of adaptive contexts after a flagging launch (rfi_adapt.cu): one thread
 // per footprint row; k_adapt takes a StreamArgs, k_adapt_batch a BatchArgs.
 const void *adapt_fn();
@@ -44,35 +46,55 @@ TmaTable tma_instances_f16();
 
 }  // namespace rfi
 
-// Entries for one (DT, SPU, P, CH, K): LB = 0 with its own batch kernel.
+// Field `pf`: 1 = the kernel holds the L2 prefetch code (used when a launch asks for
+// prefetch), 0 = it does not.  The plain 128-register kernels exist both ways; every
+// other kind holds it.
+// Entries for one (DT, SPU, P, CH, K): LB = 0 with its own batch kernel, no prefetch.
 #define RFI_INST0(DT, SPU, P, CH, K)                                                        \
-    {DT, SPU, P, CH, K, 0, 0, 0, 0, 0,                                                      \
+    {DT, SPU, P, CH, K, 0, 0, 0, 0, 0, 0,                                                   \
      (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0>,                               \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K>}
-// A tighter register budget LB for the single-stream kernel.
+// The same with the L2 prefetch code (rfi_inst_pf_*.cu).
+#define RFI_INSTF(DT, SPU, P, CH, K)                                                        \
+    {DT, SPU, P, CH, K, 0, 0, 0, 0, 0, 1,                                                   \
+     (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, false, false,   \
+                                 true>,                                                     \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, false, false, true>}
+#define RFI_INSTF_CH(DT, SPU, P, K)                                                         \
+    RFI_INSTF(DT, SPU, P, 1, K), RFI_INSTF(DT, SPU, P, 2, K), RFI_INSTF(DT, SPU, P, 4, K),  \
+        RFI_INSTF(DT, SPU, P, 5, K)
+#define RFI_INSTF_P(DT, SPU, K)                                                             \
+    RFI_INSTF_CH(DT, SPU, 1, K), RFI_INSTF_CH(DT, SPU, 2, K), RFI_INSTF_CH(DT, SPU, 4, K),  \
+        RFI_INSTF_CH(DT, SPU, 8, K), RFI_INSTF_CH(DT, SPU, 16, K),                         \
+        RFI_INSTF_CH(DT, SPU, 32, K)
+// A tighter register budget LB for the single-stream kernel (the batch kernel is the
+// 128-register one).
 #define RFI_INSTB(DT, SPU, P, CH, LB)                                                       \
-    {DT, SPU, P, CH, 0, LB, 0, 0, 0, 0,                                                     \
-     (const void *)&rfi::k_block<DT, SPU, P, CH, false, LB>,                                \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
+    {DT, SPU, P, CH, 0, LB, 0, 0, 0, 0, 1,                                                  \
+     (const void *)&rfi::k_block<DT, SPU, P, CH, false, LB, false, false, false, false,    \
+                                 true>,                                                     \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, false, false, false, false, true>}
 // The paper-mixed precision mode (one lane per row).
 #define RFI_INSTM(DT, SPU, CH)                                                              \
-    {DT, SPU, 1, CH, 0, 0, 1, 0, 0, 0,                                                      \
-     (const void *)&rfi::k_block<DT, SPU, 1, CH, false, 0, true>,                           \
-     (const void *)&rfi::k_batch<DT, SPU, 1, CH, false, true>}
+    {DT, SPU, 1, CH, 0, 0, 1, 0, 0, 0, 1,                                                   \
+     (const void *)&rfi::k_block<DT, SPU, 1, CH, false, 0, true, false, false, false, true>, \
+     (const void *)&rfi::k_batch<DT, SPU, 1, CH, false, true, false, false, true>}
 // Buffered 16-byte output stores (for small windows); shares the batch kernel.
 #define RFI_INSTV(DT, SPU, P, CH)                                                           \
-    {DT, SPU, P, CH, 0, 0, 0, 1, 0, 0,                                                      \
-     (const void *)&rfi::k_block<DT, SPU, P, CH, false, 0, false, true>,                   \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
+    {DT, SPU, P, CH, 0, 0, 0, 1, 0, 0, 1,                                                   \
+     (const void *)&rfi::k_block<DT, SPU, P, CH, false, 0, false, true, false, false,      \
+                                 true>,                                                     \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, false, false, false, false, true>}
 #define RFI_INSTV_P(DT, SPU)                                                                \
     RFI_INSTV(DT, SPU, 1, 1), RFI_INSTV(DT, SPU, 1, 2), RFI_INSTV(DT, SPU, 1, 4),           \
         RFI_INSTV(DT, SPU, 2, 1), RFI_INSTV(DT, SPU, 2, 2), RFI_INSTV(DT, SPU, 2, 4),       \
         RFI_INSTV(DT, SPU, 4, 1), RFI_INSTV(DT, SPU, 4, 2), RFI_INSTV(DT, SPU, 4, 4)
 // Partial windows (blocks of any length), 128-register budget.
 #define RFI_INSTP(DT, SPU, P, CH, K)                                                        \
-    {DT, SPU, P, CH, K, 0, 0, 0, 1, 0,                                                      \
-     (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, true>,          \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, true>}
+    {DT, SPU, P, CH, K, 0, 0, 0, 1, 0, 1,                                                   \
+     (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, true, false,    \
+                                 true>,                                                     \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, true, false, true>}
 #define RFI_INSTP_CH(DT, SPU, P, K)                                                         \
     RFI_INSTP(DT, SPU, P, 1, K), RFI_INSTP(DT, SPU, P, 2, K), RFI_INSTP(DT, SPU, P, 4, K),  \
         RFI_INSTP(DT, SPU, P, 5, K)
@@ -82,9 +104,10 @@ TmaTable tma_instances_f16();
         RFI_INSTP_CH(DT, SPU, 32, K)
 // Online per-stream SK thresholds, 128-register budget.
 #define RFI_INSTA(DT, SPU, P, CH, K)                                                        \
-    {DT, SPU, P, CH, K, 0, 0, 0, 0, 1,                                                      \
-     (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, false, true>,   \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, false, true>}
+    {DT, SPU, P, CH, K, 0, 0, 0, 0, 1, 1,                                                   \
+     (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, false, true,    \
+                                 true>,                                                     \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, false, true, true>}
 #define RFI_INSTA_CH(DT, SPU, P, K)                                                         \
     RFI_INSTA(DT, SPU, P, 1, K), RFI_INSTA(DT, SPU, P, 2, K), RFI_INSTA(DT, SPU, P, 4, K),  \
         RFI_INSTA(DT, SPU, P, 5, K)
