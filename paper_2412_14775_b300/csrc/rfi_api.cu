@@ -124,6 +124,7 @@ struct rfi_ctx {
     rfi_adaptation adp;
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     const Instance *inst;
+    const void *batch_fn;               // persistent kernel of rfi_process_batch
     long long n_seen;
     int status;
     float *carry;                       // [R][P][9]
@@ -147,7 +148,7 @@ struct rfi_batch_graph {
     cudaGraphExec_t exec;
     cudaGraphNode_t node;
     cudaGraphNode_t adapt_node;         // state update of adaptive contexts, or null
-    const Instance *inst;
+    const void *batch_fn;
     int grid, block;
 };
 
@@ -260,6 +261,14 @@ int choose_shape(rfi_ctx *c, int P_req) {
     const int pf = plain ? (c->pf_groups > 0 ? 1 : 0) : 1;
     c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs, c->pw, c->ad,
                             pf);
+    if (c->inst) {
+        c->batch_fn = c->inst->batch_fn;
+        if (!c->batch_fn) {     // kernels with prefetch batch with the plain batch kernel
+            const Instance *plain0 =
+                find_instance(dt, spu, P, c->ch, c->kahan, 0, 0, 0, 0, 0, 0);
+            c->batch_fn = plain0 ? plain0->batch_fn : nullptr;
+        }
+    }
     if (c->ad && (!c->inst || c->loader != 0))
         return fail(RFI_EUNSUPPORTED, "adaptive needs the direct loader, the 128-register "
                                       "budget and float32 arithmetic, without buffered_stores "
@@ -444,22 +453,22 @@ int adapt_batch_grid(int device) {
 
 // Resident blocks of a batch kernel on the whole GPU (cached per kernel, block size
 // and device).
-int persistent_grid(const Instance *in, int wpb, int device) {
+int persistent_grid(const void *batch_fn, int wpb, int device) {
     struct Entry { const void *fn; int wpb, device, grid; };
     static std::mutex mu;
     static std::vector<Entry> cache;
     std::lock_guard<std::mutex> lk(mu);
     for (const Entry &e : cache)
-        if (e.fn == in->batch_fn && e.wpb == wpb && e.device == device) return e.grid;
+        if (e.fn == batch_fn && e.wpb == wpb && e.device == device) return e.grid;
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, in->batch_fn, 32 * wpb, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_fn, 32 * wpb, 0) !=
             cudaSuccess ||
         per < 1) {
         cudaGetLastError();
         per = 1;
     }
-    cache.push_back({in->batch_fn, wpb, device, std::max(sms, 1) * per});
+    cache.push_back({batch_fn, wpb, device, std::max(sms, 1) * per});
     return cache.back().grid;
 }
 
@@ -473,7 +482,7 @@ int build_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *
         if ((rc = check_ctx(ctxs[i]))) return rc;
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return fail(RFI_EINVAL, "context %d appears twice", i);
-        if (ctxs[i]->inst->batch_fn != ctxs[0]->inst->batch_fn ||
+        if (!ctxs[i]->batch_fn || ctxs[i]->batch_fn != ctxs[0]->batch_fn ||
             ctxs[i]->device != ctxs[0]->device)
             return fail(RFI_EINVAL, "context %d differs in dtype, M or launch shape", i);
     }
@@ -864,9 +873,9 @@ int rfi_process_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const
     int rc = build_batch(ctxs, n, vis, T, flags, avg, weight, stats, true, b);
     if (rc) return rc;
     rfi_ctx *c0 = ctxs[0];
-    const int grid = persistent_grid(c0->inst, c0->wpb, c0->device);
+    const int grid = persistent_grid(c0->batch_fn, c0->wpb, c0->device);
     void *args[] = {b};
-    cudaError_t e = cudaLaunchKernel(c0->inst->batch_fn, dim3(grid), dim3(32 * c0->wpb), args, 0,
+    cudaError_t e = cudaLaunchKernel(c0->batch_fn, dim3(grid), dim3(32 * c0->wpb), args, 0,
                                      static_cast<cudaStream_t>(stream));
     if (e == cudaSuccess && c0->ad)
         e = cudaLaunchKernel(adapt_batch_fn(), dim3(adapt_batch_grid(c0->device)), dim3(256),
@@ -897,12 +906,12 @@ int rfi_batch_graph_create(rfi_batch_graph **out, rfi_ctx *const *ctxs, int n, c
     g->n = n;
     g->ctxs.assign(ctxs, ctxs + n);
     g->T.assign(T, T + n);
-    g->inst = ctxs[0]->inst;
+    g->batch_fn = ctxs[0]->batch_fn;
     g->block = 32 * ctxs[0]->wpb;
-    g->grid = persistent_grid(g->inst, ctxs[0]->wpb, ctxs[0]->device);
+    g->grid = persistent_grid(g->batch_fn, ctxs[0]->wpb, ctxs[0]->device);
     cudaKernelNodeParams kp = {};
     void *args[] = {b};
-    kp.func = const_cast<void *>(g->inst->batch_fn);
+    kp.func = const_cast<void *>(g->batch_fn);
     kp.gridDim = dim3(g->grid);
     kp.blockDim = dim3(g->block);
     kp.kernelParams = args;
@@ -942,7 +951,7 @@ int rfi_batch_graph_launch(rfi_batch_graph *g, const void *const *vis, uint32_t 
     if (rc) return rc;
     cudaKernelNodeParams kp = {};
     void *args[] = {b};
-    kp.func = const_cast<void *>(g->inst->batch_fn);
+    kp.func = const_cast<void *>(g->batch_fn);
     kp.gridDim = dim3(g->grid);
     kp.blockDim = dim3(g->block);
     kp.kernelParams = args;

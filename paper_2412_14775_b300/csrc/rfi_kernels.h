@@ -10,8 +10,9 @@ namespace rfi {
 struct Instance {
     int dt, spu, P, ch, kahan, lb, mixed, vs, pw, ad, pf;
     const void *block_fn;   // k_block<...>
-    const void *batch_fn;   // k_batch<...>; the register budget does not change results,
-                            // so every budget shares the LB = 0 batch kernel
+    const void *batch_fn;   // k_batch<...>; the register budget, the buffered stores and
+                            // the prefetch do not change results, so all those share the
+                            // plain batch kernel (null: take the plain sibling's)
 };
 
 struct InstanceTable {
@@ -54,12 +55,14 @@ TmaTable tma_instances_f16();
     {DT, SPU, P, CH, K, 0, 0, 0, 0, 0, 0,                                                   \
      (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0>,                               \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K>}
-// The same with the L2 prefetch code (rfi_inst_pf_*.cu).
+// The same with the L2 prefetch code (rfi_inst_pf_*.cu).  No batch kernel of its own: a
+// batch of plain contexts runs the RFI_INST0 batch kernel (without prefetch), so that
+// contexts with and without prefetch batch together.
 #define RFI_INSTF(DT, SPU, P, CH, K)                                                        \
     {DT, SPU, P, CH, K, 0, 0, 0, 0, 0, 1,                                                   \
      (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, false, false,   \
                                  true>,                                                     \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, false, false, true>}
+     nullptr}
 #define RFI_INSTF_CH(DT, SPU, P, K)                                                         \
     RFI_INSTF(DT, SPU, P, 1, K), RFI_INSTF(DT, SPU, P, 2, K), RFI_INSTF(DT, SPU, P, 4, K),  \
         RFI_INSTF(DT, SPU, P, 5, K)
@@ -68,12 +71,12 @@ TmaTable tma_instances_f16();
         RFI_INSTF_CH(DT, SPU, 8, K), RFI_INSTF_CH(DT, SPU, 16, K),                         \
         RFI_INSTF_CH(DT, SPU, 32, K)
 // A tighter register budget LB for the single-stream kernel (the batch kernel is the
-// 128-register one).
+// plain 128-register one).
 #define RFI_INSTB(DT, SPU, P, CH, LB)                                                       \
     {DT, SPU, P, CH, 0, LB, 0, 0, 0, 0, 1,                                                  \
      (const void *)&rfi::k_block<DT, SPU, P, CH, false, LB, false, false, false, false,    \
                                  true>,                                                     \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, false, false, false, false, true>}
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
 // The paper-mixed precision mode (one lane per row).
 #define RFI_INSTM(DT, SPU, CH)                                                              \
     {DT, SPU, 1, CH, 0, 0, 1, 0, 0, 0, 1,                                                   \
@@ -84,7 +87,7 @@ TmaTable tma_instances_f16();
     {DT, SPU, P, CH, 0, 0, 0, 1, 0, 0, 1,                                                   \
      (const void *)&rfi::k_block<DT, SPU, P, CH, false, 0, false, true, false, false,      \
                                  true>,                                                     \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, false, false, false, false, true>}
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
 #define RFI_INSTV_P(DT, SPU)                                                                \
     RFI_INSTV(DT, SPU, 1, 1), RFI_INSTV(DT, SPU, 1, 2), RFI_INSTV(DT, SPU, 1, 4),           \
         RFI_INSTV(DT, SPU, 2, 1), RFI_INSTV(DT, SPU, 2, 2), RFI_INSTV(DT, SPU, 2, 4),       \
