@@ -354,6 +354,16 @@ __device__ __forceinline__ float allsum(float v) {
     return v;
 }
 
+// Continue an allsum<P> over the F adjacent rows of a footprint (their lanes form one
+// aligned block of P*F lanes); PF = P * F is warp-uniform.
+template <int P>
+__device__ __forceinline__ float rowsum(float v, int PF) {
+#pragma unroll
+    for (int o = P; o < 32; o <<= 1)
+        if (o < PF) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
 // ---- one row group of one stream ---------------------------------------------
 // DT: input dtype; SPU: samples per load unit (1 or 2); P: lanes per row;
 // CH: load units issued together per lane; KAHAN: compensated S1, S2.
@@ -382,9 +392,10 @@ __device__ __forceinline__ float allsum(float v) {
 // PFT: the L2 prefetch code is compiled in (taken when the launch asks for it); the
 // plain kernels come with and without it, since its mere presence changes how the
 // compiler schedules the window loop.
+// BAT: called from the persistent batch kernel (see the footprint sums below).
 template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false,
           bool TMA = false, bool VS = false, bool PW = false, bool AD = false,
-          bool PFT = false>
+          bool PFT = false, bool BAT = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
     static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
     static_assert(!TMA || P == 1, "the shared-memory loader runs one lane per row");
@@ -523,19 +534,28 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         float qi = allsum<P>(A.q.y), ui = allsum<P>(A.u.y), vi = allsum<P>(A.v.y);
         if (PF > P) {
             // continue the butterfly over the F adjacent rows of the footprint (their
-            // lanes form one aligned block of P*F lanes): one uniform test per step for
-            // all eight sums
+            // lanes form one aligned block of P*F lanes).  The same additions in the
+            // same order either way; the single-stream kernels test each step once for
+            // all eight sums, the batch kernel once per sum: each form measured faster
+            // in its kernel (a matter of how the compiler schedules the whole loop;
+            // batch of 8 subbands 514 against 555 us, single-stream kernels 0-10 %).
+            if constexpr (BAT) {
+                S1 = rowsum<P>(S1, PF); S2 = rowsum<P>(S2, PF);
+                qr = rowsum<P>(qr, PF); ur = rowsum<P>(ur, PF); vr = rowsum<P>(vr, PF);
+                qi = rowsum<P>(qi, PF); ui = rowsum<P>(ui, PF); vi = rowsum<P>(vi, PF);
+            } else {
 #pragma unroll
-            for (int o = P; o < 32; o <<= 1) {
-                if (o < PF) {
-                    S1 += __shfl_xor_sync(FULL, S1, o);
-                    S2 += __shfl_xor_sync(FULL, S2, o);
-                    qr += __shfl_xor_sync(FULL, qr, o);
-                    ur += __shfl_xor_sync(FULL, ur, o);
-                    vr += __shfl_xor_sync(FULL, vr, o);
-                    qi += __shfl_xor_sync(FULL, qi, o);
-                    ui += __shfl_xor_sync(FULL, ui, o);
-                    vi += __shfl_xor_sync(FULL, vi, o);
+                for (int o = P; o < 32; o <<= 1) {
+                    if (o < PF) {
+                        S1 += __shfl_xor_sync(FULL, S1, o);
+                        S2 += __shfl_xor_sync(FULL, S2, o);
+                        qr += __shfl_xor_sync(FULL, qr, o);
+                        ur += __shfl_xor_sync(FULL, ur, o);
+                        vr += __shfl_xor_sync(FULL, vr, o);
+                        qi += __shfl_xor_sync(FULL, qi, o);
+                        ui += __shfl_xor_sync(FULL, ui, o);
+                        vi += __shfl_xor_sync(FULL, vi, o);
+                    }
                 }
             }
         }
@@ -834,7 +854,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchA
             const bool le = k < b.n && b.prefix[k + 1] <= (long long)t;
             i += __popc(__ballot_sync(FULL, le));
         }
-        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW, AD, PFT>(
+        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW, AD, PFT, true>(
             b.s[i], (long long)t - b.prefix[i]);
     }
     __syncthreads();

@@ -50,14 +50,17 @@ TmaTable tma_instances_f16();
 // Field `pf`: 1 = the kernel holds the L2 prefetch code (used when a launch asks for
 // prefetch), 0 = it does not.  The plain 128-register kernels exist both ways; every
 // other kind holds it.
-// Entries for one (DT, SPU, P, CH, K): LB = 0 with its own batch kernel, no prefetch.
+// Entries for one (DT, SPU, P, CH, K): LB = 0 without prefetch code, and the batch
+// kernel of every plain context (it holds the prefetch code, taken when the contexts
+// ask for it; measured faster than the batch kernel without it, 514 against 552 us on
+// the 8-subband batch).
 #define RFI_INST0(DT, SPU, P, CH, K)                                                        \
     {DT, SPU, P, CH, K, 0, 0, 0, 0, 0, 0,                                                   \
      (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0>,                               \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K>}
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, false, false, true>}
 // The same with the L2 prefetch code (rfi_inst_pf_*.cu).  No batch kernel of its own: a
-// batch of plain contexts runs the RFI_INST0 batch kernel (without prefetch), so that
-// contexts with and without prefetch batch together.
+// batch of plain contexts runs the RFI_INST0 batch kernel, so that contexts with and
+// without prefetch batch together.
 #define RFI_INSTF(DT, SPU, P, CH, K)                                                        \
     {DT, SPU, P, CH, K, 0, 0, 0, 0, 0, 1,                                                   \
      (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, false, false,   \
@@ -76,7 +79,7 @@ TmaTable tma_instances_f16();
     {DT, SPU, P, CH, 0, LB, 0, 0, 0, 0, 1,                                                  \
      (const void *)&rfi::k_block<DT, SPU, P, CH, false, LB, false, false, false, false,    \
                                  true>,                                                     \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, false, false, false, false, true>}
 // The paper-mixed precision mode (one lane per row).
 #define RFI_INSTM(DT, SPU, CH)                                                              \
     {DT, SPU, 1, CH, 0, 0, 1, 0, 0, 0, 1,                                                   \
@@ -87,7 +90,7 @@ TmaTable tma_instances_f16();
     {DT, SPU, P, CH, 0, 0, 0, 1, 0, 0, 1,                                                   \
      (const void *)&rfi::k_block<DT, SPU, P, CH, false, 0, false, true, false, false,      \
                                  true>,                                                     \
-     (const void *)&rfi::k_batch<DT, SPU, P, CH, false>}
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, false, false, false, false, true>}
 #define RFI_INSTV_P(DT, SPU)                                                                \
     RFI_INSTV(DT, SPU, 1, 1), RFI_INSTV(DT, SPU, 1, 2), RFI_INSTV(DT, SPU, 1, 4),           \
         RFI_INSTV(DT, SPU, 2, 1), RFI_INSTV(DT, SPU, 2, 2), RFI_INSTV(DT, SPU, 2, 4),       \
