@@ -26,6 +26,9 @@ Facts used (paper: arXiv 2412.14775, Sections 2.1, 2.2, Tables 1-2):
   P10 Windows are runs of consecutive samples of a stream (Sec. 2), whatever the
       correlator's block length: with partial windows, blocks of any length give the
       windows, flags and averages of the unsplit stream, each reported once.
+  P11 Online thresholds follow their stated rule (oracle/adaptive.py).
+  P12 Symmetries of the definitions: sample order within a window, feed swap, sign,
+      conjugation and scale leave the statistics unchanged; a factor j swaps the parts.
 """
 import itertools
 import math
@@ -536,3 +539,47 @@ def pin_p11_online_thresholds(seed=12):
 
 
 ALL_PINS.append(pin_p11_online_thresholds)
+
+
+def pin_p12_symmetries(seed=13):
+    """P12: transformations of the data that the method's definitions leave unchanged
+    (Sec. 2: Stokes parameters; Sec. 2.1: SK of |I|; Sec. 2.2: directions of (q, u, v)).
+
+    (a) permuting the samples inside a window: every statistic is a sum over the window;
+    (b) swapping the two polarisation feeds (xx <-> yy, xy <-> yx): I stays, Q and V
+        change sign, so tau and both r stay;
+    (c) negating every correlation, and (e) conjugating every correlation: |I| stays and
+        each part of (Q, U, V) changes signs component-wise, so tau and both r stay;
+    (d) scaling every correlation by c > 0 with eps = 0: tau and r are homogeneous of
+        degree 0 in the data;
+    (f) multiplying every correlation by j: |I| stays, the Re and Im parts of (Q, U, V)
+        trade places (up to sign), so r_Re and r_Im swap."""
+    rng = np.random.default_rng(seed)
+    R, M, nw = 9, 8, 40
+    vis = rng.standard_normal((R, M * nw, 4)) + 1j * rng.standard_normal((R, M * nw, 4))
+    vis[2, 40:80] *= 6.0
+    vis[5, 120:200, :] = (2.0 + 1j) * np.array([1.0, 0.3 - 0.2j, 0.3 + 0.2j, 0.1])
+    vis[7, :, 1:3] *= 0.01
+
+    def stats(v, eps=EPS32):
+        out = OracleStream(R, M, M, 1.3, -1e300, 1e300, 1e300, eps).process(v)
+        return out["tau"], out["r_re"], out["r_im"]
+
+    def close(a, b, tol=1e-12):
+        for x, y in zip(a, b):
+            assert np.allclose(x, y, rtol=tol, atol=tol), float(np.max(np.abs(x - y)))
+
+    base = stats(vis)
+    perm = vis.reshape(R, nw, M, 4)[:, :, rng.permutation(M)].reshape(R, M * nw, 4)
+    close(stats(perm), base)                                            # (a)
+    close(stats(vis[..., [3, 2, 1, 0]]), base)                          # (b)
+    close(stats(-vis), base)                                            # (c)
+    close(stats(np.conj(vis)), base)                                    # (e)
+    b0 = stats(vis, eps=0.0)
+    close(stats(4.0 * vis, eps=0.0), b0)                                # (d)
+    close(stats(0.25 * vis, eps=0.0), b0)
+    t, rr, ri = stats(1j * vis)                                         # (f)
+    close((t, rr, ri), (base[0], base[2], base[1]))
+
+
+ALL_PINS.append(pin_p12_symmetries)
