@@ -572,6 +572,39 @@ def test_partial_windows_batch_host_and_checkpoint():
             torch.zeros(10, 24, 4, 2, device="cuda"))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_symmetries_bit_exact(dtype):
+    """The kernels' Stokes wiring under the symmetries of pin P12, exactly: swapping the
+    polarisation feeds, negating or conjugating every correlation leave every statistic
+    and flag bit unchanged (each is the same operations on operands that differ only in
+    sign or order of a commutative addition); multiplying by j swaps r_Re and r_Im."""
+    M, K, T = 16, 64, 256
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=61, stations=6, channels=8, T=T)["vis"]
+    v = to_device_rows(d, dtype)                             # [R, T, 4, 2]
+
+    def run(x):
+        st = RfiStream(6, 8, M, K, thr, dtype, lanes_per_row=2)
+        o = st.process(x.contiguous())
+        torch.cuda.synchronize()
+        st.close()
+        return o
+    base = run(v)
+    conj = v.clone()
+    conj[..., 1] = -conj[..., 1]
+    jv = torch.stack([-v[..., 1], v[..., 0]], dim=-1)
+    for name, x in (("feed swap", v[:, :, [3, 2, 1, 0], :]), ("negation", -v),
+                    ("conjugation", conj)):
+        o = run(x)
+        assert torch.equal(o["stats"], base["stats"]), name
+        assert torch.equal(o["flags"], base["flags"]), name
+    o = run(jv)
+    assert torch.equal(o["stats"][0], base["stats"][0])
+    assert torch.equal(o["stats"][1], base["stats"][2])
+    assert torch.equal(o["stats"][2], base["stats"][1])
+    assert torch.equal(o["flags"], base["flags"])
+
+
 def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
     """Failure detection without a GPU fault: with the injection option the staged
     loader expects more bytes than it copies, so every stage wait gives up after about
