@@ -238,7 +238,10 @@ int rfi_adaptive_state(rfi_ctx *ctx, float *host, size_t n_floats, int write, vo
  *   stats  [3][R/F][n_win] float32: tau, r_Re, r_Im of every completed window (SoA;
  *          F = 1 unless the context has a T x F footprint).
  * avg and weight may be NULL only when n_out == 0, flags and stats only when n_win ==
- * 0.  Asynchronous on `stream`. */
+ * 0.  Asynchronous on `stream`; allocates nothing and never synchronises, so a call can
+ * be captured in a CUDA graph (the captured launch keeps this call's arguments: replay
+ * it only where they repeat, e.g. K = T with whole windows; rfi_batch_graph_* updates
+ * them per launch). */
 int rfi_process_block(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags, float *avg,
                       float *weight, float *stats, void *stream);
 

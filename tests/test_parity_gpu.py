@@ -605,6 +605,36 @@ def test_symmetries_bit_exact(dtype):
     assert torch.equal(o["flags"], base["flags"])
 
 
+def test_process_block_captures_in_a_cuda_graph():
+    """rfi_process_block allocates nothing and never synchronises, so it can be captured
+    in a CUDA graph; with K = T every block's launch arguments are the same, and each
+    replay equals a direct call on the same block."""
+    M, K, T = 16, 256, 256
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=67, stations=8, channels=8, T=T)["vis"]
+    v = to_device_rows(d, "f32")
+    st = RfiStream(8, 8, M, K, thr, "f32", lanes_per_row=4)
+    ref = RfiStream(8, 8, M, K, thr, "f32", lanes_per_row=4)
+    out = st.alloc_outputs(T)
+    st.process(v, out=out)                     # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            st.process(v, out=out, stream=s)
+    for _ in range(3):
+        for k in out:
+            out[k].zero_()
+        g.replay()
+        e = ref.process(v)
+        torch.cuda.synchronize()
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(out[k], e[k]), k
+    st.close()
+    ref.close()
+
+
 def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
     """Failure detection without a GPU fault: with the injection option the staged
     loader expects more bytes than it copies, so every stage wait gives up after about
