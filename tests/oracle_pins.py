@@ -553,7 +553,8 @@ def pin_p12_symmetries(seed=13):
     (d) scaling every correlation by c > 0 with eps = 0: tau and r are homogeneous of
         degree 0 in the data;
     (f) multiplying every correlation by j: |I| stays, the Re and Im parts of (Q, U, V)
-        trade places (up to sign), so r_Re and r_Im swap."""
+        trade places (up to sign), so r_Re and r_Im swap;
+    (g) on heavy-tailed data 0 <= r < 1 and tau <= Wd + 1 (above 0 up to the eps term)."""
     rng = np.random.default_rng(seed)
     R, M, nw = 9, 8, 40
     vis = rng.standard_normal((R, M * nw, 4)) + 1j * rng.standard_normal((R, M * nw, 4))
@@ -580,6 +581,14 @@ def pin_p12_symmetries(seed=13):
     close(stats(0.25 * vis, eps=0.0), b0)
     t, rr, ri = stats(1j * vis)                                         # (f)
     close((t, rr, ri), (base[0], base[2], base[1]))
+    # (g) bounds on heavy-tailed data: r is the length of a mean of vectors of length
+    # below 1 (triangle inequality), and Cauchy-Schwarz bounds tau as in P2
+    heavy = vis * rng.standard_cauchy((R, M * nw, 1))
+    t, rr, ri = stats(heavy)
+    d, W = 1.3, M
+    lead = (W * d + 1.0) / (W - 1.0)
+    assert np.all((rr >= 0) & (rr < 1)) and np.all((ri >= 0) & (ri < 1))
+    assert np.all(t <= W * d + 1.0) and np.all(t >= -lead * 1e-6)
 
 
 ALL_PINS.append(pin_p12_symmetries)
