@@ -109,14 +109,17 @@ typedef enum {
  *                  binary32, every operation rounded in the tables' order, eps =
  *                  2^-10 inside binary16 groups; one lane per row, time-only windows,
  *                  no Kahan.  Statistics are then binary16 values.
- *   loader         0 = direct 32-byte global loads (default).  1 = each lane owns a
- *                  row, staged in shared memory a few windows at a time by
- *                  cp.async.bulk (TMA) copies that complete on one mbarrier per stage;
- *                  rows are padded so that the lanes' reads are bank-conflict free.
- *                  Every stage wait is bounded (about 2 s); a wait that gives up sets
- *                  the context's error word, read by rfi_check.  Needs lanes_per_row 1,
- *                  float32 arithmetic and the 128-register budget; results equal the
- *                  direct loader with lanes_per_row = 1.
+ *   loader         0 = direct 32-byte global loads (default).  1 = the rows are
+ *                  staged in shared memory a few windows at a time by cp.async.bulk
+ *                  (TMA) copies, one per row and stage issued by the row's first lane,
+ *                  that complete on one mbarrier per stage; the row's lanes then read
+ *                  the same units as the direct loader.  Rows are padded so that the
+ *                  reads spread over all banks.  Every stage wait is bounded (about
+ *                  2 s); a wait that gives up sets the context's error word, read by
+ *                  rfi_check.  Needs float32 arithmetic and lanes_per_row <= 8 (all
+ *                  register budgets; Kahan with 128); results equal the direct loader's
+ *                  with the same lanes_per_row.  Single-stream calls only: batches run
+ *                  the direct loader (bit-identical results).
  *   tma_stage_windows  windows of every row per stage (0 = 1).
  *   tma_stages     stages in flight per warp (0 = 2); shared memory per block must
  *                  stay within 227 KB.

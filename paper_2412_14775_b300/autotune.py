@@ -93,16 +93,21 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
                 stage1.append((run(o), o))
             except B.RfiError:          # no kernel with this register budget
                 continue
-    if F * 1 <= 32:      # rows staged in shared memory by TMA, one lane per row
-        for wpb, G, NS in ((4, 1, 2), (8, 1, 2), (4, 2, 2), (4, 1, 3), (8, 2, 2), (2, 4, 2)):
-            o = dict(lanes_per_row=1, warps_per_block=wpb, max_registers=0, prefetch_groups=0,
-                     prefetch_bytes=1024, loader=1, tma_stage_windows=G, tma_stages=NS)
-            try:
-                stage1.append((run(o), o))
-            except B.RfiError:          # does not fit the shared memory
-                continue
+    # rows staged in shared memory by TMA bulk copies (no register buffers for loads in
+    # flight, so tighter register budgets are candidates too)
+    for P in [p for p in candidates_p(M, dtype) if p <= 8 and p * F <= 32]:
+        for regs in (0, 80, 64):
+            for wpb, G, NS in ((4, 2, 2), (4, 1, 2), (8, 1, 2), (4, 1, 3)):
+                o = dict(lanes_per_row=P, warps_per_block=wpb, max_registers=regs,
+                         prefetch_groups=0, prefetch_bytes=1024, loader=1,
+                         tma_stage_windows=G, tma_stages=NS)
+                try:
+                    stage1.append((run(o), o))
+                except B.RfiError:      # no such kernel, or it does not fit the shared memory
+                    continue
     stage1.sort(key=lambda x: x[0])
-    # the best direct-load shapes again with 16-byte buffered output stores
+    # the best direct-load shapes again with 16-byte buffered output stores (prefetch is
+    # tried in stage 2 for the direct loader only)
     for _, base in [x for x in stage1 if x[1].get("loader", 0) == 0][:3]:
         o = dict(base, buffered_stores=1)
         try:
@@ -111,7 +116,7 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
             continue
     stage1.sort(key=lambda x: x[0])
     best_t, best = stage1[0]
-    for _, base in stage1[:3]:
+    for _, base in [x for x in stage1 if x[1].get("loader", 0) == 0][:3]:
         for pg in (1, 2):
             for pb in (512, 1024):
                 o = dict(base, prefetch_groups=pg, prefetch_bytes=pb)

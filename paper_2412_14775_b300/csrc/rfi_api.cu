@@ -55,12 +55,14 @@ const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb,
     return nullptr;
 }
 
-const void *find_tma(int dt, int spu, int ch, int kahan) {
+const void *find_tma(int dt, int spu, int P, int ch, int kahan, int lb) {
     const TmaTable tabs[] = {tma_instances_f32(), tma_instances_f16()};
     for (const TmaTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const TmaInstance &in = t.items[i];
-            if (in.dt == dt && in.spu == spu && in.ch == ch && in.kahan == kahan) return in.fn;
+            if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan &&
+                in.lb == lb)
+                return in.fn;
         }
     return nullptr;
 }
@@ -224,10 +226,6 @@ int choose_shape(rfi_ctx *c, int P_req) {
     // samples per 32-byte load unit: binary16 packs two samples when M is even
     int spu = (dt == DT_F16 && c->M % 2 == 0) ? 2 : 1;
     int P = P_req;
-    if (c->loader == 1) {
-        if (P != 0 && P != 1) return fail(RFI_EINVAL, "loader = 1 runs one lane per row");
-        P = 1;
-    }
     if (c->mixed) {
         // sums run sample after sample in one lane, as the tables order them
         if (P != 0 && P != 1) return fail(RFI_EINVAL, "precision = 1 needs lanes_per_row = 1");
@@ -281,15 +279,18 @@ int choose_shape(rfi_ctx *c, int P_req) {
                                       "arithmetic, the 128-register budget, no Kahan, "
                                       "lanes_per_row <= 4 and 1, 2 or 4 load units per chunk");
     if (c->loader == 1) {
-        c->tma_fn = find_tma(dt, spu, c->ch, c->kahan);
-        if (!c->tma_fn || c->mixed || c->lb != 0)
-            return fail(RFI_EUNSUPPORTED, "no shared-memory loader for this shape "
-                                          "(float32 arithmetic, 128-register budget only)");
+        c->tma_fn = c->mixed ? nullptr : find_tma(dt, spu, P, c->ch, c->kahan, c->lb);
+        if (!c->tma_fn)
+            return fail(RFI_EUNSUPPORTED, "no shared-memory loader for this shape (float32 "
+                                          "arithmetic, lanes_per_row <= 8, Kahan only with "
+                                          "the 128-register budget)");
         const unsigned SR = (unsigned)(c->tma_G * c->M * (dt == DT_F32 ? 32 : 16));
-        c->tma_pitch = SR + (((SR / 16) % 2 == 0) ? 16u : 32u);   // odd multiple of 16 B
+        // row pitch = 16 mod 128 bytes: consecutive rows start 4 banks apart, so the
+        // lanes' 16-byte shared-memory reads spread over all banks
+        c->tma_pitch = ((SR + 111u) / 128u) * 128u + 16u;
         auto smem_for = [&](int wpb) {
             const size_t bars = (8u * c->tma_NS * wpb + 127u) & ~(size_t)127u;
-            return bars + (size_t)wpb * c->tma_NS * 32 * c->tma_pitch;
+            return bars + (size_t)wpb * c->tma_NS * (32 / P) * c->tma_pitch;
         };
         if (c->wpb_auto)      // the largest block that fits the shared memory
             while (c->wpb > 1 && smem_for(c->wpb) > 227 * 1024) c->wpb >>= 1;

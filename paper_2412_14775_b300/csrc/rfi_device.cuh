@@ -401,7 +401,6 @@ template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED
           bool PFT = false, bool BAT = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
     static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
-    static_assert(!TMA || P == 1, "the shared-memory loader runs one lane per row");
     constexpr int RW = 32 / P;
     constexpr int SB = (DT == DT_F32) ? 32 : 16;   // bytes per sample
     constexpr int UB = SB * SPU;                   // bytes per load unit
@@ -707,15 +706,18 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     }
 
     if constexpr (TMA) {
-        // stages of G windows for the warp's 32 rows: [stage][lane][pitch] bytes
+        // stages of G windows for the warp's RW rows: [stage][row][pitch] bytes; the
+        // row's first lane issues its copies, and its P lanes read their units (the
+        // same units as the direct loader: j, j + P, ... of each window) from there
         extern __shared__ __align__(128) unsigned char smem_raw[];
         const int warp = threadIdx.x >> 5;
         const int NS = a.stages, G = a.stage_windows;
+        const int r = lane / P;                       // the lane's row in the warp
         uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + warp * NS;
         const unsigned bar_bytes = (8u * NS * (blockDim.x >> 5) + 127u) & ~127u;
-        unsigned char *wbuf = smem_raw + bar_bytes + (size_t)warp * NS * 32 * a.pitch;
+        unsigned char *wbuf = smem_raw + bar_bytes + (size_t)warp * NS * RW * a.pitch;
         const int ngroups = (a.nwin + G - 1) / G;
-        const unsigned n_active = __popc(__ballot_sync(FULL, active));
+        const unsigned n_active = __popc(__ballot_sync(FULL, lead));   // rows with data
         if (lane == 0) {
             for (int st = 0; st < NS; ++st) mbar_init(&bars[st], 1);
             mbar_init_fence();
@@ -728,8 +730,8 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             if (lane == 0) mbar_arrive_expect_tx(&bars[st], bytes * n_active + a.tx_extra);
             __syncwarp();
             // (a copy skipped by the debug-bounds check leaves its stage wait to time out)
-            if (active && rfi_in(rp + (size_t)w0 * a.M * SB, bytes, a.vis, vis_ext, a.err))
-                tma_load_1d(wbuf + ((size_t)st * 32 + lane) * a.pitch, rp + (size_t)w0 * a.M * SB,
+            if (lead && rfi_in(rp + (size_t)w0 * a.M * SB, bytes, a.vis, vis_ext, a.err))
+                tma_load_1d(wbuf + ((size_t)st * RW + r) * a.pitch, rp + (size_t)w0 * a.M * SB,
                             bytes, &bars[st]);
         };
         for (int g = 0; g < min(NS, ngroups); ++g) issue(g);
@@ -742,13 +744,14 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
                 if (lane == 0) atomicOr(a.err, 1);
                 break;
             }
-            const unsigned char *sp = wbuf + ((size_t)st * 32 + lane) * a.pitch;
+            const unsigned char *sp = wbuf + ((size_t)st * RW + r) * a.pitch + j * UB;
             const int nw = min(G, a.nwin - g * G);
             for (int wi = 0; wi < nw; ++wi) {
                 for (int q = 0; q < nch; ++q) {
                     Unit<UB> u[CH];
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) load_unit_smem(sp + (q * CH + c) * UB, u[c]);
+                    for (int c = 0; c < CH; ++c)
+                        load_unit_smem(sp + (q * CH + c) * (P * UB), u[c]);
                     consume(u);
                 }
                 end_window();
@@ -829,13 +832,16 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS, PW, AD, PFT>(a, group);
 }
 
-// One lane per row, rows staged in shared memory by TMA bulk copies; dynamic shared
-// memory = round_up(8 * warps * stages, 128) + warps * stages * 32 * pitch bytes.
-template <int DT, int SPU, int CH, bool KAHAN>
-__global__ void __launch_bounds__(512, 1) k_tma(const __grid_constant__ StreamArgs a) {
+// P lanes per row, rows staged in shared memory by TMA bulk copies; dynamic shared
+// memory = round_up(8 * warps * stages, 128) + warps * stages * (32/P) * pitch bytes.
+// Without register buffers for loads in flight, tighter register budgets (LB) leave
+// room for more resident warps.
+template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0>
+__global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
+    k_tma(const __grid_constant__ StreamArgs a) {
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (group * 32 >= a.R) return;     // whole warp leaves together
-    process_group<DT, SPU, 1, CH, KAHAN, false, false, true>(a, group);
+    if (group * (32 / P) >= a.R) return;     // whole warp leaves together
+    process_group<DT, SPU, P, CH, KAHAN, false, false, true>(a, group);
 }
 
 // Persistent batch: every warp takes (stream, row group) tasks from a device counter

@@ -21,15 +21,4 @@ static const Instance k_table[] = {
 
 InstanceTable instances_f16() { return {k_table, (int)(sizeof(k_table) / sizeof(k_table[0]))}; }
 
-static const TmaInstance k_tma_table[] = {
-    RFI_TMA_CH(DT_F16, 2, 0),
-    RFI_TMA_CH(DT_F16, 2, 1),
-    RFI_TMA_CH(DT_F16, 1, 0),
-    RFI_TMA_CH(DT_F16, 1, 1),
-};
-
-TmaTable tma_instances_f16() {
-    return {k_tma_table, (int)(sizeof(k_tma_table) / sizeof(k_tma_table[0]))};
-}
-
 }  // namespace rfi

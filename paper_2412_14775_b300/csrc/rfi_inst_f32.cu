@@ -15,13 +15,4 @@ static const Instance k_table[] = {
 
 InstanceTable instances_f32() { return {k_table, (int)(sizeof(k_table) / sizeof(k_table[0]))}; }
 
-static const TmaInstance k_tma_table[] = {
-    RFI_TMA_CH(DT_F32, 1, 0),
-    RFI_TMA_CH(DT_F32, 1, 1),
-};
-
-TmaTable tma_instances_f32() {
-    return {k_tma_table, (int)(sizeof(k_tma_table) / sizeof(k_tma_table[0]))};
-}
-
 }  // namespace rfi

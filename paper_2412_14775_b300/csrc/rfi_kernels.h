@@ -33,9 +33,9 @@ InstanceTable instances_f16_pf();     // plain kernels with L2 prefetch (rfi_ins
 const void *adapt_fn();
 const void *adapt_batch_fn();
 
-// The shared-memory (TMA) loader: one lane per row, direct-load twin for batches.
+// The shared-memory (TMA) loader for one stream (batches use the direct loader).
 struct TmaInstance {
-    int dt, spu, ch, kahan;
+    int dt, spu, P, ch, kahan, lb;
     const void *fn;         // k_tma<...>
 };
 struct TmaTable {
@@ -135,6 +135,12 @@ TmaTable tma_instances_f16();
 #define RFI_INSTB_P(DT, SPU, LB)                                                            \
     RFI_INSTB_CH(DT, SPU, 1, LB), RFI_INSTB_CH(DT, SPU, 2, LB), RFI_INSTB_CH(DT, SPU, 4, LB), \
         RFI_INSTB_CH(DT, SPU, 8, LB)
-#define RFI_TMA(DT, SPU, CH, K) {DT, SPU, CH, K, (const void *)&rfi::k_tma<DT, SPU, CH, (bool)K>}
-#define RFI_TMA_CH(DT, SPU, K)                                                              \
-    RFI_TMA(DT, SPU, 1, K), RFI_TMA(DT, SPU, 2, K), RFI_TMA(DT, SPU, 4, K), RFI_TMA(DT, SPU, 5, K)
+#define RFI_TMA(DT, SPU, P, CH, K, LB)                                                      \
+    {DT, SPU, P, CH, K, LB, (const void *)&rfi::k_tma<DT, SPU, P, CH, (bool)K, LB>}
+#define RFI_TMA_CH(DT, SPU, P, K, LB)                                                       \
+    RFI_TMA(DT, SPU, P, 1, K, LB), RFI_TMA(DT, SPU, P, 2, K, LB),                           \
+        RFI_TMA(DT, SPU, P, 4, K, LB), RFI_TMA(DT, SPU, P, 5, K, LB)
+// lanes per row 1-8; Kahan with the 128-register budget, budgets 80 and 64 without
+#define RFI_TMA_PB(DT, SPU, P)                                                              \
+    RFI_TMA_CH(DT, SPU, P, 0, 0), RFI_TMA_CH(DT, SPU, P, 1, 0), RFI_TMA_CH(DT, SPU, P, 0, 1), \
+        RFI_TMA_CH(DT, SPU, P, 0, 2)

@@ -119,6 +119,12 @@ SHAPES = [
     ("f32", 6, 3, 20, 40, [40, 60, 100], {"loader": 1, "tma_stages": 1, "warps_per_block": 2}),
     ("f16", 5, 4, 10, 20, [20, 40], {"loader": 1, "window_F": 2}),
     ("f32", 5, 4, 64, 128, [128, 64, 192], {"loader": 1}),
+    ("f32", 5, 6, 16, 64, [256, 128], {"loader": 1, "lanes_per_row": 4}),
+    ("f16", 6, 4, 16, 32, [96, 64], {"loader": 1, "lanes_per_row": 2, "max_registers": 64}),
+    ("f32", 4, 5, 20, 40, [40, 80], {"loader": 1, "lanes_per_row": 2, "max_registers": 80,
+                                     "tma_stage_windows": 2}),
+    ("f16", 5, 4, 32, 64, [128, 64], {"loader": 1, "lanes_per_row": 8, "tma_stages": 3}),
+    ("f32", 5, 4, 10, 20, [20, 40], {"loader": 1, "lanes_per_row": 2, "window_F": 2}),
     # statistics and flag words written 16 bytes at a time (falls back to plain
     # stores where T/M or the flag words per row are not multiples of 4)
     ("f16", 5, 4, 8, 32, [128, 64, 32], {"buffered_stores": 1, "lanes_per_row": 2}),
@@ -445,18 +451,19 @@ def test_invalid_arguments():
 
 
 def test_tma_loader_bit_identical_to_direct_loads():
-    """The shared-memory loader and the direct loader with one lane per row perform
-    the same arithmetic in the same order."""
+    """The shared-memory loader and the direct loader with the same lanes per row
+    perform the same arithmetic in the same order."""
     M, K, T = 16, 64, 256
     thr = default_thresholds(M)
     d = synth.tiny_block(seed=31, stations=9, channels=11, T=T)["vis"]
-    for dtype in ("f32", "f16"):
+    for dtype, P in (("f32", 1), ("f16", 1), ("f32", 4), ("f16", 2), ("f32", 8)):
         v = to_device_rows(d, dtype)
-        a = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=1).process(v)
-        b = RfiStream(9, 11, M, K, thr, dtype, loader=1, tma_stage_windows=2).process(v)
+        a = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P).process(v)
+        b = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P, loader=1, tma_stage_windows=2,
+                      max_registers=64 if P > 1 else 0).process(v)
         torch.cuda.synchronize()
         for k in ("flags", "avg", "weight", "stats"):
-            assert torch.equal(a[k], b[k]), (dtype, k)
+            assert torch.equal(a[k], b[k]), (dtype, P, k)
 
 
 def test_buffered_stores_bit_identical_to_plain_stores():
@@ -654,7 +661,8 @@ def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
     good = RfiStream(6, 4, M, K, thr, "f32", loader=1)
     out = good.process(v)
     binding.rfi_check(good.ctx)
-    want = RfiStream(6, 4, M, K, thr, "f32", lanes_per_row=1).process(v)
+    want = RfiStream(6, 4, M, K, thr, "f32",
+                     lanes_per_row=good.options["lanes_per_row"]).process(v)
     torch.cuda.synchronize()
     for k in ("flags", "avg", "weight", "stats"):
         assert torch.equal(out[k], want[k]), k
