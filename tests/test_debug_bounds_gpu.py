@@ -1,8 +1,8 @@
 """The debug-bounds build (every global access of the kernels checked against the
 extent its launch declares; a violation is skipped and reported by rfi_check) runs the
-GPU parity, batching, partial-window and online-threshold tests.  They must pass
-unchanged: the checks alter no result, and no kernel touches memory outside its
-buffers on any of those shapes.
+GPU parity, batching, partial-window, online-threshold and random-combination tests.
+They must pass unchanged: the checks alter no result, and no kernel touches memory
+outside its buffers on any of those shapes.
 
 compute-sanitizer is not available on the GPU pool; this build stands in for its
 memory checker.  Each parity stream ends with rfi_check, which fails on any caught
@@ -24,9 +24,9 @@ def test_parity_suite_under_debug_bounds_build():
     lib = lib_build.build(debug_bounds=True)          # compiles only if missing or stale
     env = dict(os.environ, RFI_LIBRARY=lib)
     cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider",
-           "tests/test_parity_gpu.py", "tests/test_adaptive_gpu.py",
+           "tests/test_parity_gpu.py", "tests/test_adaptive_gpu.py", "tests/test_fuzz_gpu.py",
            "-k", "shapes or partial or batch or host or tma or buffered or footprints or "
-                 "checkpoint or degenerate or online or warm_up or edge"]
+                 "checkpoint or degenerate or online or warm_up or edge or random"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1500)
     tail = (r.stdout + r.stderr)[-3000:]
     assert r.returncode == 0, tail
