@@ -56,9 +56,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(dtype):
-    """DRAM bytes per launch from profiles/k_block_lofar_block_<dtype>.md, or None
-    when the kernel sources changed after that capture."""
+def _profile(dtype):
+    """Header fields of profiles/k_block_lofar_block_<dtype>.md, or {} when the kernel
+    sources changed after that capture."""
     path = os.path.join(ROOT, "profiles", f"k_block_lofar_block_{dtype}.md")
     try:
         kv = {}
@@ -66,11 +66,21 @@ def profiled_traffic(dtype):
             if ":" in line and not line.startswith(("|", " ", "#")):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("source_sha256_16") != kernel_source_hash():
-            return None
-        return int(kv["traffic_bytes_per_launch"])
-    except Exception:
-        return None
+        return kv if kv.get("source_sha256_16") == kernel_source_hash() else {}
+    except OSError:
+        return {}
+
+
+def profiled_traffic(dtype):
+    """DRAM bytes per launch from the ncu capture of the current kernel, or None."""
+    v = _profile(dtype).get("traffic_bytes_per_launch")
+    return int(v) if v else None
+
+
+def profiled_dram_gbs(dtype):
+    """ncu's DRAM throughput (GB/s) of that capture (cold caches, serialised), or None."""
+    v = _profile(dtype).get("ncu_dram_gbs")
+    return float(v) if v else None
 
 
 def algo_bytes(R, T, M, K, n_out, sample_bytes):
@@ -701,6 +711,7 @@ def main():
             "hbm_gbs": achieved * ws,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(main_dt),
+                         "ncu_dram_gbs": profiled_dram_gbs(main_dt),
                          "peak_kind": peak_kind, "kernel_us": kern * 1e6,
                          "algorithmic_bytes_per_launch": bytes_launch},
             "frac_of_8tbs": achieved / 8000.0,
