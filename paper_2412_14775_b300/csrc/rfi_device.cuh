@@ -487,6 +487,22 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     const int Q = a.nwin * nch;                   // chunks per lane in this block
     const char *cp_ = fp + j * UB;
     auto load_chunk = [&](int q, Unit<UB>(&u)[CH]) {
+        if (PW && head && q < nch) {
+            // window 0 began in an earlier block: its units before the block come from
+            // the raw-sample carry (a warp-uniform branch, taken for window 0 only)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int off = q * CHB + c * (P * UB) + j * UB;
+                if (off < a.phase * SB) {
+                    if (rfi_in(hwp + off, UB, a.hw, hw_ext, a.err)) load_unit_rw(hwp + off, u[c]);
+                    else u[c] = Unit<UB>{};
+                } else {
+                    if (rfi_in(fp + off, UB, a.vis, vis_ext, a.err)) load_unit(fp + off, u[c]);
+                    else u[c] = Unit<UB>{};
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             const char *p = cp_ + (long long)q * CHB + c * (P * UB);
@@ -681,28 +697,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
 
     int q0 = 0;                                   // first chunk of the pipelined loop
     if constexpr (!TMA && PW) {
-        if (head) {
-            // window 0 began in an earlier block: its units before the block come from
-            // the raw-sample carry; loaded chunk by chunk, outside the pipelined loop
-            for (int q = 0; q < nch; ++q) {
-                Unit<UB> u[CH];
-#pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const int off = q * CHB + c * (P * UB) + j * UB;
-                    if (off < a.phase * SB) {
-                        if (rfi_in(hwp + off, UB, a.hw, hw_ext, a.err)) load_unit_rw(hwp + off, u[c]);
-                        else u[c] = Unit<UB>{};
-                    } else {
-                        if (rfi_in(fp + off, UB, a.vis, vis_ext, a.err)) load_unit(fp + off, u[c]);
-                        else u[c] = Unit<UB>{};
-                    }
-                }
-                consume(u);
-            }
-            end_window();
-            q0 = nch;
-        }
-        if (q0 < Q) load_chunk(q0, ua);
+        if (Q > 0) load_chunk(0, ua);
     }
 
     if constexpr (TMA) {
