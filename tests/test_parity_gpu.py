@@ -132,6 +132,11 @@ SHAPES = [
     ("f16", 4, 6, 16, 64, [512, 192], {"buffered_stores": 1}),
     ("f32", 5, 4, 4, 8, [128, 8, 256], {"buffered_stores": 1, "lanes_per_row": 1}),
     ("f32", 5, 4, 8, 16, [64, 32], {"buffered_stores": 1, "window_F": 2}),
+    # long windows and long blocks
+    ("f32", 3, 4, 1024, 2048, [2048, 1024], {"lanes_per_row": 8}),
+    ("f16", 3, 4, 256, 512, [1024, 512], {"lanes_per_row": 4}),
+    ("f32", 3, 2, 250, 500, [1000, 500], {"lanes_per_row": 2}),
+    ("f16", 3, 2, 16, 8192, [8192, 4096], {}),
     # blocks of any length: windows left open by a block are completed by the next
     ("f32", 5, 4, 16, 64, [250, 7, 1, 100, 300], {"partial_windows": 1, "lanes_per_row": 4}),
     ("f16", 4, 5, 8, 32, [50, 6, 2, 100], {"partial_windows": 1, "lanes_per_row": 2}),
