@@ -69,3 +69,45 @@ def test_default_thresholds():
     # d = 1 reduces to the classic SK variance 4 M^2 / ((M-1)(M+2)(M+3))
     for M in (8, 16, 64):
         assert abs(sk_sigma(M, 1.0) ** 2 - 4 * M * M / ((M - 1) * (M + 2) * (M + 3))) < 1e-14
+
+
+def test_header_is_c_and_matches_the_binding(tmp_path):
+    """include/rfi.h compiles as strict C99 against librfi.so, calls fail cleanly from C
+    without a GPU, and the structures have the sizes and field offsets the ctypes
+    binding assumes."""
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib = build.build()
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "abi.c"
+    src.write_text(r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "rfi.h"
+int main(void) {
+    rfi_ctx *ctx = (rfi_ctx *)1;
+    rfi_thresholds thr = {1.0, 0.0, 2.0, 0.5, 1e-7};
+    int rc = rfi_create(NULL, 4, 4, 16, 64, &thr, RFI_C64);
+    printf("%d %d %s\n", rc, ctx != NULL, rfi_status_str(RFI_EINVAL));
+    printf("%zu %zu %zu\n", sizeof(rfi_options), sizeof(rfi_thresholds), sizeof(rfi_adaptation));
+    printf("%zu %zu %zu\n", offsetof(rfi_options, partial_windows),
+           offsetof(rfi_options, adaptive), offsetof(rfi_adaptation, n_warm));
+    return 0;
+}
+""")
+    exe = tmp_path / "abi"
+    subprocess.check_call([gcc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", inc,
+                           str(src), "-o", str(exe), lib, f"-Wl,-rpath,{os.path.dirname(lib)}"])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    rc, _, name = out[0].split(" ", 2)
+    assert int(rc) == 1 and name.startswith("RFI_EINVAL")
+    sizes = [int(x) for x in out[1].split()]
+    assert sizes == [ctypes.sizeof(binding.rfi_options), ctypes.sizeof(binding.rfi_thresholds),
+                     ctypes.sizeof(binding.rfi_adaptation)]
+    offs = [int(x) for x in out[2].split()]
+    assert offs == [binding.rfi_options.partial_windows.offset, binding.rfi_options.adaptive.offset,
+                    binding.rfi_adaptation.n_warm.offset]
