@@ -258,8 +258,9 @@ int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags
 /* Process one block for each of n contexts (1 <= n <= 64) in ONE persistent launch.
  * All contexts must share dtype, M, lanes_per_row, Kahan summation and the kernel
  * variant (precision, partial_windows, adaptive) (else RFI_EINVAL); register budget,
- * buffered stores, prefetch and loader may differ (a batch always runs the direct
- * loader, without prefetch).  T[i], sizes and layouts per context are as for
+ * buffered stores, prefetch and loader may differ (a batch runs the direct loader with
+ * the 128-register budget and plain stores, prefetching as each context asks).  T[i],
+ * sizes and layouts per context are as for
  * rfi_process_block.  Warps take (context, row group) tasks from a device counter
  * owned by ctxs[0]; two batches that share ctxs[0] must not run concurrently.  Results
  * are bit-identical to rfi_process_block on each context alone (Sec. 2: every
