@@ -720,6 +720,7 @@ def main():
             "frac_of_8tbs": achieved / 8000.0,
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": args.steps,
+            "correlations_per_s": 4 * value,
             "real_time_factor": BLOCK_SECONDS / kern,
             "real_time_factor_native_channel_rate": NATIVE_BLOCK_SECONDS / kern,
             "flag_fractions": flag_fractions,
