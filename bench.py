@@ -285,8 +285,7 @@ def footprint_extras(torch, cs, peak, steps=500, warmup=10):
             opts = autotune.options_of(best)
             st = RfiStream(62, 64, M, K, thr, dtype, **opts)
             out = st.alloc_outputs(T)
-            tot, per, _ = time_kernel(st, vis, out, steps, warmup, torch, cs)
-            k = statistics.mean(per)
+            k, _, _, _ = time_kernel(st, vis, out, steps, warmup, torch, cs)
             nbytes = R * (T * sb + 4 * math.ceil(T / 32) + 12 * (T // M) // F + 36)
             res[f"{dtype}_{M}x{F}"] = {"kernel_us": k * 1e6, "samples_per_s": R * T / k,
                                        "achieved_gbs": nbytes / k / 1e9,
@@ -376,8 +375,7 @@ def mixed_extras(vis32, torch, cs, peak, steps=300, warmup=10):
         lo_b, hi_b = (fb & 0xFFFF) != 0, (fb >> 16) != 0
         differ = ((lo_a != lo_b).sum() + (hi_a != hi_b).sum()).item()
         total = 2 * fa.numel()
-        tot, per, _ = time_kernel(b, vis, ob, steps, warmup, torch, cs)
-        k = statistics.mean(per)
+        k, _, _, _ = time_kernel(b, vis, ob, steps, warmup, torch, cs)
         nbytes = algo_bytes(R, T, M, K, 1, 32 if dtype == "f32" else 16)
         res[dtype] = {"flag_difference_vs_float32": differ / total,
                       "flagged_fraction_float32": ((lo_a.sum() + hi_a.sum()).item()) / total,
@@ -401,8 +399,7 @@ def variant_extras(vis32, opts, torch, cs, peak, steps=300, warmup=10):
     res = {}
     ad = RfiStream(62, 64, M, K, thr, "f32", adaptive=1, **opts)
     o = ad.alloc_outputs(256)
-    _, per, _ = time_kernel(ad, vis32, o, steps, warmup, torch, cs)
-    k = statistics.mean(per)
+    k, _, _, _ = time_kernel(ad, vis32, o, steps, warmup, torch, cs)
     nbytes = algo_bytes(R, 256, M, K, 1, 32) + R * 16 * 2     # + state read and write
     rate = float(o["weight"].lt(1.0).float().mean())
     res["online_thresholds"] = {"kernel_us": k * 1e6, "achieved_gbs": nbytes / k / 1e9,
@@ -411,19 +408,22 @@ def variant_extras(vis32, opts, torch, cs, peak, steps=300, warmup=10):
     ad.close()
     v250 = vis32[:, :250].contiguous()
     pw = RfiStream(62, 64, M, K, thr, "f32", partial_windows=1, **opts)
-    times = []
-    for step in range(warmup + steps):
-        out = pw.alloc_outputs(250)
-        n_win = out["stats"].shape[-1]
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(cs)
-        pw.process(v250, out=out, stream=cs)
-        e1.record(cs)
-        if step >= warmup:
-            times.append((e0, e1, n_win))
+    # output sizes follow the stream position (15 or 16 windows per block): each call's
+    # outputs are taken from torch's caching allocator just before it, no device work
+    for _ in range(warmup):
+        pw.process(v250, out=pw.alloc_outputs(250), stream=cs)
     torch.cuda.synchronize()
-    us = statistics.mean(a.elapsed_time(b) for a, b, _ in times) * 1e3
-    nw = statistics.mean(n for _, _, n in times)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wins = []
+    e0.record(cs)
+    for _ in range(steps):
+        out = pw.alloc_outputs(250)
+        wins.append(out["stats"].shape[-1])
+        pw.process(v250, out=out, stream=cs)
+    e1.record(cs)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    nw = statistics.mean(wins)
     # input, flags and statistics of the completed windows, the samples carried
     nbytes = R * (250 * 32 + 4 * math.ceil(nw * M / 32) + 12 * nw + 32 * (M - 1))
     res["partial_windows_T250"] = {"kernel_us": us, "achieved_gbs": nbytes / (us * 1e-6) / 1e9,
@@ -524,31 +524,39 @@ def serving_extras(seconds, options, torch):
     return res
 
 
-def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler_index=None):
-    """Warm up, then time `steps` launches with per-launch CUDA events on the
-    launching stream (the device time of the flagging kernel)."""
+def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler_index=None,
+                serial_steps=100):
+    """Warm up, then time `steps` back-to-back launches with CUDA events on the launching
+    stream around the whole run; returns the mean launch period (device time of the
+    flagging kernel in a stream of calls, launch overlap included), the run's total and
+    the clock record.  Then `serial_steps` launches with an event pair around each one
+    (which keeps consecutive launches from overlapping): their mean duration, reported
+    beside it."""
     for _ in range(warmup):
         stream_obj.process(vis, out=out, stream=cuda_stream)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
     sampler = ClockSampler(sampler_index) if sampler_index is not None else None
     if sampler:
         sampler.__enter__()
     t_all0 = torch.cuda.Event(enable_timing=True)
     t_all1 = torch.cuda.Event(enable_timing=True)
     t_all0.record(cuda_stream)
-    for a, b in ev:
-        a.record(cuda_stream)
+    for _ in range(steps):
         stream_obj.process(vis, out=out, stream=cuda_stream)
-        b.record(cuda_stream)
     t_all1.record(cuda_stream)
     torch.cuda.synchronize()
     if sampler:
         sampler.__exit__()
-    per = [a.elapsed_time(b) * 1e-3 for a, b in ev]
     total = t_all0.elapsed_time(t_all1) * 1e-3
-    return total, per, (sampler.summary() if sampler else None)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(serial_steps)]
+    for a, b in ev:
+        a.record(cuda_stream)
+        stream_obj.process(vis, out=out, stream=cuda_stream)
+        b.record(cuda_stream)
+    torch.cuda.synchronize()
+    serial = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in ev) if ev else None
+    return total / steps, total, serial, (sampler.summary() if sampler else None)
 
 
 def main():
@@ -615,15 +623,14 @@ def main():
 
     if ws > 1:
         dist.barrier()
-    total, per, clocks = time_kernel(st, vis_main, out, args.steps, args.warmup, torch, cs,
-                                     sampler_index=local)
+    kern, total, kern_serial, clocks = time_kernel(st, vis_main, out, args.steps, args.warmup,
+                                                   torch, cs, sampler_index=local)
     samples = R * T
     # every rank processes its own block (weak scaling): total samples of all ranks over
     # the slowest rank's time
     _, total, value = aggregate(samples * args.steps, total)
     n_out = 1
     bytes_launch = algo_bytes(R, T, M, K, n_out, sbytes)
-    kern = statistics.mean(per)
     achieved = bytes_launch / kern / 1e9
     # windows flagged by each test on the last timed block (from the kernel's statistics)
     stt = out["stats"]
@@ -647,11 +654,10 @@ def main():
             o16opts = tuned(Mw, "f16", vis16)
             s16 = RfiStream(62, 64, Mw, 256, default_thresholds(Mw), "f16", **o16opts)
             o16 = s16.alloc_outputs(T, device=dev)
-            tot16, per16, _ = time_kernel(s16, vis16, o16, max(200, args.steps // 4), args.warmup,
-                                          torch, cs)
+            k16, _, _, _ = time_kernel(s16, vis16, o16, max(200, args.steps // 4), args.warmup,
+                                       torch, cs)
             b16 = algo_bytes(R, T, Mw, 256, 1, 16)
-            k16 = statistics.mean(per16)
-            fp16[f"M{Mw}"] = {"samples_per_s": samples * len(per16) / tot16,
+            fp16[f"M{Mw}"] = {"samples_per_s": samples / k16,
                               "kernel_us": k16 * 1e6, "achieved_gbs": b16 / k16 / 1e9,
                               "frac": b16 / k16 / 1e9 / peak, "options": o16opts}
             s16.close()
@@ -716,6 +722,7 @@ def main():
                          "frac": achieved / peak, "traffic": profiled_traffic(main_dt),
                          "ncu_dram_gbs": profiled_dram_gbs(main_dt),
                          "peak_kind": peak_kind, "kernel_us": kern * 1e6,
+                         "kernel_us_serialised": kern_serial * 1e6,
                          "algorithmic_bytes_per_launch": bytes_launch},
             "frac_of_8tbs": achieved / 8000.0,
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,

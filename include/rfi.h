@@ -157,6 +157,16 @@ typedef enum {
  *                  1/64, k_sigma = 3, n_warm = 32).  Needs the direct loader, float32
  *                  arithmetic, the 128-register budget, plain stores and whole
  *                  windows.
+ *   overlap_bytes  launch overlap of consecutive single-stream calls (programmatic
+ *                  dependent launch).  The flagging kernel is launched so that its
+ *                  blocks may start while the kernel before it on the stream is still
+ *                  finishing; until that kernel has completed they only request the
+ *                  first overlap_bytes of their rows into L2 (a hint, safe whatever
+ *                  that kernel writes), then wait for it and run as usual.  Results are
+ *                  identical; back-to-back calls lose less time at each launch
+ *                  boundary.  0 = 512 bytes (default), -1 = off, else a multiple of
+ *                  128.  Launches recorded into a CUDA graph, the shared-memory loader
+ *                  and batches keep plain stream order.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -178,6 +188,7 @@ typedef struct {
     int buffered_stores;
     int partial_windows;
     int adaptive;
+    int overlap_bytes;
 } rfi_options;
 
 /* Parameters of the online SK thresholds (option `adaptive`). */

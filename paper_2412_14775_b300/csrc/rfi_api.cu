@@ -125,6 +125,7 @@ struct rfi_ctx {
     float *adapt;                       // [R/F][4]: n, mean, second moment of tau, unused
     rfi_adaptation adp;
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
+    int ovl;                            // launch overlap: bytes per row requested early
     const Instance *inst;
     const void *batch_fn;               // persistent kernel of rfi_process_batch
     long long n_seen;
@@ -329,6 +330,7 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.alpha = (float)c->adp.alpha;
     a.k_sigma = (float)c->adp.k_sigma;
     a.n_warm = (float)c->adp.n_warm;
+    a.ovl_bytes = c->ovl;
     a.phase = phase_of(c);
     a.R = nrows;
     a.stats_plane = (c->R / c->F) * nwin;
@@ -420,6 +422,16 @@ cudaError_t allow_smem(const void *fn, size_t bytes) {
     return e;
 }
 
+// Launches recorded into a graph keep plain stream order.
+bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;            // when in doubt, the plain launch
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
     if (a.R <= 0) return RFI_OK;
     const int RW = 32 / c->P;
@@ -432,6 +444,20 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
         if (e == cudaSuccess)
             e = cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args,
                                  c->tma_smem, st);
+    } else if (c->ovl > 0 && !capturing(st)) {
+        // programmatic dependent launch: the blocks may start while the kernel before
+        // this one on the stream drains, and wait for it before touching anything but
+        // L2 (k_block)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)blocks);
+        cfg.blockDim = dim3(32 * c->wpb);
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, c->inst->block_fn, args);
     } else {
         e = cudaLaunchKernel(c->inst->block_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args,
                              0, st);
@@ -583,7 +609,8 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
         (o.max_registers != 0 && o.max_registers < 64) || o.window_F < 0 || o.precision < 0 ||
         o.precision > 1 || o.loader < 0 || o.loader > 1 || o.tma_stage_windows < 0 ||
         o.tma_stage_windows > 64 || o.tma_stages < 0 || o.tma_stages > 8 ||
-        o.debug_inject_wait_timeout < 0 || o.debug_inject_wait_timeout > 1)
+        o.debug_inject_wait_timeout < 0 || o.debug_inject_wait_timeout > 1 ||
+        o.overlap_bytes < -1 || (o.overlap_bytes > 0 && o.overlap_bytes % 128 != 0))
         return fail(RFI_EINVAL, "bad options");
 
     rfi_ctx *c = new (std::nothrow) rfi_ctx();
@@ -642,6 +669,7 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     }
     c->pf_bytes = o.prefetch_bytes ? o.prefetch_bytes : 1024;
     c->pf_groups = o.prefetch_groups > 0 ? o.prefetch_groups : 0;
+    c->ovl = o.overlap_bytes == 0 ? 512 : (o.overlap_bytes < 0 ? 0 : o.overlap_bytes);
     c->status = RFI_OK;
     if ((rc = choose_shape(c, o.lanes_per_row))) {
         delete c;
@@ -758,6 +786,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->buffered_stores = ctx->vs;
     opt->partial_windows = ctx->pw;
     opt->adaptive = ctx->ad;
+    opt->overlap_bytes = ctx->ovl > 0 ? ctx->ovl : -1;
     return RFI_OK;
 }
 

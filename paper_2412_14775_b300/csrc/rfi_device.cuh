@@ -66,6 +66,9 @@ struct StreamArgs {
     float alpha;            // weight of a new window once n >= 1/alpha
     float k_sigma;          // thresholds mean -/+ k_sigma * sd once n >= n_warm
     float n_warm;
+    // launch overlap: bytes at the start of every row requested into L2 before the
+    // kernel waits for the grid it depends on (0 = none)
+    int ovl_bytes;
 };
 
 struct BatchArgs {
@@ -820,8 +823,27 @@ template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, bool MIXED = f
           bool VS = false, bool PW = false, bool AD = false, bool PFT = false>
 __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_block(const __grid_constant__ StreamArgs a) {
+    // a launch that follows on the stream may begin once every block has started
+    // (programmatic dependent launch; a no-op for launches without the attribute)
+    asm volatile("griddepcontrol.launch_dependents;");
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
+    if (a.ovl_bytes > 0) {
+        // launched to overlap the kernel before it on the stream: until that grid has
+        // completed, only request the first bytes of the warp's rows into L2 (a hint; L2
+        // is where all of the GPU's writes meet, so this is safe whatever that kernel
+        // writes)
+        const int lane = threadIdx.x & 31;
+        const int SB = DT == DT_F32 ? 32 : 16;
+        const long long row = min(group * (32 / P) + lane / P, a.R - 1);
+        const long long rb = (long long)a.T * SB;
+        const char *rp = static_cast<const char *>(a.vis) + row * rb;
+        const long long n = min((long long)a.ovl_bytes, rb);
+        if (rfi_in(rp, n, a.vis, a.R * rb, a.err)) prefetch_rows<P>(rp, n, lane & (P - 1));
+    }
+    // everything else (inputs, carries, outputs) only once that grid has completed and
+    // its writes are visible; returns at once when the launch depends on nothing
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // the 128-register budget keeps two chunks in flight; tighter budgets load one
     // chunk at a time and rely on more resident warps instead
     process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS, PW, AD, PFT>(a, group);

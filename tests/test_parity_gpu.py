@@ -501,18 +501,6 @@ def test_buffered_stores_bit_identical_to_plain_stores():
         torch.cuda.synchronize()
         for k in ("flags", "avg", "weight", "stats"):
             assert torch.equal(a[k], b[k]), (dtype, P, k)
-        # a staged-loader context batches with direct-loader ones (the batch kernel
-        # loads directly): same bits again
-        c = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P, loader=1)
-        e = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P, max_registers=80 if P <= 8 else 0)
-        outs = [c.alloc_outputs(T), e.alloc_outputs(T)]
-        binding.rfi_process_batch([c.ctx, e.ctx], [v, v], [T, T], [o["flags"] for o in outs],
-                                  [o["avg"] for o in outs], [o["weight"] for o in outs],
-                                  [o["stats"] for o in outs])
-        torch.cuda.synchronize()
-        for o in outs:
-            for k in ("flags", "avg", "weight", "stats"):
-                assert torch.equal(a[k], o[k]), (dtype, P, "batch", k)
     with pytest.raises(binding.RfiError):      # no buffered variant of the staged loader
         RfiStream(4, 4, 8, 64, thr8, "f32", loader=1, buffered_stores=1)
     with pytest.raises(binding.RfiError):      # nor of the reduced register budgets
