@@ -44,7 +44,8 @@ def _peaks():
         return 6400.0, "fallback"
 
 
-KERNEL_SOURCES = ("rfi_device.cuh", "rfi_inst_f16.cu", "rfi_inst_f32.cu", "rfi_kernels.h")
+KERNEL_SOURCES = ("rfi_device.cuh", "rfi_inst_f16.cu", "rfi_inst_f32.cu", "rfi_inst_pf_f16.cu",
+                  "rfi_inst_pf_f32.cu", "rfi_kernels.h")
 
 
 def kernel_source_hash():
@@ -549,7 +550,7 @@ def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler
         sampler.__exit__()
     total = t_all0.elapsed_time(t_all1) * 1e-3
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(serial_steps)]
+          for _ in range(min(serial_steps, steps))]
     for a, b in ev:
         a.record(cuda_stream)
         stream_obj.process(vis, out=out, stream=cuda_stream)
