@@ -244,3 +244,38 @@ int oracle_process_block(const double *vis, int R, int T, int W, int K,
     return oracle_process_block_tf(vis, R, T, W, 1, K, thr, compensated, n_seen, carry_sum,
                                    carry_cnt, tau, r_re, r_im, wflag, flagbits, avg, weight);
 }
+
+/* ---- Overlapping windows (an extension: the paper's windows do not overlap) -------
+ * Windows of W samples that start every H samples (H divides W), aligned to the
+ * buffer's first sample: window k covers buffer samples [kH, kH + W).  For every row
+ * of vis [R][Tb][8] and every window that fits in the buffer, the statistics of
+ * Secs. 2.1 and 2.2 and the window's flag, exactly as for a window that does not
+ * overlap another (the same W samples, the same order).
+ * Outputs tau, r_re, r_im, wflag [R][nk] with nk = Tb >= W ? (Tb - W) / H + 1 : 0, which
+ * must equal nk_capacity.  Returns nk, or -1 on invalid sizes (nothing written). */
+int oracle_window_stats_hop(const double *vis, int R, int Tb, int W, int H,
+                            const double thr[5], int compensated, int nk_capacity,
+                            double *tau, double *r_re, double *r_im, uint8_t *wflag)
+{
+    if (R < 0 || Tb < 0 || W < 2 || H < 1 || W % H != 0) return -1;
+    const double d = thr[0], s_low = thr[1], s_high = thr[2], gamma = thr[3], eps = thr[4];
+    const int nk = Tb >= W ? (Tb - W) / H + 1 : 0;
+    if (nk != nk_capacity) return -1;           /* the caller sized the outputs for nk */
+    double *stokes = (double *)malloc(sizeof(double) * 8 * (size_t)(Tb > 0 ? Tb : 1));
+    if (!stokes) return -1;
+    for (int row = 0; row < R; ++row) {
+        const double *v = vis + (size_t)row * Tb * 8;
+        for (int i = 0; i < Tb; ++i) oracle_stokes(v + 8 * i, stokes + 8 * (size_t)i);
+        for (int k = 0; k < nk; ++k) {
+            const double *sw = stokes + 8 * (size_t)k * H;      /* the window's W samples */
+            const double t  = oracle_sk_window(sw, W, d, eps, compensated, 0, 0);
+            const double rr = oracle_ds_window(sw, W, 0, eps, compensated, 0);
+            const double ri = oracle_ds_window(sw, W, 1, eps, compensated, 0);
+            const size_t o = (size_t)row * nk + k;
+            tau[o] = t; r_re[o] = rr; r_im[o] = ri;
+            wflag[o] = (uint8_t)oracle_flag(t, rr, ri, s_low, s_high, gamma);
+        }
+    }
+    free(stokes);
+    return nk;
+}

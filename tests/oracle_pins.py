@@ -29,6 +29,9 @@ Facts used (paper: arXiv 2412.14775, Sections 2.1, 2.2, Tables 1-2):
   P11 Online thresholds follow their stated rule (oracle/adaptive.py).
   P12 Symmetries of the definitions: sample order within a window, feed swap, sign,
       conjugation and scale leave the statistics unchanged; a factor j swaps the parts.
+  P13 Overlapping windows (an extension): each window is a window of the plain method
+      on a shifted stream; a spike flags exactly the samples of the windows holding it;
+      averages by brute force; any split at multiples of the hop changes nothing.
 """
 import itertools
 import math
@@ -592,3 +595,90 @@ def pin_p12_symmetries(seed=13):
 
 
 ALL_PINS.append(pin_p12_symmetries)
+
+
+def pin_p13_sliding_windows(seed=14):
+    """P13: overlapping windows (the build's extension, oracle/sliding.py).
+
+    (a) window w of hop H is window i of the non-overlapping method run on the stream
+        from sample (w mod L) H on, i = w div L (L = M / H): statistics and window
+        flags equal those of the (independently pinned) plain oracle exactly;
+    (b) one strong spike at sample t0 in noise, with thresholds that only the spike's
+        windows cross (tau = Wd+1 for them, P2): the flagged samples are exactly
+        [w1 H, w2 H + M), w1 = max(0, ceil((t0 - M + 1) / H)), w2 = floor(t0 / H);
+    (c) averages over those flags, by brute force (mean of the unflagged samples of each
+        bin of K samples, weight n / K);
+    (d) splitting the stream into blocks at multiples of H changes nothing, and each
+        call reports its windows, flags from the first sample that became final and
+        the bins that closed;
+    (e) H = M is the plain method."""
+    rng = np.random.default_rng(seed)
+    for R, M, H, K, N in ((5, 8, 4, 16, 96), (4, 12, 3, 24, 96), (3, 8, 2, 8, 64)):
+        L = M // H
+        vis = rng.standard_normal((R, N, 4)) + 1j * rng.standard_normal((R, N, 4))
+        vis[1, 20:30] *= 8.0
+        vis[2, 40:52, :] = 3.0 * (1 + 1j)
+        thr = (1.0, 0.3, 2.2, 0.7, EPS32)
+        sl = oracle.SlidingOracleStream(R, M, H, K, *thr).process(vis)
+        E = (N - M) // H + 1
+        assert sl["tau"].shape == (R, E) and sl["first_sample"] == 0
+        # (a)
+        for j in range(L):
+            n = ((N - j * H) // M) * M
+            pl = OracleStream(R, M, M, *thr).process(vis[:, j * H:j * H + n])
+            for key in ("tau", "r_re", "r_im", "wflag"):
+                assert np.array_equal(sl[key][:, j::L], pl[key]), (M, H, j, key)
+        # (d)
+        for cuts in ((H, 5 * H), tuple(range(2 * H, N, 3 * H)), (M - H, M, M + H)):
+            st = oracle.SlidingOracleStream(R, M, H, K, *thr)
+            edges = (0,) + tuple(c for c in cuts if 0 < c < N) + (N,)
+            parts = []
+            for a, b in zip(edges[:-1], edges[1:]):
+                nwin, f0 = st.windows_for(b - a)
+                n_out = st.outputs_for(b - a)
+                out = st.process(vis[:, a:b])
+                assert out["tau"].shape[1] == nwin and out["avg"].shape[1] == n_out
+                assert out["first_sample"] == f0
+                parts.append(out)
+            for key in ("tau", "r_re", "r_im", "wflag", "avg", "weight"):
+                got = np.concatenate([p[key] for p in parts], axis=1)
+                assert np.array_equal(got, sl[key]), (M, H, cuts, key)
+            for r in range(R):
+                bits = []
+                for p in parts:
+                    bits += _bits(p["flagbits"][r], p["tau"].shape[1] * H)
+                assert bits == _bits(sl["flagbits"][r], E * H), (M, H, cuts, r)
+        # (b), (c)
+        for t0 in (0, 1, H, M - 1, M + H + 1, N - M - 1):
+            d = 1.0
+            v = (rng.standard_normal((1, N, 4)) + 1j * rng.standard_normal((1, N, 4))) * 0.1
+            v[0, t0] = 1e6
+            # clean windows: tau <= Wd + 1 - 1e-3 almost surely; the spike's: ~ Wd + 1;
+            # gamma = 1 never flags (r <= 1, strict comparison)
+            out = oracle.SlidingOracleStream(1, M, H, K, d, -1e300, M * d + 1 - 1e-3, 1.0,
+                                             EPS32).process(v)
+            w1, w2 = max(0, -((M - 1 - t0) // H)), t0 // H
+            want = np.zeros(E * H, dtype=bool)
+            want[w1 * H:min(w2 * H + M, E * H)] = True
+            got = np.array(_bits(out["flagbits"][0], E * H), dtype=bool)
+            assert np.array_equal(got, want), (M, H, t0)
+            n_bins = (E * H) // K
+            for b in range(n_bins):
+                keep = ~want[b * K:(b + 1) * K]
+                x = v[0, b * K:(b + 1) * K][keep]
+                mean = x.mean(axis=0) if keep.any() else np.zeros(4)
+                ref = np.stack([mean.real, mean.imag], axis=-1).reshape(8)
+                assert np.allclose(out["avg"][0, b], ref, rtol=1e-12, atol=1e-15), (M, H, t0, b)
+                assert out["weight"][0, b] == keep.sum() / K
+    # (e)
+    R, M, K, N = 4, 8, 16, 64
+    vis = rng.standard_normal((R, N, 4)) + 1j * rng.standard_normal((R, N, 4))
+    vis[0, 8:16] *= 10.0
+    thr = (1.0, 0.3, 2.2, 0.7, EPS32)
+    a = oracle.SlidingOracleStream(R, M, M, K, *thr).process(vis)
+    b = OracleStream(R, M, K, *thr).process(vis)
+    for key in ("tau", "r_re", "r_im", "wflag", "flagbits", "avg", "weight"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+ALL_PINS.append(pin_p13_sliding_windows)

@@ -128,3 +128,33 @@ def test_online_threshold_pin_catches_mutant(name, monkeypatch):
     monkeypatch.setattr(oracle, "AdaptiveOracleStream", mod.AdaptiveOracleStream)
     with pytest.raises((AssertionError, ValueError, ZeroDivisionError)):
         oracle_pins.pin_p11_online_thresholds()
+
+
+# Overlapping windows (oracle/sliding.py): mistakes there must fail pin P13.
+SLIDING_MUTANTS = {
+    "sliding_or_misses_oldest_window": ("allw[:, i:i + L].any(axis=1)",
+                                        "allw[:, i + 1:i + L].any(axis=1)"),
+    "sliding_history_not_kept": ("self.history = allw[:, allw.shape[1] - (L - 1):].copy()",
+                                 "self.history = self.history"),
+    "sliding_pending_dropped": ("self.pending = buf[:, nbits:].copy()",
+                                "self.pending = buf[:, :0].copy()"),
+    "sliding_counts_flagged_samples": ("self.carry_cnt[keep] += 1.0", "self.carry_cnt += 1.0"),
+    "sliding_hop_ignored": ("max(0, (n - self.M) // self.H + 1)",
+                            "max(0, (n - self.M) // self.M + 1)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SLIDING_MUTANTS))
+def test_sliding_window_pin_catches_mutant(name, monkeypatch):
+    import types
+    import oracle.sliding
+    old, new = SLIDING_MUTANTS[name]
+    with open(oracle.sliding.__file__) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mod = types.ModuleType("oracle._sliding_mutant")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(text.replace(old, new), "sliding_mutant.py", "exec"), mod.__dict__)
+    monkeypatch.setattr(oracle, "SlidingOracleStream", mod.SlidingOracleStream)
+    with pytest.raises((AssertionError, ValueError, IndexError)):
+        oracle_pins.pin_p13_sliding_windows()
