@@ -391,8 +391,9 @@ def mixed_extras(vis32, torch, cs, peak, steps=300, warmup=10):
 
 def variant_extras(vis32, opts, torch, cs, peak, steps=300, warmup=10):
     """The LOFAR-scale complex64 block through the kernel variants with their own
-    instances: online per-stream SK thresholds (T = 256) and partial windows (blocks
-    of T = 250 samples, so windows straddle blocks), each against the plain kernel."""
+    instances: online per-stream SK thresholds (T = 256), partial windows (blocks of
+    T = 250 samples, so windows straddle blocks) and overlapping windows (a window of
+    16 samples every 8)."""
     from paper_2412_14775_b300 import RfiStream, default_thresholds
     M, K = 16, 256
     thr = default_thresholds(M)
@@ -432,6 +433,27 @@ def variant_extras(vis32, opts, torch, cs, peak, steps=300, warmup=10):
                                    "samples_per_s": R * 250 / (us * 1e-6)}
     pw.close()
     del v250
+    # overlapping windows: a window of 16 samples every 8 (twice the windows), steady
+    # state (the first call of a stream completes one window fewer per row)
+    best = None
+    for P in (2, 4):
+        sw = RfiStream(62, 64, M, K, thr, "f32", window_hop=M // 2, lanes_per_row=P,
+                       warps_per_block=4)
+        sw.process(vis32, out=sw.alloc_outputs(256), stream=cs)    # leave the stream start
+        o = sw.alloc_outputs(256)
+        k, _, _, _ = time_kernel(sw, vis32, o, steps, warmup, torch, cs)
+        if best is None or k < best[0]:
+            best = (k, P, o["stats"].shape[-1])
+        sw.close()
+    k, P, nw = best
+    H = M // 2
+    # input, flags, statistics of 2x the windows, averages, and the pending half-window
+    # carried between blocks (totals 32 B, averaging sums 32 B per lane, 4 B of window
+    # flags; read and written)
+    nbytes = R * (256 * 32 + 4 * math.ceil(nw * H / 32) + 12 * nw + 36 + 2 * (36 + 32 * P))
+    res["sliding_windows_hop8"] = {"kernel_us": k * 1e6, "achieved_gbs": nbytes / k / 1e9,
+                                   "frac": nbytes / k / 1e9 / peak, "windows_per_row": nw,
+                                   "samples_per_s": R * 256 / k, "lanes_per_row": P}
     torch.cuda.empty_cache()
     return res
 

@@ -167,6 +167,20 @@ typedef enum {
  *                  boundary.  0 = 512 bytes (default), -1 = off, else a multiple of
  *                  128.  Launches recorded into a CUDA graph, the shared-memory loader
  *                  and batches keep plain stream order.
+ *   window_hop     overlapping windows: a window of M samples starts every H =
+ *                  window_hop samples (0 or M = no overlap, the paper's windows).
+ *                  Only H = M/2 is built: every sample lies in two windows and is
+ *                  flagged when either is.  A sample is final (flag known, averaged)
+ *                  once the second window holding it has been evaluated, M - H samples
+ *                  later, so a call returns the windows it completes (T/H, one fewer at
+ *                  the stream's start), the flag bits of the samples that became final
+ *                  (n_win * H bits from first_sample, see rfi_windows_for) and the bins
+ *                  of K samples (K a multiple of H) that closed.  T must be a multiple of
+ *                  H.  Needs time-only windows, float32 arithmetic, the direct loader,
+ *                  the 128-register budget, plain stores, no Kahan summation and
+ *                  lanes_per_row <= 4; excludes partial_windows and adaptive; single-
+ *                  stream calls only (a batch rejects the context).  Any split of a
+ *                  stream at multiples of H gives bit-identical results.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -189,6 +203,7 @@ typedef struct {
     int partial_windows;
     int adaptive;
     int overlap_bytes;
+    int window_hop;
 } rfi_options;
 
 /* Parameters of the online SK thresholds (option `adaptive`). */
@@ -221,7 +236,9 @@ int rfi_outputs_for(const rfi_ctx *ctx, int T, int *n_out);
  * partial_windows, n_win = T/M and first_sample = n_seen.  With it, a window left
  * open by earlier blocks is completed first: n_win = (n_seen mod M + T) / M and
  * first_sample = n_seen - n_seen mod M (Sec. 2: windows of consecutive samples of a
- * stream, whatever the correlator's block length). */
+ * stream, whatever the correlator's block length).  With overlapping windows (hop H),
+ * E(n) = n >= M ? (n - M)/H + 1 : 0 windows are complete after n samples: n_win =
+ * E(n_seen + T) - E(n_seen), n_win H flag bits per row, first_sample = E(n_seen) H. */
 int rfi_windows_for(const rfi_ctx *ctx, int T, int *n_win, long long *first_sample);
 
 /* The launch shape the context uses (after automatic choice). */

@@ -57,7 +57,8 @@ class rfi_options(ctypes.Structure):
                 ("loader", ctypes.c_int), ("tma_stage_windows", ctypes.c_int),
                 ("tma_stages", ctypes.c_int), ("debug_inject_wait_timeout", ctypes.c_int),
                 ("buffered_stores", ctypes.c_int), ("partial_windows", ctypes.c_int),
-                ("adaptive", ctypes.c_int), ("overlap_bytes", ctypes.c_int)]
+                ("adaptive", ctypes.c_int), ("overlap_bytes", ctypes.c_int),
+                ("window_hop", ctypes.c_int)]
 
 
 _lib = None

@@ -9,6 +9,7 @@
 #include "rfi_device.cuh"
 #include "rfi_internal.h"
 #include "rfi_kernels.h"
+#include "rfi_sliding.cuh"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -62,6 +63,17 @@ const void *find_tma(int dt, int spu, int P, int ch, int kahan, int lb) {
             const TmaInstance &in = t.items[i];
             if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan &&
                 in.lb == lb)
+                return in.fn;
+        }
+    return nullptr;
+}
+
+const void *find_sw(int dt, int spu, int P, int ch, int L) {
+    const SwTable tabs[] = {sw_instances_f32(), sw_instances_f16()};
+    for (const SwTable &t : tabs)
+        for (int i = 0; i < t.n; ++i) {
+            const SwInstance &in = t.items[i];
+            if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.L == L)
                 return in.fn;
         }
     return nullptr;
@@ -126,6 +138,10 @@ struct rfi_ctx {
     rfi_adaptation adp;
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     int ovl;                            // launch overlap: bytes per row requested early
+    int sw, H;                          // overlapping windows: a window every H samples
+    const void *sw_fn;                  // k_slide<...>
+    float *sw_buf;                      // [R][1][8] totals, [R][P][1][8] averaging sums of
+                                        // the pending segment, [R] window flag history
     const Instance *inst;
     const void *batch_fn;               // persistent kernel of rfi_process_batch
     long long n_seen;
@@ -225,7 +241,9 @@ int check_thresholds(const rfi_thresholds *t) {
 int choose_shape(rfi_ctx *c, int P_req) {
     const int dt = c->dtype == RFI_C64 ? DT_F32 : DT_F16;
     // samples per 32-byte load unit: binary16 packs two samples when M is even
-    int spu = (dt == DT_F16 && c->M % 2 == 0) ? 2 : 1;
+    // the run of samples the lanes of a row split: a window, or a hop of overlapping ones
+    const int U = c->sw ? c->H : c->M;
+    int spu = (dt == DT_F16 && U % 2 == 0) ? 2 : 1;
     int P = P_req;
     if (c->mixed) {
         // sums run sample after sample in one lane, as the tables order them
@@ -235,25 +253,37 @@ int choose_shape(rfi_ctx *c, int P_req) {
     }
     if (P == 0) {
         P = 2;
-        while (P > 1 && (c->M % (P * spu)) != 0) P >>= 1;
+        while (P > 1 && (U % (P * spu)) != 0) P >>= 1;
     }
     if (P * c->F > 32)
         return fail(RFI_EINVAL, "lanes_per_row (%d) x window_F (%d) must not exceed 32", P, c->F);
     if (P != 1 && P != 2 && P != 4 && P != 8 && P != 16 && P != 32)
         return fail(RFI_EINVAL, "lanes_per_row must be a power of two <= 32");
-    if (c->M % (P * spu) != 0) {
+    if (U % (P * spu) != 0) {
         if (dt == DT_F16 && spu == 2 && P_req != 0) {
-            return fail(RFI_EINVAL, "window M=%d is not a multiple of 2*lanes_per_row=%d", c->M,
-                        2 * P);
+            return fail(RFI_EINVAL, "%s %d is not a multiple of 2*lanes_per_row=%d",
+                        c->sw ? "hop H" : "window M", U, 2 * P);
         }
-        return fail(RFI_EINVAL, "window M=%d is not a multiple of lanes_per_row=%d", c->M, P);
+        return fail(RFI_EINVAL, "%s %d is not a multiple of lanes_per_row=%d",
+                    c->sw ? "hop H" : "window M", U, P);
     }
     if (dt == DT_F16 && spu == 1 && P != 1)
         return fail(RFI_EINVAL, "odd windows of binary16 input need lanes_per_row = 1");
     c->P = P;
     c->spu = spu;
-    c->S = c->M / (P * spu);
+    c->S = U / (P * spu);
     c->ch = largest_chunk(c->S);
+    if (c->sw) {
+        // overlapping windows: their own kernels, single-stream calls only
+        c->ch = c->S % 4 == 0 ? 4 : (c->S % 2 == 0 ? 2 : 1);
+        c->sw_fn = find_sw(dt, spu, P, c->ch, c->M / c->H);
+        c->inst = nullptr;
+        c->batch_fn = nullptr;
+        if (!c->sw_fn)
+            return fail(RFI_EUNSUPPORTED, "no overlapping-window kernel for lanes_per_row=%d "
+                                          "(1, 2 or 4)", P);
+        return RFI_OK;
+    }
     // the plain 128-register kernels exist with and without the prefetch code; the
     // other kinds always hold it
     const bool plain = c->lb == 0 && !c->mixed && !c->vs && !c->pw && !c->ad;
@@ -311,14 +341,36 @@ int choose_shape(rfi_ctx *c, int P_req) {
 // Samples of the open window carried into the next block, and the windows (hence
 // statistics columns and M nwin flag bits) a block of T samples completes.
 int phase_of(const rfi_ctx *c) { return c->pw ? (int)(c->n_seen % c->M) : 0; }
-int windows_for(const rfi_ctx *c, int T) { return (phase_of(c) + T) / c->M; }
+// Overlapping windows: windows complete once n samples of the stream have arrived.
+long long sw_evaluated(const rfi_ctx *c, long long n) {
+    return n >= c->M ? (n - c->M) / c->H + 1 : 0;
+}
+int windows_for(const rfi_ctx *c, int T) {
+    if (c->sw) return (int)(sw_evaluated(c, c->n_seen + T) - sw_evaluated(c, c->n_seen));
+    return (phase_of(c) + T) / c->M;
+}
+// Flag bits a completed window adds to a call's output (its samples that became final).
+int bits_per_window(const rfi_ctx *c) { return c->sw ? c->H : c->M; }
+// Stream index of the first sample whose flag the next call reports.
+long long first_final(const rfi_ctx *c) {
+    return c->sw ? sw_evaluated(c, c->n_seen) * c->H : c->n_seen - phase_of(c);
+}
+// Averaging bins the next call of T samples closes (bins close with final samples).
+long long outputs_for_c(const rfi_ctx *c, int T) {
+    if (c->sw) {
+        const long long f0 = first_final(c);
+        const long long f1 = sw_evaluated(c, c->n_seen + T) * c->H;
+        return f1 / c->K - f0 / c->K;
+    }
+    return (c->n_seen + T) / c->K - c->n_seen / c->K;
+}
 
 StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, float *avg,
                      float *weight, float *stats, long long r0, long long nrows) {
     StreamArgs a = {};
     const int nwin = windows_for(c, T);
-    const int Wpr = (nwin * c->M + 31) / 32;
-    const long long n_out = (c->n_seen + T) / c->K - c->n_seen / c->K;
+    const int Wpr = (nwin * bits_per_window(c) + 31) / 32;
+    const long long n_out = outputs_for_c(c, T);
     a.vis = static_cast<const char *>(vis) + r0 * (long long)T * sample_bytes(c->dtype);
     a.flags = flags + r0 * Wpr;
     a.avg = avg ? avg + r0 * n_out * 8 : nullptr;
@@ -348,8 +400,9 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.Wpr = Wpr;
     a.nwin = nwin;
     a.n_out = (int)n_out;
-    // samples of the open bin before window 0 (which may itself start in an earlier block)
-    a.bin_pos0 = (int)((c->n_seen - a.phase) % c->K);
+    // samples of the open bin before window 0 (which may itself start in an earlier block;
+    // with overlapping windows: final samples of the open bin)
+    a.bin_pos0 = (int)(first_final(c) % c->K);
     const double Md = (double)c->M * c->F;     // W = M F samples per window
     a.c0 = (float)((Md * c->thr.d + 1.0) / (Md - 1.0));
     a.s_low = (float)c->thr.s_low;
@@ -366,6 +419,11 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
 }
 
 int check_T(const rfi_ctx *c, int T) {
+    if (c->sw) {
+        if (T <= 0 || T % c->H != 0)
+            return fail(RFI_EINVAL, "T=%d must be a positive multiple of the hop H=%d", T, c->H);
+        return RFI_OK;
+    }
     if (c->pw) {
         if (T <= 0) return fail(RFI_EINVAL, "T=%d must be positive", T);
         if (T % c->spu != 0)
@@ -383,11 +441,11 @@ int check_block_args(const rfi_ctx *c, const void *vis, int T, const uint32_t *f
     int rc0;
     if ((rc0 = check_T(c, T))) return rc0;
     if ((long long)T * c->R > (1ll << 40)) return fail(RFI_EINVAL, "block too large");
-    const long long n_out = (c->n_seen + T) / c->K - c->n_seen / c->K;
+    const long long n_out = outputs_for_c(c, T);
     const size_t sb = sample_bytes(c->dtype);
     const size_t vis_align = (size_t)sb * c->spu;
     const size_t R = (size_t)c->R;
-    const size_t nw = windows_for(c, T), wpr = (nw * c->M + 31) / 32;
+    const size_t nw = windows_for(c, T), wpr = (nw * bits_per_window(c) + 31) / 32;
     if (!device) {
         if (!vis || (nw > 0 && (!flags || !stats)) || (n_out > 0 && (!avg || !weight)))
             return fail(RFI_EINVAL, "null host buffer");
@@ -432,12 +490,31 @@ bool capturing(cudaStream_t st) {
     return cs != cudaStreamCaptureStatusNone;
 }
 
-int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
+// Overlapping-window state of rows [r0, ...) (the pending segment and window flags).
+size_t sw_tot_floats(const rfi_ctx *c) { return (size_t)c->R * 8; }
+size_t sw_pend_floats(const rfi_ctx *c) { return (size_t)c->R * c->P * 8; }
+size_t sw_bytes(const rfi_ctx *c) {
+    return c->sw ? sizeof(float) * (sw_tot_floats(c) + sw_pend_floats(c)) + 4 * (size_t)c->R : 0;
+}
+
+int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st, long long r0 = 0) {
     if (a.R <= 0) return RFI_OK;
     const int RW = 32 / c->P;
     const long long groups = (a.R + RW - 1) / RW;
     const long long blocks = (groups + c->wpb - 1) / c->wpb;
     void *args[] = {const_cast<StreamArgs *>(&a)};
+    SlideArgs g;
+    const void *fn = c->sw ? c->sw_fn : (c->inst ? c->inst->block_fn : nullptr);
+    if (c->sw) {
+        g.s = a;
+        g.H = c->H;
+        g.warm = (int)std::min<long long>(c->n_seen / c->H, c->M / c->H - 1);
+        g.tot = c->sw_buf + r0 * 8;
+        g.pend = c->sw_buf + sw_tot_floats(c) + r0 * c->P * 8;
+        g.hist = reinterpret_cast<uint32_t *>(c->sw_buf + sw_tot_floats(c) + sw_pend_floats(c)) +
+                 r0;
+        args[0] = &g;
+    }
     cudaError_t e;
     if (c->loader == 1) {
         e = allow_smem(c->tma_fn, c->tma_smem);
@@ -457,10 +534,9 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelExC(&cfg, c->inst->block_fn, args);
+        e = cudaLaunchKernelExC(&cfg, fn, args);
     } else {
-        e = cudaLaunchKernel(c->inst->block_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args,
-                             0, st);
+        e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args, 0, st);
     }
     if (e == cudaSuccess && c->ad && a.nwin > 0) {     // advance the online thresholds
         const long long G = a.R / c->F;
@@ -509,6 +585,9 @@ int build_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *
         if ((rc = check_ctx(ctxs[i]))) return rc;
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return fail(RFI_EINVAL, "context %d appears twice", i);
+        if (ctxs[i]->sw)
+            return fail(RFI_EUNSUPPORTED, "context %d has overlapping windows (single-stream "
+                                          "calls only)", i);
         if (!ctxs[i]->batch_fn || ctxs[i]->batch_fn != ctxs[0]->batch_fn ||
             ctxs[i]->device != ctxs[0]->device)
             return fail(RFI_EINVAL, "context %d differs in dtype, M or launch shape", i);
@@ -544,6 +623,7 @@ void free_ctx(rfi_ctx *c) {
     if (c->carry) cudaFree(c->carry);
     if (c->hw) cudaFree(c->hw);
     if (c->adapt) cudaFree(c->adapt);
+    if (c->sw_buf) cudaFree(c->sw_buf);
     if (c->counter) cudaFree(c->counter);
     if (c->h_vis) cudaFree(c->h_vis);
     if (c->h_flags) cudaFree(c->h_flags);
@@ -595,9 +675,20 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     if (stations < 1 || channels < 1) return fail(RFI_EINVAL, "stations and channels must be >= 1");
     if (window_M < 1 || (window_M < 2 && !(opt && opt->window_F > 1)))
         return fail(RFI_EINVAL, "a window needs at least 2 samples (tau divides by W-1)");
-    if (avg_K < window_M || avg_K % window_M != 0)
+    // overlapping windows: a window every H = window_hop samples (0 or M: no overlap)
+    const int hop = (opt && opt->window_hop > 0) ? opt->window_hop : window_M;
+    if (opt && opt->window_hop < 0) return fail(RFI_EINVAL, "window_hop must be >= 0");
+    if (hop != window_M) {
+        if (hop > window_M || window_M % hop != 0 || window_M / hop != 2)
+            return fail(RFI_EUNSUPPORTED, "window_hop must be M/2 (two windows hold every "
+                                          "sample), got %d for M=%d", hop, window_M);
+        if (avg_K < hop || avg_K % hop != 0)
+            return fail(RFI_EINVAL, "averaging factor K=%d must be a positive multiple of the "
+                                    "hop H=%d", avg_K, hop);
+    } else if (avg_K < window_M || avg_K % window_M != 0) {
         return fail(RFI_EINVAL, "averaging factor K=%d must be a positive multiple of M=%d", avg_K,
                     window_M);
+    }
     if (dtype != RFI_C64 && dtype != RFI_C32H) return fail(RFI_EINVAL, "unknown dtype");
     int rc;
     if ((rc = check_thresholds(thr))) return rc;
@@ -670,6 +761,19 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->pf_bytes = o.prefetch_bytes ? o.prefetch_bytes : 1024;
     c->pf_groups = o.prefetch_groups > 0 ? o.prefetch_groups : 0;
     c->ovl = o.overlap_bytes == 0 ? 512 : (o.overlap_bytes < 0 ? 0 : o.overlap_bytes);
+    c->H = hop;
+    c->sw = hop != window_M;
+    if (c->sw) {
+        if (c->F != 1 || c->mixed || c->loader != 0 || c->lb != 0 || c->vs || c->pw || c->ad ||
+            o.compensated == 1) {
+            delete c;
+            return fail(RFI_EUNSUPPORTED, "overlapping windows need time-only windows, float32 "
+                                          "arithmetic, the direct loader, the 128-register "
+                                          "budget, plain stores and no Kahan summation, and "
+                                          "exclude partial_windows and adaptive");
+        }
+        c->kahan = 0;
+    }
     c->status = RFI_OK;
     if ((rc = choose_shape(c, o.lanes_per_row))) {
         delete c;
@@ -683,7 +787,9 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
         (c->pw && (e = cudaMalloc(&c->hw, (size_t)c->R * c->M * sample_bytes(dtype))) !=
                       cudaSuccess) ||
         (c->ad && (e = cudaMalloc(&c->adapt, adapt_bytes(c))) != cudaSuccess) ||
-        (c->ad && (e = cudaMemset(c->adapt, 0, adapt_bytes(c))) != cudaSuccess)) {
+        (c->ad && (e = cudaMemset(c->adapt, 0, adapt_bytes(c))) != cudaSuccess) ||
+        (c->sw && (e = cudaMalloc(&c->sw_buf, sw_bytes(c))) != cudaSuccess) ||
+        (c->sw && (e = cudaMemset(c->sw_buf, 0, sw_bytes(c))) != cudaSuccess)) {
         cudaGetLastError();
         free_ctx(c);
         return fail(e == cudaErrorMemoryAllocation ? RFI_ENOMEM : RFI_ECUDA,
@@ -692,8 +798,9 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->host_max_T = o.host_max_T;
     c->host_chunks = o.host_chunks ? o.host_chunks : 4;
     if (c->host_max_T > 0) {
-        const int T = c->pw ? c->host_max_T : c->host_max_T - c->host_max_T % c->M;
-        if (T < (c->pw ? 1 : c->M)) {
+        const int unit = c->sw ? c->H : c->M;
+        const int T = c->pw ? c->host_max_T : c->host_max_T - c->host_max_T % unit;
+        if (T < (c->pw ? 1 : unit)) {
             free_ctx(c);
             return fail(RFI_EINVAL, "host_max_T smaller than M");
         }
@@ -701,9 +808,11 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
         const size_t R = (size_t)c->R;
         const size_t n_out_max = (size_t)T / c->K + 1;
         // a carried partial window adds at most one completed window per block
-        const size_t nw_max = (size_t)(T + (c->pw ? c->M - 1 : 0)) / c->M;
+        const size_t nw_max =
+            c->sw ? (size_t)T / c->H : (size_t)(T + (c->pw ? c->M - 1 : 0)) / c->M;
         bool ok = cudaMalloc(&c->h_vis, R * T * sample_bytes(dtype)) == cudaSuccess &&
-                  cudaMalloc(&c->h_flags, R * ((nw_max * c->M + 31) / 32) * 4) == cudaSuccess &&
+                  cudaMalloc(&c->h_flags, R * ((nw_max * bits_per_window(c) + 31) / 32) * 4) ==
+                      cudaSuccess &&
                   cudaMalloc(&c->h_avg, R * n_out_max * 32) == cudaSuccess &&
                   cudaMalloc(&c->h_weight, R * n_out_max * 4) == cudaSuccess &&
                   cudaMalloc(&c->h_stats, 3 * R * nw_max * 4) == cudaSuccess &&
@@ -750,19 +859,21 @@ int rfi_rows(const rfi_ctx *ctx, long long *rows) {
 int rfi_outputs_for(const rfi_ctx *ctx, int T, int *n_out) {
     if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
     if (!n_out) return fail(RFI_EINVAL, "null output");
-    if (T < 0 || (!ctx->pw && T % ctx->M != 0))
-        return fail(RFI_EINVAL, "T must be a multiple of M");
-    *n_out = (int)((ctx->n_seen + T) / ctx->K - ctx->n_seen / ctx->K);
+    if (T < 0 || (!ctx->pw && T % (ctx->sw ? ctx->H : ctx->M) != 0))
+        return fail(RFI_EINVAL, "T must be a multiple of M (of the hop H with overlapping "
+                                "windows)");
+    *n_out = (int)outputs_for_c(ctx, T);
     return RFI_OK;
 }
 
 int rfi_windows_for(const rfi_ctx *ctx, int T, int *n_win, long long *first_sample) {
     if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
     if (!n_win) return fail(RFI_EINVAL, "null output");
-    if (T < 0 || (!ctx->pw && T % ctx->M != 0))
-        return fail(RFI_EINVAL, "T must be a multiple of M");
+    if (T < 0 || (!ctx->pw && T % (ctx->sw ? ctx->H : ctx->M) != 0))
+        return fail(RFI_EINVAL, "T must be a multiple of M (of the hop H with overlapping "
+                                "windows)");
     *n_win = windows_for(ctx, T);
-    if (first_sample) *first_sample = ctx->n_seen - phase_of(ctx);
+    if (first_sample) *first_sample = first_final(ctx);
     return RFI_OK;
 }
 
@@ -787,6 +898,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->partial_windows = ctx->pw;
     opt->adaptive = ctx->ad;
     opt->overlap_bytes = ctx->ovl > 0 ? ctx->ovl : -1;
+    opt->window_hop = ctx->sw ? ctx->H : 0;
     return RFI_OK;
 }
 
@@ -847,8 +959,8 @@ int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     const long long R = ctx->R;
     const int nch = (int)std::min<long long>(ctx->host_chunks, R);
-    const int nwin = windows_for(ctx, T), wpr = (nwin * ctx->M + 31) / 32;
-    const long long n_out = (ctx->n_seen + T) / ctx->K - ctx->n_seen / ctx->K;
+    const int nwin = windows_for(ctx, T), wpr = (nwin * bits_per_window(ctx) + 31) / 32;
+    const long long n_out = outputs_for_c(ctx, T);
     const size_t sb = sample_bytes(ctx->dtype);
     cudaError_t e;
     if ((e = cudaEventRecord(ctx->ev_start, user)) != cudaSuccess ||
@@ -868,7 +980,7 @@ int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "host path copy-in");
         StreamArgs a = make_args(ctx, ctx->h_vis, T, ctx->h_flags, ctx->h_avg, ctx->h_weight,
                                  ctx->h_stats, r0, nr);
-        if ((rc = launch_block(ctx, a, ctx->s_run))) return rc;
+        if ((rc = launch_block(ctx, a, ctx->s_run, r0))) return rc;
         e = cudaEventRecord(ctx->ev_run[k], ctx->s_run);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_run[k], 0);
         if (e == cudaSuccess && nwin > 0)
@@ -1021,7 +1133,7 @@ namespace {
 struct StateHeader {
     unsigned int magic, version;
     long long R, n_seen;
-    int P, M, K, F, dtype, pw, ad, pad;
+    int P, M, K, F, dtype, pw, ad, hop;
     rfi_thresholds thr;
     rfi_adaptation adp;
 };
@@ -1036,7 +1148,7 @@ int rfi_state_size(const rfi_ctx *ctx, size_t *bytes) {
     if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
     if (!bytes) return fail(RFI_EINVAL, "null output");
     *bytes = sizeof(StateHeader) + carry_bytes(ctx) + hw_bytes(ctx) +
-             (ctx->ad ? adapt_bytes(ctx) : 0);
+             (ctx->ad ? adapt_bytes(ctx) : 0) + sw_bytes(ctx);
     return RFI_OK;
 }
 
@@ -1048,8 +1160,9 @@ int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream) {
     if (!buf || bytes < need) return fail(RFI_EINVAL, "state buffer needs %zu bytes", need);
     StateHeader h = {};
     h.magic = STATE_MAGIC;
-    h.version = 3;
+    h.version = 4;
     h.pw = ctx->pw;
+    h.hop = ctx->H;
     h.ad = ctx->ad;
     h.adp = ctx->adp;
     h.R = ctx->R;
@@ -1070,6 +1183,9 @@ int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream) {
     if (e == cudaSuccess && ctx->ad)
         e = cudaMemcpy(dst + carry_bytes(ctx) + hw_bytes(ctx), ctx->adapt, adapt_bytes(ctx),
                        cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ctx->sw)
+        e = cudaMemcpy(dst + carry_bytes(ctx) + hw_bytes(ctx), ctx->sw_buf, sw_bytes(ctx),
+                       cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_get_state");
     return RFI_OK;
 }
@@ -1083,14 +1199,14 @@ int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes) {
                                           bytes, need);
     StateHeader h;
     std::memcpy(&h, buf, sizeof h);
-    if (h.magic != STATE_MAGIC || h.version != 3)
+    if (h.magic != STATE_MAGIC || h.version != 4)
         return fail(RFI_EINVAL, "not a saved stream state");
     if (h.R != ctx->R || h.P != ctx->P || h.M != ctx->M || h.K != ctx->K || h.F != ctx->F ||
-        h.pw != ctx->pw || h.ad != ctx->ad || h.dtype != (int)ctx->dtype)
+        h.pw != ctx->pw || h.ad != ctx->ad || h.dtype != (int)ctx->dtype || h.hop != ctx->H)
         return fail(RFI_EINVAL, "saved state is for another geometry or launch shape "
                                 "(rows %lld, lanes %d, M %d, K %d, F %d, partial windows %d, "
-                                "adaptive %d)",
-                    h.R, h.P, h.M, h.K, h.F, h.pw, h.ad);
+                                "adaptive %d, hop %d)",
+                    h.R, h.P, h.M, h.K, h.F, h.pw, h.ad, h.hop);
     if ((rc = check_thresholds(&h.thr))) return rc;
     cudaError_t e = cudaDeviceSynchronize();
     const char *src = static_cast<const char *>(buf) + sizeof h;
@@ -1100,6 +1216,9 @@ int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes) {
         e = cudaMemcpy(ctx->hw, src + carry_bytes(ctx), hw_bytes(ctx), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && ctx->ad)
         e = cudaMemcpy(ctx->adapt, src + carry_bytes(ctx) + hw_bytes(ctx), adapt_bytes(ctx),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ctx->sw)
+        e = cudaMemcpy(ctx->sw_buf, src + carry_bytes(ctx) + hw_bytes(ctx), sw_bytes(ctx),
                        cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_set_state");
     ctx->n_seen = h.n_seen;
@@ -1140,6 +1259,7 @@ int rfi_reset(rfi_ctx *ctx) {
         e = cudaMemset(ctx->carry, 0, sizeof(float) * 9 * (size_t)ctx->P * ctx->R);
     if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess && ctx->ad) e = cudaMemset(ctx->adapt, 0, adapt_bytes(ctx));
+    if (e == cudaSuccess && ctx->sw) e = cudaMemset(ctx->sw_buf, 0, sw_bytes(ctx));
     if (e != cudaSuccess) {
         ctx->status = RFI_ECUDA;
         return fail(RFI_ECUDA, "reset: %s", cudaGetErrorString(e));

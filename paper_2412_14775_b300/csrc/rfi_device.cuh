@@ -810,6 +810,28 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
 }
 
 // ---- kernels ---------------------------------------------------------------------
+// Launch overlap (programmatic dependent launch).  Every flagging kernel executes
+// griddepcontrol.launch_dependents on entry, so that the launch after it on the stream
+// may begin once all of its blocks have started.  A launch made with the attribute
+// calls this before anything else: until the grid before it has completed it only
+// requests the first ovl_bytes of the warp's rows into L2 (a hint; L2 is where all of
+// the GPU's writes meet, so this is safe whatever that grid writes); then it waits for
+// that grid, after which its writes are visible.  For a launch without the attribute
+// the wait returns at once.
+template <int DT, int P>
+__device__ __forceinline__ void overlap_prologue(const StreamArgs &a, long long group) {
+    if (a.ovl_bytes > 0) {
+        const int lane = threadIdx.x & 31;
+        const int SB = DT == DT_F32 ? 32 : 16;
+        const long long row = min(group * (32 / P) + lane / P, a.R - 1);
+        const long long rb = (long long)a.T * SB;
+        const char *rp = static_cast<const char *>(a.vis) + row * rb;
+        const long long n = min((long long)a.ovl_bytes, rb);
+        if (rfi_in(rp, n, a.vis, a.R * rb, a.err)) prefetch_rows<P>(rp, n, lane & (P - 1));
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // LB selects the register budget through the launch bounds: 0 -> at most 128
 // registers (blocks up to 512 threads), 1 -> 80 (256 threads, 3 blocks per SM),
 // 2 -> 64 (256 threads, 4 blocks per SM).  The arithmetic, hence every result, is the
@@ -823,27 +845,10 @@ template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, bool MIXED = f
           bool VS = false, bool PW = false, bool AD = false, bool PFT = false>
 __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_block(const __grid_constant__ StreamArgs a) {
-    // a launch that follows on the stream may begin once every block has started
-    // (programmatic dependent launch; a no-op for launches without the attribute)
     asm volatile("griddepcontrol.launch_dependents;");
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
-    if (a.ovl_bytes > 0) {
-        // launched to overlap the kernel before it on the stream: until that grid has
-        // completed, only request the first bytes of the warp's rows into L2 (a hint; L2
-        // is where all of the GPU's writes meet, so this is safe whatever that kernel
-        // writes)
-        const int lane = threadIdx.x & 31;
-        const int SB = DT == DT_F32 ? 32 : 16;
-        const long long row = min(group * (32 / P) + lane / P, a.R - 1);
-        const long long rb = (long long)a.T * SB;
-        const char *rp = static_cast<const char *>(a.vis) + row * rb;
-        const long long n = min((long long)a.ovl_bytes, rb);
-        if (rfi_in(rp, n, a.vis, a.R * rb, a.err)) prefetch_rows<P>(rp, n, lane & (P - 1));
-    }
-    // everything else (inputs, carries, outputs) only once that grid has completed and
-    // its writes are visible; returns at once when the launch depends on nothing
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    overlap_prologue<DT, P>(a, group);
     // the 128-register budget keeps two chunks in flight; tighter budgets load one
     // chunk at a time and rely on more resident warps instead
     process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS, PW, AD, PFT>(a, group);

@@ -45,6 +45,19 @@ struct TmaTable {
 TmaTable tma_instances_f32();
 TmaTable tma_instances_f16();
 
+// Overlapping windows (rfi_sliding.cuh): L = M / H = 2 windows hold every sample (the
+// registers of two more pending segments, L = 4, spill).
+struct SwInstance {
+    int dt, spu, P, ch, L;
+    const void *fn;         // k_slide<...>
+};
+struct SwTable {
+    const SwInstance *items;
+    int n;
+};
+SwTable sw_instances_f32();   // rfi_inst_sw_f32.cu
+SwTable sw_instances_f16();   // rfi_inst_sw_f16.cu
+
 }  // namespace rfi
 
 // Field `pf`: 1 = the kernel holds the L2 prefetch code (used when a launch asks for
@@ -144,3 +157,8 @@ TmaTable tma_instances_f16();
 #define RFI_TMA_PB(DT, SPU, P)                                                              \
     RFI_TMA_CH(DT, SPU, P, 0, 0), RFI_TMA_CH(DT, SPU, P, 1, 0), RFI_TMA_CH(DT, SPU, P, 0, 1), \
         RFI_TMA_CH(DT, SPU, P, 0, 2)
+
+#define RFI_SW(DT, SPU, P, CH, L) {DT, SPU, P, CH, L, (const void *)&rfi::k_slide<DT, SPU, P, CH, L>}
+// Chunks of 1, 2 or 4 units (5 would spill with the two pending-segment rings).
+#define RFI_SW_CH(DT, SPU, P, L)                                                            \
+    RFI_SW(DT, SPU, P, 1, L), RFI_SW(DT, SPU, P, 2, L), RFI_SW(DT, SPU, P, 4, L)

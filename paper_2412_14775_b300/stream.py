@@ -17,6 +17,9 @@ class RfiStream:
         self.R = B.rfi_rows(self.ctx)
         self.options = B.rfi_get_options(self.ctx)
         self.F = self.options["window_F"]
+        # flag bits a completed window adds to a call's output: M, or the hop H when
+        # windows overlap (the samples that became final)
+        self.bits_per_window = self.options["window_hop"] or M
 
     # -- outputs ------------------------------------------------------------------
     def outputs_for(self, T):
@@ -34,7 +37,8 @@ class RfiStream:
         n_win = self.windows_for(T)[0]
         kw = dict(device=device) if device != "cpu" else dict(pin_memory=pin_memory)
         return dict(
-            flags=torch.empty((self.R, (n_win * self.M + 31) // 32), dtype=torch.int32, **kw),
+            flags=torch.empty((self.R, (n_win * self.bits_per_window + 31) // 32),
+                              dtype=torch.int32, **kw),
             avg=torch.empty((self.R, n_out, 4, 2), dtype=torch.float32, **kw),
             weight=torch.empty((self.R, n_out), dtype=torch.float32, **kw),
             stats=torch.empty((3, self.R // self.F, n_win), dtype=torch.float32, **kw))
