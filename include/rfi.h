@@ -181,6 +181,16 @@ typedef enum {
  *                  lanes_per_row <= 4; excludes partial_windows and adaptive; single-
  *                  stream calls only (a batch rejects the context).  Any split of a
  *                  stream at multiples of H gives bit-identical results.
+ *   lane_split     0 = the lanes_per_row lanes of a row split every window's load
+ *                  units (default).  1 = they take whole windows in turn (lane j the
+ *                  stream's windows g with g mod P = j): no butterfly over the row's
+ *                  lanes and one evaluation per window, for small windows and T x F
+ *                  footprints, with P times shorter tasks than one lane per row.
+ *                  lanes_per_row 2, 4 or 8 (P need not divide M), K/M a multiple of
+ *                  lanes_per_row; float32 arithmetic, the direct loader, the 128-register
+ *                  budget, plain stores, no Kahan; excludes partial_windows, adaptive and
+ *                  window_hop; single-stream calls only.  Results differ from the
+ *                  default split only in the order in which a bin's sums are added.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */
@@ -204,6 +214,7 @@ typedef struct {
     int adaptive;
     int overlap_bytes;
     int window_hop;
+    int lane_split;
 } rfi_options;
 
 /* Parameters of the online SK thresholds (option `adaptive`). */

@@ -2,7 +2,8 @@
 
 For one workload (dtype, M, K, T, rows) it times candidate options of rfi_create_ex
 -- lanes per row P, warps per block, register budget, shared-memory staging,
-buffered output stores, L2 prefetch group size and distance -- on the
+window-parallel lanes, buffered output stores, L2 prefetch group size and distance --
+on the
 caller's device data with CUDA events, and returns the fastest.  Results are cached
 in memory and, when `cache_path` is given, in a JSON file keyed by the workload.
 
@@ -32,22 +33,27 @@ def candidates_p(M, dtype):
 
 
 def time_options(stations, channels, M, K, thr, dtype, vis, reps=30, warmup=5, **opts):
-    """Mean per-launch time (s) of one option set on `vis` (device tensor)."""
+    """Launch period (s) of one option set on `vis` (device tensor): launches back to
+    back, as a stream of blocks runs them (consecutive launches may overlap), events
+    around each of three runs of reps/3 launches, the median run."""
     import torch
     st = RfiStream(stations, channels, M, K, thr, dtype, **opts)
     T = vis.shape[-3]
     out = st.alloc_outputs(T, device=vis.device)
+    n = max(1, reps // 3)
     try:
         for _ in range(warmup):
             st.process(vis, out=out)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(reps)]
-        for a, b in ev:
+        runs = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            st.process(vis, out=out)
+            for _ in range(n):
+                st.process(vis, out=out)
             b.record()
+            runs.append((a, b))
         torch.cuda.synchronize()
-        return statistics.median(a.elapsed_time(b) for a, b in ev) * 1e-3
+        return statistics.median(a.elapsed_time(b) for a, b in runs) * 1e-3 / n
     finally:
         st.close()
 
@@ -105,10 +111,26 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
                     stage1.append((run(o), o))
                 except B.RfiError:      # no such kernel, or it does not fit the shared memory
                     continue
+    # window-parallel lanes: the lanes of a row take whole windows in turn (bins must
+    # hold a multiple of lanes_per_row windows)
+    for P in (2, 4, 8):
+        if P * F > 32 or (K // M) % P:
+            continue
+        for wpb in (4, 8):
+            o = dict(lanes_per_row=P, warps_per_block=wpb, max_registers=0, prefetch_groups=0,
+                     prefetch_bytes=1024, lane_split=1)
+            try:
+                stage1.append((run(o), o))
+            except B.RfiError:
+                continue
     stage1.sort(key=lambda x: x[0])
+
+    def direct(o):                      # unit-split direct loader: buffered stores, prefetch
+        return o.get("loader", 0) == 0 and o.get("lane_split", 0) == 0
+
     # the best direct-load shapes again with 16-byte buffered output stores (prefetch is
     # tried in stage 2 for the direct loader only)
-    for _, base in [x for x in stage1 if x[1].get("loader", 0) == 0][:3]:
+    for _, base in [x for x in stage1 if direct(x[1])][:3]:
         o = dict(base, buffered_stores=1)
         try:
             stage1.append((run(o), o))
@@ -116,7 +138,7 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
             continue
     stage1.sort(key=lambda x: x[0])
     best_t, best = stage1[0]
-    for _, base in [x for x in stage1 if x[1].get("loader", 0) == 0][:3]:
+    for _, base in [x for x in stage1 if direct(x[1])][:3]:
         for pg in (1, 2):
             for pb in (512, 1024):
                 o = dict(base, prefetch_groups=pg, prefetch_bytes=pb)

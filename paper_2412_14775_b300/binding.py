@@ -58,7 +58,7 @@ class rfi_options(ctypes.Structure):
                 ("tma_stages", ctypes.c_int), ("debug_inject_wait_timeout", ctypes.c_int),
                 ("buffered_stores", ctypes.c_int), ("partial_windows", ctypes.c_int),
                 ("adaptive", ctypes.c_int), ("overlap_bytes", ctypes.c_int),
-                ("window_hop", ctypes.c_int)]
+                ("window_hop", ctypes.c_int), ("lane_split", ctypes.c_int)]
 
 
 _lib = None

@@ -10,6 +10,7 @@
 #include "rfi_internal.h"
 #include "rfi_kernels.h"
 #include "rfi_sliding.cuh"
+#include "rfi_wpar.cuh"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -79,6 +80,16 @@ const void *find_sw(int dt, int spu, int P, int ch, int L) {
     return nullptr;
 }
 
+const void *find_wp(int dt, int spu, int P, int ch) {
+    const WpTable tabs[] = {wp_instances_f32(), wp_instances_f16()};
+    for (const WpTable &t : tabs)
+        for (int i = 0; i < t.n; ++i) {
+            const WpInstance &in = t.items[i];
+            if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch) return in.fn;
+        }
+    return nullptr;
+}
+
 int largest_chunk(int S) {
     static const int opts[] = {5, 4, 2, 1};
     for (int c : opts)
@@ -142,6 +153,8 @@ struct rfi_ctx {
     const void *sw_fn;                  // k_slide<...>
     float *sw_buf;                      // [R][1][8] totals, [R][P][1][8] averaging sums of
                                         // the pending segment, [R] window flag history
+    int wp;                             // window-parallel lanes (lane_split = 1)
+    const void *wp_fn;                  // k_wpar<...>
     const Instance *inst;
     const void *batch_fn;               // persistent kernel of rfi_process_batch
     long long n_seen;
@@ -241,6 +254,28 @@ int check_thresholds(const rfi_thresholds *t) {
 int choose_shape(rfi_ctx *c, int P_req) {
     const int dt = c->dtype == RFI_C64 ? DT_F32 : DT_F16;
     // samples per 32-byte load unit: binary16 packs two samples when M is even
+    if (c->wp) {
+        // window-parallel lanes: each lane loads whole windows, so P need not divide M
+        const int spu_w = (dt == DT_F16 && c->M % 2 == 0) ? 2 : 1;
+        const int P = P_req ? P_req : 2;
+        if (P != 2 && P != 4 && P != 8)
+            return fail(RFI_EINVAL, "lane_split = 1 needs lanes_per_row 2, 4 or 8");
+        if (P * c->F > 32)
+            return fail(RFI_EINVAL, "lanes_per_row (%d) x window_F (%d) must not exceed 32", P,
+                        c->F);
+        if ((c->K / c->M) % P != 0)
+            return fail(RFI_EINVAL, "lane_split = 1 needs K/M = %d windows per bin to be a "
+                                    "multiple of lanes_per_row = %d", c->K / c->M, P);
+        c->P = P;
+        c->spu = spu_w;
+        c->S = c->M / spu_w;                   // load units per window, all in one lane
+        c->ch = largest_chunk(c->S);
+        c->wp_fn = find_wp(dt, spu_w, P, c->ch);
+        c->inst = nullptr;
+        c->batch_fn = nullptr;
+        if (!c->wp_fn) return fail(RFI_EUNSUPPORTED, "no window-parallel kernel for this shape");
+        return RFI_OK;
+    }
     // the run of samples the lanes of a row split: a window, or a hop of overlapping ones
     const int U = c->sw ? c->H : c->M;
     int spu = (dt == DT_F16 && U % 2 == 0) ? 2 : 1;
@@ -504,7 +539,7 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st, long long r0 
     const long long blocks = (groups + c->wpb - 1) / c->wpb;
     void *args[] = {const_cast<StreamArgs *>(&a)};
     SlideArgs g;
-    const void *fn = c->sw ? c->sw_fn : (c->inst ? c->inst->block_fn : nullptr);
+    const void *fn = c->sw ? c->sw_fn : (c->wp ? c->wp_fn : (c->inst ? c->inst->block_fn : nullptr));
     if (c->sw) {
         g.s = a;
         g.H = c->H;
@@ -585,9 +620,9 @@ int build_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *
         if ((rc = check_ctx(ctxs[i]))) return rc;
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return fail(RFI_EINVAL, "context %d appears twice", i);
-        if (ctxs[i]->sw)
-            return fail(RFI_EUNSUPPORTED, "context %d has overlapping windows (single-stream "
-                                          "calls only)", i);
+        if (ctxs[i]->sw || ctxs[i]->wp)
+            return fail(RFI_EUNSUPPORTED, "context %d has overlapping windows or window-"
+                                          "parallel lanes (single-stream calls only)", i);
         if (!ctxs[i]->batch_fn || ctxs[i]->batch_fn != ctxs[0]->batch_fn ||
             ctxs[i]->device != ctxs[0]->device)
             return fail(RFI_EINVAL, "context %d differs in dtype, M or launch shape", i);
@@ -701,7 +736,8 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
         o.precision > 1 || o.loader < 0 || o.loader > 1 || o.tma_stage_windows < 0 ||
         o.tma_stage_windows > 64 || o.tma_stages < 0 || o.tma_stages > 8 ||
         o.debug_inject_wait_timeout < 0 || o.debug_inject_wait_timeout > 1 ||
-        o.overlap_bytes < -1 || (o.overlap_bytes > 0 && o.overlap_bytes % 128 != 0))
+        o.overlap_bytes < -1 || (o.overlap_bytes > 0 && o.overlap_bytes % 128 != 0) ||
+        o.lane_split < 0 || o.lane_split > 1)
         return fail(RFI_EINVAL, "bad options");
 
     rfi_ctx *c = new (std::nothrow) rfi_ctx();
@@ -763,6 +799,16 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->ovl = o.overlap_bytes == 0 ? 512 : (o.overlap_bytes < 0 ? 0 : o.overlap_bytes);
     c->H = hop;
     c->sw = hop != window_M;
+    c->wp = o.lane_split == 1;
+    if (c->wp && (c->sw || c->mixed || c->loader != 0 || c->lb != 0 || c->vs || c->pw || c->ad ||
+                  o.compensated == 1)) {
+        delete c;
+        return fail(RFI_EUNSUPPORTED, "lane_split = 1 needs float32 arithmetic, the direct "
+                                      "loader, the 128-register budget, plain stores and no "
+                                      "Kahan summation, and excludes partial_windows, adaptive "
+                                      "and window_hop");
+    }
+    if (c->wp) c->kahan = 0;
     if (c->sw) {
         if (c->F != 1 || c->mixed || c->loader != 0 || c->lb != 0 || c->vs || c->pw || c->ad ||
             o.compensated == 1) {
@@ -899,6 +945,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->adaptive = ctx->ad;
     opt->overlap_bytes = ctx->ovl > 0 ? ctx->ovl : -1;
     opt->window_hop = ctx->sw ? ctx->H : 0;
+    opt->lane_split = ctx->wp;
     return RFI_OK;
 }
 
@@ -1133,7 +1180,7 @@ namespace {
 struct StateHeader {
     unsigned int magic, version;
     long long R, n_seen;
-    int P, M, K, F, dtype, pw, ad, hop;
+    int P, M, K, F, dtype, pw, ad, hop, split, pad;
     rfi_thresholds thr;
     rfi_adaptation adp;
 };
@@ -1163,6 +1210,7 @@ int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream) {
     h.version = 4;
     h.pw = ctx->pw;
     h.hop = ctx->H;
+    h.split = ctx->wp;
     h.ad = ctx->ad;
     h.adp = ctx->adp;
     h.R = ctx->R;
@@ -1202,7 +1250,8 @@ int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes) {
     if (h.magic != STATE_MAGIC || h.version != 4)
         return fail(RFI_EINVAL, "not a saved stream state");
     if (h.R != ctx->R || h.P != ctx->P || h.M != ctx->M || h.K != ctx->K || h.F != ctx->F ||
-        h.pw != ctx->pw || h.ad != ctx->ad || h.dtype != (int)ctx->dtype || h.hop != ctx->H)
+        h.pw != ctx->pw || h.ad != ctx->ad || h.dtype != (int)ctx->dtype || h.hop != ctx->H ||
+        h.split != ctx->wp)
         return fail(RFI_EINVAL, "saved state is for another geometry or launch shape "
                                 "(rows %lld, lanes %d, M %d, K %d, F %d, partial windows %d, "
                                 "adaptive %d, hop %d)",

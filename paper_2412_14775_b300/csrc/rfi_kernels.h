@@ -58,6 +58,18 @@ struct SwTable {
 SwTable sw_instances_f32();   // rfi_inst_sw_f32.cu
 SwTable sw_instances_f16();   // rfi_inst_sw_f16.cu
 
+// Window-parallel lanes (rfi_wpar.cuh): the P lanes of a row take whole windows in turn.
+struct WpInstance {
+    int dt, spu, P, ch;
+    const void *fn;         // k_wpar<...>
+};
+struct WpTable {
+    const WpInstance *items;
+    int n;
+};
+WpTable wp_instances_f32();   // rfi_inst_wp_f32.cu
+WpTable wp_instances_f16();   // rfi_inst_wp_f16.cu
+
 }  // namespace rfi
 
 // Field `pf`: 1 = the kernel holds the L2 prefetch code (used when a launch asks for
@@ -162,3 +174,7 @@ SwTable sw_instances_f16();   // rfi_inst_sw_f16.cu
 // Chunks of 1, 2 or 4 units (5 would spill with the two pending-segment rings).
 #define RFI_SW_CH(DT, SPU, P, L)                                                            \
     RFI_SW(DT, SPU, P, 1, L), RFI_SW(DT, SPU, P, 2, L), RFI_SW(DT, SPU, P, 4, L)
+
+#define RFI_WP(DT, SPU, P, CH) {DT, SPU, P, CH, (const void *)&rfi::k_wpar<DT, SPU, P, CH>}
+#define RFI_WP_CH(DT, SPU, P)                                                               \
+    RFI_WP(DT, SPU, P, 1), RFI_WP(DT, SPU, P, 2), RFI_WP(DT, SPU, P, 4), RFI_WP(DT, SPU, P, 5)

@@ -1,0 +1,250 @@
+// rfi_wpar.cuh -- window-parallel lanes: the P lanes of a row take whole windows in
+// turn (lane j evaluates the stream's windows g with g mod P = j) instead of splitting
+// every window's load units.
+//
+// For small windows (few samples per lane per window) and T x F footprints this keeps
+// the per-window work (butterfly, statistics, flag bits, stores) at one evaluation per
+// window with no butterfly over the row's lanes, like one lane per row, while a warp
+// holds 32/P rows instead of 32, so a launch is cut into P times more, shorter tasks
+// (one lane per row left 1.65 waves of 32-row tasks on the LOFAR-scale block).  The
+// arithmetic of a window is that of process_group with P = 1 (the same per-sample
+// sums in the same order, then the footprint butterfly over the F rows); the
+// averaging sums of a bin are kept per lane (the lane's windows) and added over the P
+// lanes when the bin closes, so results differ from the other lane splits only by the
+// order of those additions, and any split of a stream at multiples of M is
+// bit-identical to one block (window ownership follows the stream's window index).
+#pragma once
+#include "rfi_device.cuh"
+
+namespace rfi {
+
+template <int DT, int SPU, int P, int CH>
+__device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long group) {
+    static_assert(P >= 2, "one lane per row is the plain kernel");
+    constexpr int RW = 32 / P;
+    constexpr int SB = (DT == DT_F32) ? 32 : 16;
+    constexpr int UB = SB * SPU;
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (P - 1);
+    const int r = lane / P;                          // the lane's row in the warp
+    const long long row = group * RW + r;
+    const bool active = row < a.R;
+    const long long rowc = active ? row : a.R - 1;
+    const int MU = a.M / SPU;                        // load units per window
+    const long long WB = (long long)a.M * SB;        // bytes per window of one row
+    const char *rp = static_cast<const char *>(a.vis) + rowc * (long long)a.T * SB;
+    const long long vis_ext = a.R * (long long)a.T * SB;
+    const long long carry_ext = a.R * P * 9 * 4ll;
+    const long long stats_ext = (2 * a.stats_plane + (a.R / a.F) * a.nwin) * 4ll;
+    const long long flags_ext = a.R * a.Wpr * 4ll;
+    const long long avg_ext = a.R * a.n_out * 32ll;
+    const long long weight_ext = a.R * a.n_out * 4ll;
+
+    // windows of this launch are local indices 0..nwin-1, global g0 + i; lane j owns the
+    // windows with g mod P = j.  Round k covers the P windows kP - s .. kP - s + P - 1
+    // (s = g0 mod P), lane j the window kP - s + j.
+    // s = g0 mod P: bins hold a multiple of P windows and start at a multiple of K, so
+    // the windows of the open bin before this launch give it
+    const int s = (a.bin_pos0 / a.M) % P;
+    const int NR = (a.nwin + s + P - 1) / P;                  // rounds
+    const int wpbin = a.K / a.M;                              // windows per bin (mult. of P)
+    int wib = a.bin_pos0 / a.M;                               // windows of the open bin seen
+    int bin = 0;
+
+    float acc[8];
+    float cnt = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = 0.f;
+    if (a.bin_pos0 != 0) {
+        const float *cp = a.carry + (rowc * P + j) * 9;
+        if (rfi_in(cp, 36, a.carry, carry_ext, a.err)) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = cp[c];
+            cnt = cp[8];
+        }
+    }
+    float *const st_row = a.stats + (rowc / a.F) * a.nwin;
+    const bool st_lead = active && (row % a.F) == 0;
+    const int PF = P * a.F;
+    uint32_t *const fl_row = a.flags + rowc * a.Wpr;
+    const bool lead = active && j == 0;
+    const long long plane = a.stats_plane;
+    const int fmode = (32 % a.M == 0) ? 0 : ((a.M % 32 == 0) ? 1 : 2);
+    const uint32_t wmask = a.M >= 32 ? FULL : ((1u << a.M) - 1u);
+    const int words_per_window = a.M >> 5;
+    uint32_t fword = 0;
+    const int nbits = a.T;
+    const float2 eps2 = make_float2(a.eps, a.eps);
+
+    // the lane's load stream: chunk c of round k reads units c*CH .. c*CH + CH-1 of its
+    // window kP - s + j (nothing for a window outside this launch)
+    const int nch = MU / CH;
+    const int Q = NR * nch;
+    auto load_chunk = [&](int k, int c, Unit<UB>(&u)[CH]) {
+        const int i = k * P - s + j;
+        const bool ok = i >= 0 && i < a.nwin;
+        const char *p0 = rp + (long long)i * WB + (long long)c * CH * UB;
+#pragma unroll
+        for (int e = 0; e < CH; ++e) {
+            const char *p = p0 + e * UB;
+            if (ok && rfi_in(p, UB, a.vis, vis_ext, a.err)) load_unit(p, u[e]);
+            else u[e] = Unit<UB>{};
+        }
+    };
+    WinAcc A;
+    const float2 zero2 = make_float2(0.f, 0.f);
+    A.s = A.c = A.q = A.u = A.v = zero2;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) A.a[c] = zero2;
+    auto consume = [&](const Unit<UB>(&u)[CH]) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int k = 0; k < SPU; ++k) accumulate<false>(A, stokes_of<DT, UB>(u[c], k), eps2);
+    };
+    auto end_round = [&](int k) {
+        const int i = k * P - s + j;                 // this lane's window
+        const bool ok = i >= 0 && i < a.nwin;
+        float S1 = A.s.x, S2 = A.s.y, qr = A.q.x, ur = A.u.x, vr = A.v.x;
+        float qi = A.q.y, ui = A.u.y, vi = A.v.y;
+        if (PF > P) {                                // the footprint's F rows
+#pragma unroll
+            for (int o = P; o < 32; o <<= 1) {
+                if (o < PF) {
+                    S1 += __shfl_xor_sync(FULL, S1, o);
+                    S2 += __shfl_xor_sync(FULL, S2, o);
+                    qr += __shfl_xor_sync(FULL, qr, o);
+                    ur += __shfl_xor_sync(FULL, ur, o);
+                    vr += __shfl_xor_sync(FULL, vr, o);
+                    qi += __shfl_xor_sync(FULL, qi, o);
+                    ui += __shfl_xor_sync(FULL, ui, o);
+                    vi += __shfl_xor_sync(FULL, vi, o);
+                }
+            }
+        }
+        // Table 1 groups 6-7 / Sec. 2.1 and Table 2 groups 5-6 / Sec. 2.2
+        const float tau = a.c0 * (a.fM * S2 * rcp_approx(S1 * S1 + a.eps) - 1.0f);
+        const float r_re = sqrt_approx(qr * qr + ur * ur + vr * vr) * a.invM;
+        const float r_im = sqrt_approx(qi * qi + ui * ui + vi * vi) * a.invM;
+        const bool f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
+                       !(r_im <= a.gamma);
+        if (ok && st_lead && rfi_in(st_row + i, 4, a.stats, stats_ext, a.err) &&
+            rfi_in(st_row + i + 2 * plane, 4, a.stats, stats_ext, a.err)) {
+            st_row[i] = tau;
+            st_row[i + plane] = r_re;
+            st_row[i + 2 * plane] = r_im;
+        }
+        // the row's P window flags of this round, in window order, to its lead lane
+        const unsigned fb = __ballot_sync(FULL, ok && f);
+        const unsigned rowbits = (fb >> (r * P)) & ((1u << P) - 1u);
+#pragma unroll
+        for (int e = 0; e < P; ++e) {
+            const int wi = k * P - s + e;            // window of lane e of the row
+            if (wi < 0 || wi >= a.nwin) continue;
+            const bool fe = (rowbits >> e) & 1u;
+            if (fmode == 0) {
+                const int b0 = (wi * a.M) & 31;
+                if (fe) fword |= wmask << b0;
+                if (b0 + a.M == 32) {
+                    if (lead && rfi_in(fl_row + ((wi * a.M) >> 5), 4, a.flags, flags_ext, a.err))
+                        fl_row[(wi * a.M) >> 5] = fword;
+                    fword = 0;
+                }
+            } else if (fmode == 1) {
+                const int w0 = (wi * a.M) >> 5;
+                if (lead && rfi_in(fl_row + w0, 4ll * words_per_window, a.flags, flags_ext, a.err))
+                    for (int q = 0; q < words_per_window; ++q) fl_row[w0 + q] = fe ? FULL : 0u;
+            } else {
+                int lo = wi * a.M;
+                const int hi = lo + a.M;
+                while (lo < hi) {
+                    const int b0 = lo & 31;
+                    const int nb = min(hi - lo, 32 - b0);
+                    if (fe) fword |= (nb == 32 ? FULL : ((1u << nb) - 1u)) << b0;
+                    lo += nb;
+                    if ((lo & 31) == 0) {
+                        if (lead && rfi_in(fl_row + ((lo - 1) >> 5), 4, a.flags, flags_ext, a.err))
+                            fl_row[(lo - 1) >> 5] = fword;
+                        fword = 0;
+                    }
+                }
+            }
+        }
+        // flagged samples leave the average (end of Sec. 2.1); bins hold whole rounds
+        if (ok && !f) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                acc[2 * c] += A.a[c].x;
+                acc[2 * c + 1] += A.a[c].y;
+            }
+            cnt += (float)a.M;
+        }
+        // windows of the open bin seen: this round's windows inside the launch
+        const int first = max(k * P - s, 0), last = min(k * P - s + P, a.nwin);
+        wib += last - first;
+        if (wib == wpbin) {
+            float tot[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
+            const float n = allsum<P>(cnt);
+            if (lead && rfi_in(a.avg + (row * a.n_out + bin) * 8, 32, a.avg, avg_ext, a.err) &&
+                rfi_in(a.weight + row * a.n_out + bin, 4, a.weight, weight_ext, a.err)) {
+                float4 *ap = reinterpret_cast<float4 *>(a.avg + (row * a.n_out + bin) * 8);
+                const float h = n > 0.f ? 0.5f * __frcp_rn(n) : 0.f;
+                const float Ir = tot[0], Ii = tot[1], Qr = tot[2], Qi = tot[3];
+                const float Ur = tot[4], Ui = tot[5], Vr = tot[6], Vi = tot[7];
+                ap[0] = make_float4((Ir + Qr) * h, (Ii + Qi) * h, (Ur + Vi) * h, (Ui - Vr) * h);
+                ap[1] = make_float4((Ur - Vi) * h, (Ui + Vr) * h, (Ir - Qr) * h, (Ii - Qi) * h);
+                a.weight[row * a.n_out + bin] = __fdiv_rn(n, a.fK);
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = 0.f;
+            cnt = 0.f;
+            wib = 0;
+            ++bin;
+        }
+        A.s = A.q = A.u = A.v = zero2;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) A.a[c] = zero2;
+    };
+
+    Unit<UB> ua[CH], ub[CH];
+    int kl = 0, cl = 0;                              // next chunk to load (round, chunk)
+    int kc = 0, cc = 0;                              // chunk being consumed
+    auto advance = [&](int &k, int &c) {
+        if (++c == nch) { c = 0; ++k; }
+    };
+    if (Q > 0) { load_chunk(kl, cl, ua); advance(kl, cl); }
+    for (int q = 0; q < Q; q += 2) {
+        if (q + 1 < Q) { load_chunk(kl, cl, ub); advance(kl, cl); }
+        consume(ua);
+        if (cc + 1 == nch) end_round(kc);
+        advance(kc, cc);
+        if (q + 1 >= Q) break;
+        if (q + 2 < Q) { load_chunk(kl, cl, ua); advance(kl, cl); }
+        consume(ub);
+        if (cc + 1 == nch) end_round(kc);
+        advance(kc, cc);
+    }
+    if (nbits & 31) {
+        if (lead && rfi_in(fl_row + (nbits >> 5), 4, a.flags, flags_ext, a.err))
+            fl_row[nbits >> 5] = fword;
+    }
+    if (wib != 0 && active && rfi_in(a.carry + (row * P + j) * 9, 36, a.carry, carry_ext, a.err)) {
+        float *cp = a.carry + (row * P + j) * 9;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) cp[c] = acc[c];
+        cp[8] = cnt;
+    }
+}
+
+template <int DT, int SPU, int P, int CH>
+__global__ void __launch_bounds__(512, 1) k_wpar(const __grid_constant__ StreamArgs a) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (group * (32 / P) >= a.R) return;     // whole warp leaves together
+    overlap_prologue<DT, P>(a, group);
+    process_group_wp<DT, SPU, P, CH>(a, group);
+}
+
+}  // namespace rfi

@@ -25,10 +25,10 @@ def test_parity_suite_under_debug_bounds_build():
     env = dict(os.environ, RFI_LIBRARY=lib)
     cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider",
            "tests/test_parity_gpu.py", "tests/test_adaptive_gpu.py", "tests/test_fuzz_gpu.py",
-           "tests/test_sliding_gpu.py", "tests/test_overlap_gpu.py",
+           "tests/test_sliding_gpu.py", "tests/test_overlap_gpu.py", "tests/test_wpar_gpu.py",
            "-k", "shapes or partial or batch or host or tma or buffered or footprints or "
                  "checkpoint or degenerate or online or warm_up or edge or random or "
-                 "sliding or overlap"]
+                 "sliding or overlap or window_parallel"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1500)
     tail = (r.stdout + r.stderr)[-3000:]
     assert r.returncode == 0, tail

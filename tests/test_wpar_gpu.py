@@ -1,0 +1,93 @@
+"""Window-parallel lanes (lane_split = 1): the lanes of a row take whole windows in turn.
+
+Every block of a stream against the FP64 oracle (the tolerances of tests/parity.py),
+including windows of odd length, T x F footprints, bins that straddle blocks (so a
+block starts in the middle of a round of windows), and bit-identity of any split of a
+stream at multiples of M with one block.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from paper_2412_14775_b300 import RfiStream, binding, default_thresholds
+from paper_2412_14775_b300.binding import RfiError
+from parity import to_device_rows
+from test_parity_gpu import _check_stream
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype,M,K,P,F,Ts", [
+    ("f16", 5, 250, 2, 4, [250, 250]),          # the paper's 5 x 4 footprint
+    ("f32", 5, 20, 2, 4, [35, 45, 20]),         # bins straddle blocks, odd M
+    ("f32", 5, 20, 4, 4, [15, 65]),
+    ("f16", 10, 40, 2, 2, [50, 70]),            # 10 x 2 footprint
+    ("f16", 8, 32, 2, 1, [64, 24, 40]),
+    ("f16", 8, 32, 4, 1, [96, 32]),
+    ("f32", 16, 64, 4, 1, [48, 80]),
+    ("f16", 3, 12, 2, 1, [9, 15, 12]),          # odd M, one sample per 16-byte load
+    ("f32", 64, 128, 2, 1, [128, 64]),          # long windows: 16 chunks per window
+    ("f32", 4, 32, 8, 1, [40, 24]),
+], ids=["f16_5x4", "f32_5x4_straddle", "f32_5x4_P4", "f16_10x2", "f16_M8", "f16_M8_P4",
+        "f32_M16_P4", "f16_M3", "f32_M64", "f32_M4_P8"])
+def test_window_parallel_matches_oracle(dtype, M, K, P, F, Ts):
+    reps = _check_stream(7, 8, M, K, Ts, dtype, seed=91, lanes_per_row=P,
+                         window_F=F, lane_split=1)
+    assert reps
+
+
+def test_window_parallel_splits_bit_identical():
+    M, K, T = 5, 20, 400
+    thr = default_thresholds(5 * 4)
+    d = synth.tiny_block(seed=93, stations=8, channels=8, T=T, duty=0.08)["vis"]
+    v = to_device_rows(d, "f16")
+    for P in (2, 4):
+        opts = dict(lanes_per_row=P, window_F=4, lane_split=1)
+        one = RfiStream(8, 8, M, K, thr, "f16", **opts)
+        assert one.options["lane_split"] == 1
+        a = one.process(v)
+        st = RfiStream(8, 8, M, K, thr, "f16", **opts)
+        parts = [st.process(v[:, lo:hi].contiguous())
+                 for lo, hi in ((0, 5), (5, 35), (35, 200), (200, 215), (215, 400))]
+        torch.cuda.synchronize()
+        for key in ("avg", "weight"):
+            assert torch.equal(torch.cat([p[key] for p in parts], dim=1), a[key]), (P, key)
+        assert torch.equal(torch.cat([p["stats"] for p in parts], dim=2), a["stats"]), P
+        # flag bits: concatenate the blocks' bit streams
+        bits = []
+        for p in parts:
+            n = p["stats"].shape[2] * M
+            w = p["flags"].cpu().numpy().view(np.uint32).astype(np.uint64)
+            t = np.arange(n)
+            bits.append(((w[:, t // 32] >> (t % 32).astype(np.uint64)) & 1).astype(bool))
+        w = a["flags"].cpu().numpy().view(np.uint32).astype(np.uint64)
+        t = np.arange(T)
+        ref = ((w[:, t // 32] >> (t % 32).astype(np.uint64)) & 1).astype(bool)
+        assert np.array_equal(np.concatenate(bits, axis=1), ref), P
+        one.close(); st.close()
+
+
+def test_window_parallel_option_checks():
+    thr = default_thresholds(8)
+    for bad in (dict(lane_split=1, lanes_per_row=1), dict(lane_split=1, lanes_per_row=16),
+                dict(lane_split=2), dict(lane_split=1, adaptive=1),
+                dict(lane_split=1, partial_windows=1), dict(lane_split=1, window_hop=4),
+                dict(lane_split=1, loader=1), dict(lane_split=1, max_registers=64),
+                dict(lane_split=1, lanes_per_row=4, window_F=16)):
+        with pytest.raises(RfiError):
+            RfiStream(4, 16, 8, 32, thr, "f32", **bad)
+    with pytest.raises(RfiError):            # K/M = 3 windows per bin, not a multiple of 2
+        RfiStream(4, 4, 8, 24, thr, "f32", lane_split=1)
+    a = RfiStream(4, 4, 8, 32, thr, "f32", lane_split=1)
+    b = RfiStream(4, 4, 8, 32, thr, "f32")
+    with pytest.raises(RfiError):            # single-stream calls only
+        z = [s.alloc_outputs(32) for s in (a, b)]
+        v = torch.zeros((a.R, 32, 4, 2), device="cuda")
+        binding.rfi_process_batch([a.ctx, b.ctx], [v, v], [32, 32], [o["flags"] for o in z],
+                                  [o["avg"] for o in z], [o["weight"] for o in z],
+                                  [o["stats"] for o in z])
+    blob = binding.rfi_get_state(a.ctx)
+    with pytest.raises(RfiError):            # the carry means something else per lane
+        binding.rfi_set_state(b.ctx, blob)
+    a.close(); b.close()
