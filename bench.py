@@ -724,6 +724,25 @@ def main():
                "h2d_link_gbs_plain_copy": link,
                "h2d_gbs_in_e2e": hin.numel() * hin.element_size() * args.e2e_steps / dt / 1e9}
         hst.close()
+        # the same through binary16 storage: half the bytes cross the host link
+        o16 = (extras["fp16"]["M16"]["options"] if "fp16" in extras
+               else dict(lanes_per_row=2, warps_per_block=4))
+        h16 = RfiStream(62, 64, M, K, thr, "f16", **dict(o16, host_max_T=T, host_chunks=8))
+        hin16 = host32.half().pin_memory()
+        hout16 = h16.alloc_outputs(T, device="cpu", pin_memory=True)
+        for _ in range(3):
+            h16.process_host(hin16, out=hout16)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            h16.process_host(hin16, out=hout16)
+            _ = float(hout16["weight"][0, 0])
+        dt16 = time.perf_counter() - t0
+        e2e["binary16_storage"] = {
+            "value": samples * args.e2e_steps / dt16, "unit": "samples/s",
+            "h2d_bytes_per_step": hin16.numel() * hin16.element_size(),
+            "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in hout16.values())}
+        h16.close()
+        del hin16, hout16
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

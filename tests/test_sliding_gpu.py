@@ -58,7 +58,10 @@ def _run(st, orc, vis_np, cuts, dtype):
 def _compare(g, o, thr, M, H, K):
     W = M
     for key, floor in (("tau", 1.0), ("r_re", W ** -0.5), ("r_im", W ** -0.5)):
-        e = rel_err(g[key].astype(np.float64), o[key], floor)
+        x = g[key].astype(np.float64)
+        both_nan = np.isnan(x) & np.isnan(o[key])
+        assert not (np.isnan(x) ^ np.isnan(o[key])).any(), f"{key}: NaN on one side only"
+        e = np.where(both_nan, 0.0, rel_err(x, o[key], floor))
         assert e.size == 0 or float(e.max()) <= STAT_RTOL, (key, float(e.max()))
 
     def near(x, t, floor):
@@ -216,3 +219,28 @@ def test_sliding_random_combinations_match_oracle(seed):
         _compare(g, o, thr, M, H, K)
         st.close()
         ran += 1
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_sliding_non_finite_samples(dtype):
+    """A NaN or an infinity makes both windows that hold it flagged, so every sample of
+    them is flagged and left out of the averages, which stay finite."""
+    M, H, K, T = 16, 8, 32, 96
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=87, stations=3, channels=4, T=T)["vis"].copy()
+    d[0, 0] = 0.0
+    d[1, 1, 5, 2, 0] = np.nan
+    d[2, 3, 40, 0, 1] = np.inf
+    d[3, 2, 17, 3, 0] = -np.inf
+    st = RfiStream(3, 4, M, K, thr, dtype, window_hop=H)
+    orc = oracle.SlidingOracleStream(st.R, M, H, K, **thr)
+    g, o = _run(st, orc, d, (48,), dtype)
+    _compare(g, o, thr, M, H, K)
+    rows = d.reshape(st.R, T, 4, 2)
+    for r in range(st.R):
+        bad = np.flatnonzero(~np.isfinite(rows[r]).all(axis=(1, 2)))
+        for t in bad:                # windows t//H - 1 and t//H hold it
+            lo, hi = max(0, (t // H - 1) * H), min(t // H * H + M, g["bits"].shape[1])
+            assert g["bits"][r, lo:hi].all(), (r, t)
+    assert np.isfinite(g["avg"]).all() and np.isfinite(g["weight"]).all()
+    st.close()

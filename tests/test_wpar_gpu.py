@@ -91,3 +91,24 @@ def test_window_parallel_option_checks():
     with pytest.raises(RfiError):            # the carry means something else per lane
         binding.rfi_set_state(b.ctx, blob)
     a.close(); b.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_window_parallel_edge_values(dtype):
+    """All-zero windows and non-finite samples, as for the default lane split."""
+    from test_parity_gpu import _oracle_input, compare, run_gpu
+    import oracle
+    M, K, T = 8, 32, 64
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=95, stations=3, channels=4, T=T)["vis"].copy()
+    d[0, 0] = 0.0
+    d[1, 1, 5, 2, 0] = np.nan
+    d[2, 3, 40, 0, 1] = np.inf
+    d[3, 2, 17, 3, 0] = -np.inf
+    st = RfiStream(3, 4, M, K, thr, dtype, lanes_per_row=4, lane_split=1)
+    g = run_gpu(st, to_device_rows(d, dtype))
+    o = oracle.OracleStream(st.R, M, K, **thr).process(_oracle_input(d, dtype))
+    assert g["tau"][0, 0] == np.float32(-(M * thr["d"] + 1) / (M - 1))
+    compare(g, o, thr, M, K)
+    assert np.isfinite(g["avg"]).all() and np.isfinite(g["weight"]).all()
+    st.close()
