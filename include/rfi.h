@@ -189,8 +189,9 @@ typedef enum {
  *                  lanes_per_row 2, 4 or 8 (P need not divide M), K/M a multiple of
  *                  lanes_per_row; float32 arithmetic, the direct loader, the 128-register
  *                  budget, plain stores, no Kahan; excludes partial_windows, adaptive and
- *                  window_hop; single-stream calls only.  Results differ from the
- *                  default split only in the order in which a bin's sums are added.
+ *                  window_hop; a batch takes it with contexts of the same split and
+ *                  shape.  Results differ from the default split only in the order in
+ *                  which a bin's sums are added.
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */

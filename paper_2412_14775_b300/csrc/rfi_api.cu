@@ -80,12 +80,12 @@ const void *find_sw(int dt, int spu, int P, int ch, int L) {
     return nullptr;
 }
 
-const void *find_wp(int dt, int spu, int P, int ch) {
+const WpInstance *find_wp(int dt, int spu, int P, int ch) {
     const WpTable tabs[] = {wp_instances_f32(), wp_instances_f16()};
     for (const WpTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const WpInstance &in = t.items[i];
-            if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch) return in.fn;
+            if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch) return &in;
         }
     return nullptr;
 }
@@ -270,10 +270,11 @@ int choose_shape(rfi_ctx *c, int P_req) {
         c->spu = spu_w;
         c->S = c->M / spu_w;                   // load units per window, all in one lane
         c->ch = largest_chunk(c->S);
-        c->wp_fn = find_wp(dt, spu_w, P, c->ch);
+        const WpInstance *wi = find_wp(dt, spu_w, P, c->ch);
         c->inst = nullptr;
-        c->batch_fn = nullptr;
-        if (!c->wp_fn) return fail(RFI_EUNSUPPORTED, "no window-parallel kernel for this shape");
+        if (!wi) return fail(RFI_EUNSUPPORTED, "no window-parallel kernel for this shape");
+        c->wp_fn = wi->fn;
+        c->batch_fn = wi->batch_fn;
         return RFI_OK;
     }
     // the run of samples the lanes of a row split: a window, or a hop of overlapping ones
@@ -620,9 +621,9 @@ int build_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *
         if ((rc = check_ctx(ctxs[i]))) return rc;
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return fail(RFI_EINVAL, "context %d appears twice", i);
-        if (ctxs[i]->sw || ctxs[i]->wp)
-            return fail(RFI_EUNSUPPORTED, "context %d has overlapping windows or window-"
-                                          "parallel lanes (single-stream calls only)", i);
+        if (ctxs[i]->sw)
+            return fail(RFI_EUNSUPPORTED, "context %d has overlapping windows (single-stream "
+                                          "calls only)", i);
         if (!ctxs[i]->batch_fn || ctxs[i]->batch_fn != ctxs[0]->batch_fn ||
             ctxs[i]->device != ctxs[0]->device)
             return fail(RFI_EINVAL, "context %d differs in dtype, M or launch shape", i);

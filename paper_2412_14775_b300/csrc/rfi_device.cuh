@@ -869,9 +869,10 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
 // Persistent batch: every warp takes (stream, row group) tasks from a device counter
 // until none is left, claiming its next task when it starts one; the last block to
 // finish resets the counter for the next launch in stream order.
-template <int DT, int SPU, int P, int CH, bool KAHAN, bool MIXED = false, bool PW = false,
-          bool AD = false, bool PFT = false>
-__global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchArgs b) {
+// The task loop of a persistent batch launch: every warp calls task(stream, group) for
+// (stream, row group) tasks taken from the device counter until none is left.
+template <class Task>
+__device__ __forceinline__ void run_batch_tasks(const BatchArgs &b, Task &&task) {
     const int lane = threadIdx.x & 31;
     unsigned long long tn = 0;
     if (lane == 0) tn = atomicAdd(b.counter, 1ull);
@@ -888,8 +889,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchA
             const bool le = k < b.n && b.prefix[k + 1] <= (long long)t;
             i += __popc(__ballot_sync(FULL, le));
         }
-        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW, AD, PFT, true>(
-            b.s[i], (long long)t - b.prefix[i]);
+        task(b.s[i], (long long)t - b.prefix[i]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -901,6 +901,15 @@ __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchA
             atomicExch(done, 0u);
         }
     }
+}
+
+template <int DT, int SPU, int P, int CH, bool KAHAN, bool MIXED = false, bool PW = false,
+          bool AD = false, bool PFT = false>
+__global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchArgs b) {
+    run_batch_tasks(b, [](const StreamArgs &a, long long group) {
+        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW, AD, PFT, true>(a,
+                                                                                       group);
+    });
 }
 
 }  // namespace rfi

@@ -62,6 +62,7 @@ SwTable sw_instances_f16();   // rfi_inst_sw_f16.cu
 struct WpInstance {
     int dt, spu, P, ch;
     const void *fn;         // k_wpar<...>
+    const void *batch_fn;   // k_batch_wp<...>
 };
 struct WpTable {
     const WpInstance *items;
@@ -175,6 +176,8 @@ WpTable wp_instances_f16();   // rfi_inst_wp_f16.cu
 #define RFI_SW_CH(DT, SPU, P, L)                                                            \
     RFI_SW(DT, SPU, P, 1, L), RFI_SW(DT, SPU, P, 2, L), RFI_SW(DT, SPU, P, 4, L)
 
-#define RFI_WP(DT, SPU, P, CH) {DT, SPU, P, CH, (const void *)&rfi::k_wpar<DT, SPU, P, CH>}
+#define RFI_WP(DT, SPU, P, CH)                                                              \
+    {DT, SPU, P, CH, (const void *)&rfi::k_wpar<DT, SPU, P, CH>,                            \
+     (const void *)&rfi::k_batch_wp<DT, SPU, P, CH>}
 #define RFI_WP_CH(DT, SPU, P)                                                               \
     RFI_WP(DT, SPU, P, 1), RFI_WP(DT, SPU, P, 2), RFI_WP(DT, SPU, P, 4), RFI_WP(DT, SPU, P, 5)

@@ -12,7 +12,8 @@
 // averaging sums of a bin are kept per lane (the lane's windows) and added over the P
 // lanes when the bin closes, so results differ from the other lane splits only by the
 // order of those additions, and any split of a stream at multiples of M is
-// bit-identical to one block (window ownership follows the stream's window index).
+// bit-identical to one block (window ownership follows the stream's window index), as
+// is a batch (k_batch_wp runs the same routine per task).
 #pragma once
 #include "rfi_device.cuh"
 
@@ -245,6 +246,14 @@ __global__ void __launch_bounds__(512, 1) k_wpar(const __grid_constant__ StreamA
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     overlap_prologue<DT, P>(a, group);
     process_group_wp<DT, SPU, P, CH>(a, group);
+}
+
+// The persistent batch over window-parallel contexts (same task loop as k_batch).
+template <int DT, int SPU, int P, int CH>
+__global__ void __launch_bounds__(512, 1) k_batch_wp(const __grid_constant__ BatchArgs b) {
+    run_batch_tasks(b, [](const StreamArgs &a, long long group) {
+        process_group_wp<DT, SPU, P, CH>(a, group);
+    });
 }
 
 }  // namespace rfi

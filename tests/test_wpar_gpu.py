@@ -81,7 +81,7 @@ def test_window_parallel_option_checks():
         RfiStream(4, 4, 8, 24, thr, "f32", lane_split=1)
     a = RfiStream(4, 4, 8, 32, thr, "f32", lane_split=1)
     b = RfiStream(4, 4, 8, 32, thr, "f32")
-    with pytest.raises(RfiError):            # single-stream calls only
+    with pytest.raises(RfiError):            # a batch does not mix lane splits
         z = [s.alloc_outputs(32) for s in (a, b)]
         v = torch.zeros((a.R, 32, 4, 2), device="cuda")
         binding.rfi_process_batch([a.ctx, b.ctx], [v, v], [32, 32], [o["flags"] for o in z],
@@ -112,3 +112,35 @@ def test_window_parallel_edge_values(dtype):
     compare(g, o, thr, M, K)
     assert np.isfinite(g["avg"]).all() and np.isfinite(g["weight"]).all()
     st.close()
+
+
+def test_window_parallel_batch_bit_identical():
+    """Uneven window-parallel streams in one persistent launch (and from a CUDA graph)
+    give each stream's single-launch results bit for bit, block after block."""
+    M, K, T = 5, 20, 100
+    thr = default_thresholds(5 * 4)
+    geo = [(5, 8), (9, 4), (3, 12), (7, 8)]
+    opts = dict(lanes_per_row=2, window_F=4, lane_split=1)
+    data = [synth.tiny_block(seed=97 + i, stations=n, channels=c, T=2 * T, duty=0.08)["vis"]
+            for i, (n, c) in enumerate(geo)]
+    solo = [RfiStream(n, c, M, K, thr, "f16", **opts) for n, c in geo]
+    bat = [RfiStream(n, c, M, K, thr, "f16", **opts) for n, c in geo]
+    g = binding.rfi_batch_graph_create([s.ctx for s in bat[2:]], [T, T])
+    for k in range(2):
+        vis = [to_device_rows(d[:, :, k * T:(k + 1) * T], "f16") for d in data]
+        outs = [s.alloc_outputs(T) for s in bat]
+        binding.rfi_process_batch([s.ctx for s in bat[:2]], vis[:2], [T, T],
+                                  [o["flags"] for o in outs[:2]], [o["avg"] for o in outs[:2]],
+                                  [o["weight"] for o in outs[:2]], [o["stats"] for o in outs[:2]])
+        binding.rfi_batch_graph_launch(g, vis[2:], [o["flags"] for o in outs[2:]],
+                                       [o["avg"] for o in outs[2:]],
+                                       [o["weight"] for o in outs[2:]],
+                                       [o["stats"] for o in outs[2:]])
+        exp = [s.process(v) for s, v in zip(solo, vis)]
+        torch.cuda.synchronize()
+        for e, o in zip(exp, outs):
+            for key in ("flags", "avg", "weight", "stats"):
+                assert torch.equal(e[key], o[key]), (k, key)
+    binding.rfi_batch_graph_destroy(g)
+    for s in solo + bat:
+        s.close()
