@@ -370,6 +370,26 @@ __device__ __forceinline__ float rowsum(float v, int PF) {
     return v;
 }
 
+// The averaged output of one closed bin of one row (end of Sec. 2.1): tot holds the
+// sums of (I, Q, U, V), re and im, over its unflagged samples and n their count; the
+// correlations are xx = (I + Q)/2, yy = (I - Q)/2, xy = (U - jV)/2, yx = (U + jV)/2, and
+// the weight is n / K (an empty bin gives zeros).
+__device__ __forceinline__ void store_bin(const StreamArgs &a, long long row, int bin,
+                                          const float (&tot)[8], float n) {
+    float *const avp = a.avg + (row * a.n_out + bin) * 8;
+    float *const wtp = a.weight + row * a.n_out + bin;
+    if (!rfi_in(avp, 32, a.avg, a.R * a.n_out * 32ll, a.err) ||
+        !rfi_in(wtp, 4, a.weight, a.R * a.n_out * 4ll, a.err))
+        return;
+    float4 *ap = reinterpret_cast<float4 *>(avp);
+    const float h = n > 0.f ? 0.5f * __frcp_rn(n) : 0.f;
+    const float Ir = tot[0], Ii = tot[1], Qr = tot[2], Qi = tot[3];
+    const float Ur = tot[4], Ui = tot[5], Vr = tot[6], Vi = tot[7];
+    ap[0] = make_float4((Ir + Qr) * h, (Ii + Qi) * h, (Ur + Vi) * h, (Ui - Vr) * h);
+    ap[1] = make_float4((Ur - Vi) * h, (Ui + Vr) * h, (Ir - Qr) * h, (Ii - Qi) * h);
+    *wtp = __fdiv_rn(n, a.fK);
+}
+
 // ---- one row group of one stream ---------------------------------------------
 // DT: input dtype; SPU: samples per load unit (1 or 2); P: lanes per row;
 // CH: load units issued together per lane; KAHAN: compensated S1, S2.
@@ -426,8 +446,6 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     const long long carry_ext = a.R * P * 9 * 4ll;
     const long long stats_ext = (2 * a.stats_plane + (a.R / a.F) * a.nwin) * 4ll;
     const long long flags_ext = a.R * a.Wpr * 4ll;
-    const long long avg_ext = a.R * a.n_out * 32ll;
-    const long long weight_ext = a.R * a.n_out * 4ll;
     const long long adapt_ext = (a.R / a.F) * 16ll;
     // the row's SK interval (set below, from the state at the start of the launch; the
     // state is advanced afterwards by k_adapt from the statistics and flags stored here)
@@ -665,18 +683,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
 #pragma unroll
             for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
             const float n = allsum<P>(cnt);
-            if (lead && rfi_in(a.avg + (row * a.n_out + bin) * 8, 32, a.avg, avg_ext, a.err) &&
-                rfi_in(a.weight + row * a.n_out + bin, 4, a.weight, weight_ext, a.err)) {
-                // tot holds sums of (I, Q, U, V); the correlations are xx = (I + Q)/2,
-                // yy = (I - Q)/2, xy = (U - jV)/2, yx = (U + jV)/2
-                float4 *ap = reinterpret_cast<float4 *>(a.avg + (row * a.n_out + bin) * 8);
-                const float h = n > 0.f ? 0.5f * __frcp_rn(n) : 0.f;
-                const float Ir = tot[0], Ii = tot[1], Qr = tot[2], Qi = tot[3];
-                const float Ur = tot[4], Ui = tot[5], Vr = tot[6], Vi = tot[7];
-                ap[0] = make_float4((Ir + Qr) * h, (Ii + Qi) * h, (Ur + Vi) * h, (Ui - Vr) * h);
-                ap[1] = make_float4((Ur - Vi) * h, (Ui + Vr) * h, (Ir - Qr) * h, (Ii - Qi) * h);
-                a.weight[row * a.n_out + bin] = __fdiv_rn(n, a.fK);
-            }
+            if (lead) store_bin(a, row, bin, tot, n);
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = 0.f;
             cnt = 0.f;

@@ -54,8 +54,6 @@ __device__ __forceinline__ void process_group_sw(const SlideArgs &g, long long g
     const long long carry_ext = a.R * P * 9 * 4ll;
     const long long stats_ext = (2 * a.stats_plane + a.R * a.nwin) * 4ll;
     const long long flags_ext = a.R * a.Wpr * 4ll;
-    const long long avg_ext = a.R * a.n_out * 32ll;
-    const long long weight_ext = a.R * a.n_out * 4ll;
     const long long tot_ext = a.R * LM * 32ll;
     const long long pend_ext = a.R * P * LM * 32ll;
     const long long hist_ext = a.R * 4ll;
@@ -209,16 +207,7 @@ __device__ __forceinline__ void process_group_sw(const SlideArgs &g, long long g
 #pragma unroll
                 for (int c = 0; c < 8; ++c) t8[c] = allsum<P>(acc[c]);
                 const float n = allsum<P>(cnt);
-                if (lead && rfi_in(a.avg + (row * a.n_out + bin) * 8, 32, a.avg, avg_ext, a.err) &&
-                    rfi_in(a.weight + row * a.n_out + bin, 4, a.weight, weight_ext, a.err)) {
-                    float4 *ap = reinterpret_cast<float4 *>(a.avg + (row * a.n_out + bin) * 8);
-                    const float h = n > 0.f ? 0.5f * __frcp_rn(n) : 0.f;
-                    const float Ir = t8[0], Ii = t8[1], Qr = t8[2], Qi = t8[3];
-                    const float Ur = t8[4], Ui = t8[5], Vr = t8[6], Vi = t8[7];
-                    ap[0] = make_float4((Ir + Qr) * h, (Ii + Qi) * h, (Ur + Vi) * h, (Ui - Vr) * h);
-                    ap[1] = make_float4((Ur - Vi) * h, (Ui + Vr) * h, (Ir - Qr) * h, (Ii - Qi) * h);
-                    a.weight[row * a.n_out + bin] = __fdiv_rn(n, a.fK);
-                }
+                if (lead) store_bin(a, row, bin, t8, n);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) acc[c] = 0.f;
                 cnt = 0.f;

@@ -38,8 +38,6 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
     const long long carry_ext = a.R * P * 9 * 4ll;
     const long long stats_ext = (2 * a.stats_plane + (a.R / a.F) * a.nwin) * 4ll;
     const long long flags_ext = a.R * a.Wpr * 4ll;
-    const long long avg_ext = a.R * a.n_out * 32ll;
-    const long long weight_ext = a.R * a.n_out * 4ll;
 
     // windows of this launch are local indices 0..nwin-1, global g0 + i; lane j owns the
     // windows with g mod P = j.  Round k covers the P windows kP - s .. kP - s + P - 1
@@ -188,16 +186,7 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
 #pragma unroll
             for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
             const float n = allsum<P>(cnt);
-            if (lead && rfi_in(a.avg + (row * a.n_out + bin) * 8, 32, a.avg, avg_ext, a.err) &&
-                rfi_in(a.weight + row * a.n_out + bin, 4, a.weight, weight_ext, a.err)) {
-                float4 *ap = reinterpret_cast<float4 *>(a.avg + (row * a.n_out + bin) * 8);
-                const float h = n > 0.f ? 0.5f * __frcp_rn(n) : 0.f;
-                const float Ir = tot[0], Ii = tot[1], Qr = tot[2], Qi = tot[3];
-                const float Ur = tot[4], Ui = tot[5], Vr = tot[6], Vi = tot[7];
-                ap[0] = make_float4((Ir + Qr) * h, (Ii + Qi) * h, (Ur + Vi) * h, (Ui - Vr) * h);
-                ap[1] = make_float4((Ur - Vi) * h, (Ui + Vr) * h, (Ir - Qr) * h, (Ii - Qi) * h);
-                a.weight[row * a.n_out + bin] = __fdiv_rn(n, a.fK);
-            }
+            if (lead) store_bin(a, row, bin, tot, n);
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = 0.f;
             cnt = 0.f;
