@@ -144,3 +144,23 @@ def test_window_parallel_batch_bit_identical():
     binding.rfi_batch_graph_destroy(g)
     for s in solo + bat:
         s.close()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_window_parallel_random_combinations(seed):
+    """Seeded random window, footprint, lanes per row, bin and block lengths."""
+    rng = np.random.default_rng(3000 + seed)
+    ran = 0
+    while ran < 3:
+        dtype = str(rng.choice(["f32", "f16"]))
+        M = int(rng.choice([2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 32]))
+        F = int(rng.choice([1, 1, 2, 4]))
+        P = int(rng.choice([2, 4, 8]))
+        if P * F > 32 or M * F < 2:
+            continue
+        K = M * P * int(rng.integers(1, 4))
+        Ts = [M * int(rng.integers(1, 3 * P + 1)) for _ in range(int(rng.integers(1, 4)))]
+        _check_stream(int(rng.integers(2, 7)), F * int(rng.integers(1, 4)), M, K, Ts, dtype,
+                      seed=int(rng.integers(1, 1 << 30)), lanes_per_row=P, window_F=F,
+                      lane_split=1)
+        ran += 1
