@@ -164,3 +164,31 @@ def test_window_parallel_random_combinations(seed):
                       seed=int(rng.integers(1, 1 << 30)), lanes_per_row=P, window_F=F,
                       lane_split=1)
         ran += 1
+
+
+def test_window_parallel_host_path_and_state():
+    """The host-buffer entry point (rows staged in chunks) and a saved / restored state
+    give the device path's results bit for bit."""
+    M, K, T = 8, 32, 48
+    thr = default_thresholds(M)
+    d = synth.tiny_block(seed=99, stations=6, channels=8, T=4 * T, duty=0.08)["vis"]
+    v = to_device_rows(d, "f32")
+    opts = dict(lanes_per_row=4, lane_split=1)
+    dev = RfiStream(6, 8, M, K, thr, "f32", **opts)
+    host = RfiStream(6, 8, M, K, thr, "f32", host_max_T=T, host_chunks=3, **opts)
+    for k in range(2):
+        blk = v[:, k * T:(k + 1) * T].contiguous()
+        x = dev.process(blk)
+        y = host.process_host(blk.cpu().pin_memory())
+        torch.cuda.synchronize()
+        for key in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(x[key].cpu(), y[key]), (k, key)
+    other = RfiStream(6, 8, M, K, thr, "f32", **opts)
+    binding.rfi_set_state(other.ctx, binding.rfi_get_state(dev.ctx))
+    for k in range(2, 4):
+        blk = v[:, k * T:(k + 1) * T].contiguous()
+        x, z = dev.process(blk), other.process(blk)
+        torch.cuda.synchronize()
+        for key in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(x[key], z[key]), (k, key)
+    dev.close(); host.close(); other.close()
