@@ -187,9 +187,11 @@ typedef enum {
  *                  lanes and one evaluation per window, for small windows and T x F
  *                  footprints, with P times shorter tasks than one lane per row.
  *                  lanes_per_row 2, 4 or 8 (P need not divide M), K/M a multiple of
- *                  lanes_per_row; float32 arithmetic, the direct loader, the 128-register
- *                  budget, plain stores, no Kahan; excludes partial_windows, adaptive and
- *                  window_hop; a batch takes it with contexts of the same split and
+ *                  lanes_per_row; the direct loader, the 128-register budget, plain
+ *                  stores, no Kahan (precision = 1 with time-only windows: each window
+ *                  still runs sample by sample in one lane, so its statistics and flags
+ *                  equal those of the one-lane mixed kernel); excludes partial_windows,
+ *                  adaptive and window_hop; a batch takes it with contexts of the same split and
  *                  shape.  Results differ from the default split only in the order in
  *                  which a bin's sums are added.
  * The reduction order of a window depends only on (M, P, load unit), so two

@@ -80,12 +80,13 @@ const void *find_sw(int dt, int spu, int P, int ch, int L) {
     return nullptr;
 }
 
-const WpInstance *find_wp(int dt, int spu, int P, int ch) {
+const WpInstance *find_wp(int dt, int spu, int P, int ch, int mixed) {
     const WpTable tabs[] = {wp_instances_f32(), wp_instances_f16()};
     for (const WpTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const WpInstance &in = t.items[i];
-            if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch) return &in;
+            if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.mixed == mixed)
+                return &in;
         }
     return nullptr;
 }
@@ -270,7 +271,9 @@ int choose_shape(rfi_ctx *c, int P_req) {
         c->spu = spu_w;
         c->S = c->M / spu_w;                   // load units per window, all in one lane
         c->ch = largest_chunk(c->S);
-        const WpInstance *wi = find_wp(dt, spu_w, P, c->ch);
+        if (c->mixed && c->F != 1)
+            return fail(RFI_EINVAL, "precision = 1 supports time-only windows");
+        const WpInstance *wi = find_wp(dt, spu_w, P, c->ch, c->mixed);
         c->inst = nullptr;
         if (!wi) return fail(RFI_EUNSUPPORTED, "no window-parallel kernel for this shape");
         c->wp_fn = wi->fn;
@@ -801,13 +804,13 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->H = hop;
     c->sw = hop != window_M;
     c->wp = o.lane_split == 1;
-    if (c->wp && (c->sw || c->mixed || c->loader != 0 || c->lb != 0 || c->vs || c->pw || c->ad ||
+    if (c->wp && (c->sw || c->loader != 0 || c->lb != 0 || c->vs || c->pw || c->ad ||
                   o.compensated == 1)) {
         delete c;
-        return fail(RFI_EUNSUPPORTED, "lane_split = 1 needs float32 arithmetic, the direct "
-                                      "loader, the 128-register budget, plain stores and no "
-                                      "Kahan summation, and excludes partial_windows, adaptive "
-                                      "and window_hop");
+        return fail(RFI_EUNSUPPORTED, "lane_split = 1 needs the direct loader, the "
+                                      "128-register budget, plain stores and no Kahan "
+                                      "summation, and excludes partial_windows, adaptive and "
+                                      "window_hop");
     }
     if (c->wp) c->kahan = 0;
     if (c->sw) {

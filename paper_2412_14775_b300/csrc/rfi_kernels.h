@@ -60,7 +60,7 @@ SwTable sw_instances_f16();   // rfi_inst_sw_f16.cu
 
 // Window-parallel lanes (rfi_wpar.cuh): the P lanes of a row take whole windows in turn.
 struct WpInstance {
-    int dt, spu, P, ch;
+    int dt, spu, P, ch, mixed;
     const void *fn;         // k_wpar<...>
     const void *batch_fn;   // k_batch_wp<...>
 };
@@ -177,7 +177,13 @@ WpTable wp_instances_f16();   // rfi_inst_wp_f16.cu
     RFI_SW(DT, SPU, P, 1, L), RFI_SW(DT, SPU, P, 2, L), RFI_SW(DT, SPU, P, 4, L)
 
 #define RFI_WP(DT, SPU, P, CH)                                                              \
-    {DT, SPU, P, CH, (const void *)&rfi::k_wpar<DT, SPU, P, CH>,                            \
+    {DT, SPU, P, CH, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH>,                         \
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH>}
+#define RFI_WPM(DT, SPU, P, CH)                                                             \
+    {DT, SPU, P, CH, 1, (const void *)&rfi::k_wpar<DT, SPU, P, CH, true>,                   \
+     (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, true>}
 #define RFI_WP_CH(DT, SPU, P)                                                               \
     RFI_WP(DT, SPU, P, 1), RFI_WP(DT, SPU, P, 2), RFI_WP(DT, SPU, P, 4), RFI_WP(DT, SPU, P, 5)
+#define RFI_WPM_CH(DT, SPU, P)                                                              \
+    RFI_WPM(DT, SPU, P, 1), RFI_WPM(DT, SPU, P, 2), RFI_WPM(DT, SPU, P, 4),                  \
+        RFI_WPM(DT, SPU, P, 5)

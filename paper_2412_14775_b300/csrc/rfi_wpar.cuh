@@ -19,7 +19,10 @@
 
 namespace rfi {
 
-template <int DT, int SPU, int P, int CH>
+// MIXED: the paper's trained mixed precision (Tables 3 and 4): each window is still
+// summed sample by sample in one lane, in the tables' order, so statistics and flags
+// are those of the one-lane-per-row mixed kernel bit for bit (time-only windows).
+template <int DT, int SPU, int P, int CH, bool MIXED = false>
 __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long group) {
     static_assert(P >= 2, "one lane per row is the plain kernel");
     constexpr int RW = 32 / P;
@@ -99,14 +102,19 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
 #pragma unroll
         for (int c = 0; c < CH; ++c)
 #pragma unroll
-            for (int k = 0; k < SPU; ++k) accumulate<false>(A, stokes_of<DT, UB>(u[c], k), eps2);
+            for (int k = 0; k < SPU; ++k) {
+                if constexpr (MIXED)
+                    accumulate_mixed(A, stokes_of<DT, UB>(u[c], k), a.eps);
+                else
+                    accumulate<false>(A, stokes_of<DT, UB>(u[c], k), eps2);
+            }
     };
     auto end_round = [&](int k) {
         const int i = k * P - s + j;                 // this lane's window
         const bool ok = i >= 0 && i < a.nwin;
         float S1 = A.s.x, S2 = A.s.y, qr = A.q.x, ur = A.u.x, vr = A.v.x;
         float qi = A.q.y, ui = A.u.y, vi = A.v.y;
-        if (PF > P) {                                // the footprint's F rows
+        if (!MIXED && PF > P) {                      // the footprint's F rows
 #pragma unroll
             for (int o = P; o < 32; o <<= 1) {
                 if (o < PF) {
@@ -121,12 +129,18 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
                 }
             }
         }
-        // Table 1 groups 6-7 / Sec. 2.1 and Table 2 groups 5-6 / Sec. 2.2
-        const float tau = a.c0 * (a.fM * S2 * rcp_approx(S1 * S1 + a.eps) - 1.0f);
-        const float r_re = sqrt_approx(qr * qr + ur * ur + vr * vr) * a.invM;
-        const float r_im = sqrt_approx(qi * qi + ui * ui + vi * vi) * a.invM;
-        const bool f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
-                       !(r_im <= a.gamma);
+        float tau, r_re, r_im;
+        bool f;
+        if constexpr (MIXED) {
+            f = finish_mixed(a, S1, S2, qr, ur, vr, qi, ui, vi, tau, r_re, r_im);
+        } else {
+            // Table 1 groups 6-7 / Sec. 2.1 and Table 2 groups 5-6 / Sec. 2.2
+            tau = a.c0 * (a.fM * S2 * rcp_approx(S1 * S1 + a.eps) - 1.0f);
+            r_re = sqrt_approx(qr * qr + ur * ur + vr * vr) * a.invM;
+            r_im = sqrt_approx(qi * qi + ui * ui + vi * vi) * a.invM;
+            f = !(tau >= a.s_low && tau <= a.s_high) || !(r_re <= a.gamma) ||
+                !(r_im <= a.gamma);
+        }
         if (ok && st_lead && rfi_in(st_row + i, 4, a.stats, stats_ext, a.err) &&
             rfi_in(st_row + i + 2 * plane, 4, a.stats, stats_ext, a.err)) {
             st_row[i] = tau;
@@ -228,20 +242,20 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
     }
 }
 
-template <int DT, int SPU, int P, int CH>
+template <int DT, int SPU, int P, int CH, bool MIXED = false>
 __global__ void __launch_bounds__(512, 1) k_wpar(const __grid_constant__ StreamArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     overlap_prologue<DT, P>(a, group);
-    process_group_wp<DT, SPU, P, CH>(a, group);
+    process_group_wp<DT, SPU, P, CH, MIXED>(a, group);
 }
 
 // The persistent batch over window-parallel contexts (same task loop as k_batch).
-template <int DT, int SPU, int P, int CH>
+template <int DT, int SPU, int P, int CH, bool MIXED = false>
 __global__ void __launch_bounds__(512, 1) k_batch_wp(const __grid_constant__ BatchArgs b) {
     run_batch_tasks(b, [](const StreamArgs &a, long long group) {
-        process_group_wp<DT, SPU, P, CH>(a, group);
+        process_group_wp<DT, SPU, P, CH, MIXED>(a, group);
     });
 }
 

@@ -12,15 +12,19 @@ from parity import expand_window_flags, rel_err, run_gpu, to_device_rows
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("split", [0, 1], ids=["one_lane", "window_parallel"])
 @pytest.mark.parametrize("dtype,M,K", [("f32", 16, 64), ("f16", 16, 32), ("f32", 20, 40),
                                        ("f16", 8, 48), ("f16", 5, 10), ("f32", 64, 128)])
-def test_mixed_kernel_matches_emulation(dtype, M, K):
+def test_mixed_kernel_matches_emulation(dtype, M, K, split):
+    """One lane per row, or window-parallel lanes (each window still summed in one lane
+    in the tables' order): the same statistics and flags bit for bit."""
     N, C = 6, 8
     T = M * 12
     thr = default_thresholds(M)
     data = synth.tiny_block(seed=7, stations=N, channels=C, T=T, duty=0.08)["vis"]
-    st = RfiStream(N, C, M, K, thr, dtype, precision=1)
-    assert st.options["lanes_per_row"] == 1 and st.options["precision"] == 1
+    opts = dict(lane_split=1, lanes_per_row=2) if split else {}
+    st = RfiStream(N, C, M, K, thr, dtype, precision=1, **opts)
+    assert st.options["lanes_per_row"] == (2 if split else 1) and st.options["precision"] == 1
     g = run_gpu(st, to_device_rows(data, dtype))
     rows = data.reshape(-1, T, 8)
     if dtype == "f16":
