@@ -178,9 +178,10 @@ typedef enum {
  *                  of K samples (K a multiple of H) that closed.  T must be a multiple of
  *                  H.  Needs time-only windows, float32 arithmetic, the direct loader,
  *                  the 128-register budget, plain stores, no Kahan summation and
- *                  lanes_per_row <= 4; excludes partial_windows and adaptive; single-
- *                  stream calls only (a batch rejects the context).  Any split of a
- *                  stream at multiples of H gives bit-identical results.
+ *                  lanes_per_row <= 4; excludes partial_windows and adaptive; a batch
+ *                  takes it with contexts of the same hop and shape.  Any split of a
+ *                  stream at multiples of H gives bit-identical results, alone or in a
+ *                  batch.
  *   lane_split     0 = the lanes_per_row lanes of a row split every window's load
  *                  units (default).  1 = they take whole windows in turn (lane j the
  *                  stream's windows g with g mod P = j): no butterfly over the row's

@@ -69,13 +69,13 @@ const void *find_tma(int dt, int spu, int P, int ch, int kahan, int lb) {
     return nullptr;
 }
 
-const void *find_sw(int dt, int spu, int P, int ch, int L) {
+const SwInstance *find_sw(int dt, int spu, int P, int ch, int L) {
     const SwTable tabs[] = {sw_instances_f32(), sw_instances_f16()};
     for (const SwTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const SwInstance &in = t.items[i];
             if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.L == L)
-                return in.fn;
+                return &in;
         }
     return nullptr;
 }
@@ -315,12 +315,13 @@ int choose_shape(rfi_ctx *c, int P_req) {
     if (c->sw) {
         // overlapping windows: their own kernels, single-stream calls only
         c->ch = c->S % 4 == 0 ? 4 : (c->S % 2 == 0 ? 2 : 1);
-        c->sw_fn = find_sw(dt, spu, P, c->ch, c->M / c->H);
+        const SwInstance *si = find_sw(dt, spu, P, c->ch, c->M / c->H);
         c->inst = nullptr;
-        c->batch_fn = nullptr;
-        if (!c->sw_fn)
+        if (!si)
             return fail(RFI_EUNSUPPORTED, "no overlapping-window kernel for lanes_per_row=%d "
                                           "(1, 2 or 4)", P);
+        c->sw_fn = si->fn;
+        c->batch_fn = si->batch_fn;
         return RFI_OK;
     }
     // the plain 128-register kernels exist with and without the prefetch code; the
@@ -404,6 +405,14 @@ long long outputs_for_c(const rfi_ctx *c, int T) {
     return (c->n_seen + T) / c->K - c->n_seen / c->K;
 }
 
+// Overlapping-window state: the pending hop's totals [R][8] and the lanes' averaging
+// sums [R][P][8], then the last window's flag [R].
+size_t sw_tot_floats(const rfi_ctx *c) { return (size_t)c->R * 8; }
+size_t sw_pend_floats(const rfi_ctx *c) { return (size_t)c->R * c->P * 8; }
+size_t sw_bytes(const rfi_ctx *c) {
+    return c->sw ? sizeof(float) * (sw_tot_floats(c) + sw_pend_floats(c)) + 4 * (size_t)c->R : 0;
+}
+
 StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, float *avg,
                      float *weight, float *stats, long long r0, long long nrows) {
     StreamArgs a = {};
@@ -422,6 +431,14 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.k_sigma = (float)c->adp.k_sigma;
     a.n_warm = (float)c->adp.n_warm;
     a.ovl_bytes = c->ovl;
+    a.hop = c->H;
+    if (c->sw) {
+        a.warm = (int)std::min<long long>(c->n_seen / c->H, c->M / c->H - 1);
+        a.sw_tot = c->sw_buf + r0 * 8;
+        a.sw_pend = c->sw_buf + sw_tot_floats(c) + r0 * c->P * 8;
+        a.sw_hist =
+            reinterpret_cast<uint32_t *>(c->sw_buf + sw_tot_floats(c) + sw_pend_floats(c)) + r0;
+    }
     a.phase = phase_of(c);
     a.R = nrows;
     a.stats_plane = (c->R / c->F) * nwin;
@@ -529,31 +546,13 @@ bool capturing(cudaStream_t st) {
     return cs != cudaStreamCaptureStatusNone;
 }
 
-// Overlapping-window state of rows [r0, ...) (the pending segment and window flags).
-size_t sw_tot_floats(const rfi_ctx *c) { return (size_t)c->R * 8; }
-size_t sw_pend_floats(const rfi_ctx *c) { return (size_t)c->R * c->P * 8; }
-size_t sw_bytes(const rfi_ctx *c) {
-    return c->sw ? sizeof(float) * (sw_tot_floats(c) + sw_pend_floats(c)) + 4 * (size_t)c->R : 0;
-}
-
-int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st, long long r0 = 0) {
+int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
     if (a.R <= 0) return RFI_OK;
     const int RW = 32 / c->P;
     const long long groups = (a.R + RW - 1) / RW;
     const long long blocks = (groups + c->wpb - 1) / c->wpb;
     void *args[] = {const_cast<StreamArgs *>(&a)};
-    SlideArgs g;
     const void *fn = c->sw ? c->sw_fn : (c->wp ? c->wp_fn : (c->inst ? c->inst->block_fn : nullptr));
-    if (c->sw) {
-        g.s = a;
-        g.H = c->H;
-        g.warm = (int)std::min<long long>(c->n_seen / c->H, c->M / c->H - 1);
-        g.tot = c->sw_buf + r0 * 8;
-        g.pend = c->sw_buf + sw_tot_floats(c) + r0 * c->P * 8;
-        g.hist = reinterpret_cast<uint32_t *>(c->sw_buf + sw_tot_floats(c) + sw_pend_floats(c)) +
-                 r0;
-        args[0] = &g;
-    }
     cudaError_t e;
     if (c->loader == 1) {
         e = allow_smem(c->tma_fn, c->tma_smem);
@@ -624,9 +623,6 @@ int build_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *
         if ((rc = check_ctx(ctxs[i]))) return rc;
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return fail(RFI_EINVAL, "context %d appears twice", i);
-        if (ctxs[i]->sw)
-            return fail(RFI_EUNSUPPORTED, "context %d has overlapping windows (single-stream "
-                                          "calls only)", i);
         if (!ctxs[i]->batch_fn || ctxs[i]->batch_fn != ctxs[0]->batch_fn ||
             ctxs[i]->device != ctxs[0]->device)
             return fail(RFI_EINVAL, "context %d differs in dtype, M or launch shape", i);
@@ -1031,7 +1027,7 @@ int rfi_process_block_host(rfi_ctx *ctx, const void *vis, int T, uint32_t *flags
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "host path copy-in");
         StreamArgs a = make_args(ctx, ctx->h_vis, T, ctx->h_flags, ctx->h_avg, ctx->h_weight,
                                  ctx->h_stats, r0, nr);
-        if ((rc = launch_block(ctx, a, ctx->s_run, r0))) return rc;
+        if ((rc = launch_block(ctx, a, ctx->s_run))) return rc;
         e = cudaEventRecord(ctx->ev_run[k], ctx->s_run);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_run[k], 0);
         if (e == cudaSuccess && nwin > 0)

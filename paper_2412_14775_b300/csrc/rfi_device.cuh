@@ -69,6 +69,13 @@ struct StreamArgs {
     // launch overlap: bytes at the start of every row requested into L2 before the
     // kernel waits for the grid it depends on (0 = none)
     int ovl_bytes;
+    // overlapping windows (rfi_sliding.cuh): a window of M samples every hop samples;
+    // warm = min(hops of the stream before this launch, M/hop - 1); the carried totals
+    // [R][8] and the lane's averaging sums [R][P][8] of the pending hop, and the last
+    // window's flag [R]
+    int hop, warm;
+    float *sw_tot, *sw_pend;
+    uint32_t *sw_hist;
 };
 
 struct BatchArgs {

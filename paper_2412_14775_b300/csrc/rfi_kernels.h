@@ -50,6 +50,7 @@ TmaTable tma_instances_f16();
 struct SwInstance {
     int dt, spu, P, ch, L;
     const void *fn;         // k_slide<...>
+    const void *batch_fn;   // k_batch_sw<...>
 };
 struct SwTable {
     const SwInstance *items;
@@ -171,7 +172,9 @@ WpTable wp_instances_f16();   // rfi_inst_wp_f16.cu
     RFI_TMA_CH(DT, SPU, P, 0, 0), RFI_TMA_CH(DT, SPU, P, 1, 0), RFI_TMA_CH(DT, SPU, P, 0, 1), \
         RFI_TMA_CH(DT, SPU, P, 0, 2)
 
-#define RFI_SW(DT, SPU, P, CH, L) {DT, SPU, P, CH, L, (const void *)&rfi::k_slide<DT, SPU, P, CH, L>}
+#define RFI_SW(DT, SPU, P, CH, L)                                                           \
+    {DT, SPU, P, CH, L, (const void *)&rfi::k_slide<DT, SPU, P, CH, L>,                     \
+     (const void *)&rfi::k_batch_sw<DT, SPU, P, CH, L>}
 // Chunks of 1, 2 or 4 units (5 would spill with the two pending-segment rings).
 #define RFI_SW_CH(DT, SPU, P, L)                                                            \
     RFI_SW(DT, SPU, P, 1, L), RFI_SW(DT, SPU, P, 2, L), RFI_SW(DT, SPU, P, 4, L)

@@ -15,39 +15,26 @@
 // totals, oldest first.  The totals of the L-1 segments before the current one, and the
 // lane's averaging sums of those segments (their flags are not known yet), live in
 // registers and, at the end of a block, in the context's carry, so any split of a
-// stream at multiples of H gives bit-identical results.
+// stream at multiples of H gives bit-identical results, alone or in a batch.
 #pragma once
 #include "rfi_device.cuh"
 
 namespace rfi {
 
-// One stream's launch with overlapping windows.
-struct SlideArgs {
-    StreamArgs s;       // M = window length (W), T, K, thresholds, outputs, bin carry;
-                        // nwin = windows completed by this launch, bin_pos0 = final
-                        // samples of the open bin before this launch
-    int H;              // hop: a window starts every H samples
-    int warm;           // min(segments of the stream before this launch, L - 1)
-    float *tot;         // [R][L-1][8]: statistic totals of the last L-1 segments
-    float *pend;        // [R][P][L-1][8]: the lane's averaging sums of those segments
-    uint32_t *hist;     // [R]: flags of the last L-1 windows, bit k = k+1-th most recent
-};
-
 template <int DT, int SPU, int P, int CH, int L>
-__device__ __forceinline__ void process_group_sw(const SlideArgs &g, long long group) {
+__device__ __forceinline__ void process_group_sw(const StreamArgs &a, long long group) {
     static_assert(L >= 2, "overlapping windows need at least two windows per sample");
     constexpr int LM = L - 1;
     constexpr int RW = 32 / P;
     constexpr int SB = (DT == DT_F32) ? 32 : 16;
     constexpr int UB = SB * SPU;
-    const StreamArgs &a = g.s;
     const int lane = threadIdx.x & 31;
     const int j = lane & (P - 1);
     const long long row = group * RW + lane / P;
     const bool active = row < a.R;
     const long long rowc = active ? row : a.R - 1;
     const bool lead = active && j == 0;
-    const int H = g.H;
+    const int H = a.hop;
     const int S = H / (P * SPU);                    // load units per lane per segment
     const char *rp = static_cast<const char *>(a.vis) + rowc * (long long)a.T * SB;
     const long long vis_ext = a.R * (long long)a.T * SB;
@@ -63,11 +50,11 @@ __device__ __forceinline__ void process_group_sw(const SlideArgs &g, long long g
     float rt[LM][8], ra[LM][8];
     uint32_t hist = 0;
     {
-        const float *tp = g.tot + rowc * (LM * 8);
-        const float *pp = g.pend + (rowc * P + j) * (LM * 8);
-        const bool ok = rfi_in(tp, LM * 32, g.tot, tot_ext, a.err) &&
-                        rfi_in(pp, LM * 32, g.pend, pend_ext, a.err) &&
-                        rfi_in(g.hist + rowc, 4, g.hist, hist_ext, a.err);
+        const float *tp = a.sw_tot + rowc * (LM * 8);
+        const float *pp = a.sw_pend + (rowc * P + j) * (LM * 8);
+        const bool ok = rfi_in(tp, LM * 32, a.sw_tot, tot_ext, a.err) &&
+                        rfi_in(pp, LM * 32, a.sw_pend, pend_ext, a.err) &&
+                        rfi_in(a.sw_hist + rowc, 4, a.sw_hist, hist_ext, a.err);
 #pragma unroll
         for (int k = 0; k < LM; ++k)
 #pragma unroll
@@ -75,7 +62,7 @@ __device__ __forceinline__ void process_group_sw(const SlideArgs &g, long long g
                 rt[k][c] = ok ? tp[k * 8 + c] : 0.f;
                 ra[k][c] = ok ? pp[k * 8 + c] : 0.f;
             }
-        hist = ok ? g.hist[rowc] : 0u;
+        hist = ok ? a.sw_hist[rowc] : 0u;
     }
     float acc[8];
     float cnt = 0.f;
@@ -103,7 +90,7 @@ __device__ __forceinline__ void process_group_sw(const SlideArgs &g, long long g
     uint32_t fword = 0;
     int fbit = 0, fwi = 0;
     const int nbits = a.nwin * H;
-    int seen = g.warm;                              // segments before, up to L - 1
+    int seen = a.warm;                              // segments before, up to L - 1
     int w = 0;                                      // windows completed in this launch
 
     const float2 eps2 = make_float2(a.eps, a.eps);
@@ -254,22 +241,22 @@ __device__ __forceinline__ void process_group_sw(const SlideArgs &g, long long g
     }
     // carry for the next block
     if (active) {
-        float *tp = g.tot + row * (LM * 8);
-        float *pp = g.pend + (row * P + j) * (LM * 8);
-        if (j == 0 && rfi_in(tp, LM * 32, g.tot, tot_ext, a.err)) {
+        float *tp = a.sw_tot + row * (LM * 8);
+        float *pp = a.sw_pend + (row * P + j) * (LM * 8);
+        if (j == 0 && rfi_in(tp, LM * 32, a.sw_tot, tot_ext, a.err)) {
 #pragma unroll
             for (int k = 0; k < LM; ++k)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) tp[k * 8 + c] = rt[k][c];
         }
-        if (rfi_in(pp, LM * 32, g.pend, pend_ext, a.err)) {
+        if (rfi_in(pp, LM * 32, a.sw_pend, pend_ext, a.err)) {
 #pragma unroll
             for (int k = 0; k < LM; ++k)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) pp[k * 8 + c] = ra[k][c];
         }
-        if (j == 0 && rfi_in(g.hist + row, 4, g.hist, hist_ext, a.err))
-            g.hist[row] = hist & ((1u << LM) - 1u);
+        if (j == 0 && rfi_in(a.sw_hist + row, 4, a.sw_hist, hist_ext, a.err))
+            a.sw_hist[row] = hist & ((1u << LM) - 1u);
         if (wib != 0 && rfi_in(a.carry + (row * P + j) * 9, 36, a.carry, carry_ext, a.err)) {
             float *cp = a.carry + (row * P + j) * 9;
 #pragma unroll
@@ -280,12 +267,20 @@ __device__ __forceinline__ void process_group_sw(const SlideArgs &g, long long g
 }
 
 template <int DT, int SPU, int P, int CH, int L>
-__global__ void __launch_bounds__(512, 1) k_slide(const __grid_constant__ SlideArgs g) {
+__global__ void __launch_bounds__(512, 1) k_slide(const __grid_constant__ StreamArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (group * (32 / P) >= g.s.R) return;     // whole warp leaves together
-    overlap_prologue<DT, P>(g.s, group);
-    process_group_sw<DT, SPU, P, CH, L>(g, group);
+    if (group * (32 / P) >= a.R) return;     // whole warp leaves together
+    overlap_prologue<DT, P>(a, group);
+    process_group_sw<DT, SPU, P, CH, L>(a, group);
+}
+
+// The persistent batch over overlapping-window contexts (same task loop as k_batch).
+template <int DT, int SPU, int P, int CH, int L>
+__global__ void __launch_bounds__(512, 1) k_batch_sw(const __grid_constant__ BatchArgs b) {
+    run_batch_tasks(b, [](const StreamArgs &a, long long group) {
+        process_group_sw<DT, SPU, P, CH, L>(a, group);
+    });
 }
 
 }  // namespace rfi

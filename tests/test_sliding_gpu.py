@@ -180,7 +180,7 @@ def test_sliding_option_checks():
     b = RfiStream(4, 4, 16, 32, thr, "f32")
     with pytest.raises(RfiError):                   # T must be a multiple of H
         a.process(torch.zeros((a.R, 12, 4, 2), device="cuda"))
-    with pytest.raises(RfiError):                   # single-stream calls only
+    with pytest.raises(RfiError):                   # a batch does not mix kinds
         z = [s.alloc_outputs(32) for s in (a, b)]
         v = torch.zeros((a.R, 32, 4, 2), device="cuda")
         binding.rfi_process_batch([a.ctx, b.ctx], [v, v], [32, 32], [o["flags"] for o in z],
@@ -244,3 +244,35 @@ def test_sliding_non_finite_samples(dtype):
             assert g["bits"][r, lo:hi].all(), (r, t)
     assert np.isfinite(g["avg"]).all() and np.isfinite(g["weight"]).all()
     st.close()
+
+
+def test_sliding_batch_bit_identical():
+    """Uneven overlapping-window streams in one persistent launch, and from a CUDA graph,
+    give each stream's single-launch results bit for bit, block after block (the pending
+    hop carried between blocks either way)."""
+    M, H, K, T = 16, 8, 48, 72
+    thr = default_thresholds(M)
+    geo = [(5, 8), (9, 4), (3, 12), (7, 8)]
+    data = [synth.tiny_block(seed=89 + i, stations=n, channels=c, T=3 * T, duty=0.08)["vis"]
+            for i, (n, c) in enumerate(geo)]
+    solo = [RfiStream(n, c, M, K, thr, "f32", window_hop=H, lanes_per_row=2) for n, c in geo]
+    bat = [RfiStream(n, c, M, K, thr, "f32", window_hop=H, lanes_per_row=2) for n, c in geo]
+    g = binding.rfi_batch_graph_create([s.ctx for s in bat[2:]], [T, T])
+    for k in range(3):
+        vis = [to_device_rows(d[:, :, k * T:(k + 1) * T], "f32") for d in data]
+        outs = [s.alloc_outputs(T) for s in bat]
+        binding.rfi_process_batch([s.ctx for s in bat[:2]], vis[:2], [T, T],
+                                  [o["flags"] for o in outs[:2]], [o["avg"] for o in outs[:2]],
+                                  [o["weight"] for o in outs[:2]], [o["stats"] for o in outs[:2]])
+        binding.rfi_batch_graph_launch(g, vis[2:], [o["flags"] for o in outs[2:]],
+                                       [o["avg"] for o in outs[2:]],
+                                       [o["weight"] for o in outs[2:]],
+                                       [o["stats"] for o in outs[2:]])
+        exp = [s.process(v) for s, v in zip(solo, vis)]
+        torch.cuda.synchronize()
+        for e, o in zip(exp, outs):
+            for key in ("flags", "avg", "weight", "stats"):
+                assert torch.equal(e[key], o[key]), (k, key)
+    binding.rfi_batch_graph_destroy(g)
+    for s in solo + bat:
+        s.close()
