@@ -39,13 +39,14 @@ class _Stream:
         self.done = 0
         # outputs: a block completes between floor(T/K) and floor(T/K) + 1 averaging
         # bins and, with partial windows, between floor(T/M) and floor((T + M - 1)/M)
-        # windows; the storage is sized for the larger counts and viewed at this
-        # block's exact ones
+        # windows (with overlapping windows at most T/H, each adding H flag bits); the
+        # storage is sized for the larger counts and viewed at this block's exact ones
         import torch
         R, F = self.st.R, self.st.F
+        B = self.st.bits_per_window
         self.n_out_max = T // K + 1
-        self.n_win_max = (T + M - 1) // M
-        words_max = (self.n_win_max * M + 31) // 32
+        self.n_win_max = (T + M - 1) // B
+        words_max = (self.n_win_max * B + 31) // 32
         dev = blocks[0].device
         self.out_pool = []
         for _ in range(2):
@@ -66,7 +67,7 @@ class _Stream:
         R, F, M = self.st.R, self.st.F, self.st.M
         n = self.st.outputs_for(self.T)
         nw = self.st.windows_for(self.T)[0]
-        words = (nw * M + 31) // 32
+        words = (nw * self.st.bits_per_window + 31) // 32
         return dict(flags=o["flags_store"][:R * words].view(R, words),
                     stats=o["stats_store"][:3 * (R // F) * nw].view(3, R // F, nw),
                     avg=o["avg_store"][:R * n * 8].view(R, n, 4, 2),

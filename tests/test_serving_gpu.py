@@ -12,12 +12,16 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("options,T", [({}, 48), ({"adaptive": 1}, 48),
-                                       ({"partial_windows": 1}, 40)],
-                         ids=["fixed", "online_thresholds", "partial_windows"])
+                                       ({"partial_windows": 1}, 40),
+                                       ({"window_hop": 8, "lanes_per_row": 2}, 40),
+                                       ({"lane_split": 1, "lanes_per_row": 2}, 48)],
+                         ids=["fixed", "online_thresholds", "partial_windows",
+                              "overlapping_windows", "window_parallel"])
 def test_serving_mix_equals_solo(options, T):
     """With online thresholds the per-stream threshold state lives on the device too and
     advances with every block; with partial windows blocks of 40 samples leave windows
-    of 16 open between blocks.  In the mix exactly as alone."""
+    of 16 open between blocks; with overlapping windows the pending half-window waits on
+    the device between blocks.  In the mix exactly as alone."""
     M, K = 16, 32                 # bins of 32 straddle the blocks: the carry is exercised
     cfgs = [dict(stations=n, channels=c, rho=r) for n, c, r in
             ((5, 4, 3.0), (9, 8, 2.0), (7, 16, 4.0), (12, 4, 1.5), (4, 8, 3.5), (8, 16, 2.5))]
@@ -37,9 +41,9 @@ def test_serving_mix_equals_solo(options, T):
     for i, cfg in enumerate(cfgs):
         got = sorted(loop.outputs[i], key=lambda t: t[0])
         assert [k for k, _ in got] == list(range(len(got)))
-        solo = RfiStream(cfg["stations"], cfg["channels"], M, K, thr, "f16",
-                         lanes_per_row=opts["lanes_per_row"],
-                         warps_per_block=opts["warps_per_block"], **options)
+        kw = dict(lanes_per_row=opts["lanes_per_row"], warps_per_block=opts["warps_per_block"])
+        kw.update(options)
+        solo = RfiStream(cfg["stations"], cfg["channels"], M, K, thr, "f16", **kw)
         if options.get("adaptive"):
             solo.set_adaptation(alpha=1.0 / 16, k_sigma=3.0, n_warm=4)
         for k, mixed in got:
