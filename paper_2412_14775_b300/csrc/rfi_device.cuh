@@ -180,10 +180,10 @@ __device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
         : "l"(p));
 }
 // The same with L2 evict-first priority: the input is read once, so its lines may leave
-// L2 first.  Taken by the binary16 kernels without the L2 prefetch code (measured on the
-// LOFAR-scale block: M = 16 98.6 -> 93.8 us, M = 32 89.9 -> 84.5 us, 10x2 footprints
-// 115.3 -> 108.7 us; kernels that prefetch ahead into L2, complex64 and the batch
-// kernel gained nothing or lost).  16-byte units keep the plain load.
+// L2 first.  Taken by the kernels without the L2 prefetch code (measured on the
+// LOFAR-scale block: complex64 M = 16 170.5 -> 158.7 us, binary16 M = 16 98.6 -> 93.8 us,
+// binary16 M = 32 89.9 -> 84.5 us, footprints 2.5-6 %; kernels that prefetch ahead into
+// L2 gained nothing or lost).  16-byte units keep the plain load.
 __device__ __forceinline__ void load_unit_ef(const char *p, Unit<32> &u) {
     asm("ld.global.nc.L1::no_allocate.L2::evict_first.L2::256B.v8.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -548,7 +548,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         for (int c = 0; c < CH; ++c) {
             const char *p = cp_ + (long long)q * CHB + c * (P * UB);
             if (rfi_in(p, UB, a.vis, vis_ext, a.err)) {
-                if constexpr (DT == DT_F16 && !BAT && !PFT) load_unit_ef(p, u[c]);
+                if constexpr (!BAT && !PFT) load_unit_ef(p, u[c]);
                 else load_unit(p, u[c]);
             } else {
                 u[c] = Unit<UB>{};

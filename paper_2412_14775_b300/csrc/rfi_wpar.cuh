@@ -90,8 +90,7 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
         for (int e = 0; e < CH; ++e) {
             const char *p = p0 + e * UB;
             if (ok && rfi_in(p, UB, a.vis, vis_ext, a.err)) {
-                if constexpr (DT == DT_F16) load_unit_ef(p, u[e]);    // read once
-                else load_unit(p, u[e]);
+                load_unit_ef(p, u[e]);                                 // read once
             } else {
                 u[e] = Unit<UB>{};
             }
