@@ -183,9 +183,11 @@ __device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
 // L2 first.  Taken by the kernels without the L2 prefetch code (measured on the
 // LOFAR-scale block: complex64 M = 16 170.5 -> 158.7 us, binary16 M = 16 98.6 -> 93.8 us,
 // binary16 M = 32 89.9 -> 84.5 us, footprints 2.5-6 %; kernels that prefetch ahead into
-// L2 gained nothing or lost).  16-byte units keep the plain load.
+// L2 gained nothing or lost).  With evict-first, 128-byte L2 fills measured 1.4 % faster
+// than 256-byte ones for binary16 M = 16 (the same elsewhere).  16-byte units keep the
+// plain load.
 __device__ __forceinline__ void load_unit_ef(const char *p, Unit<32> &u) {
-    asm("ld.global.nc.L1::no_allocate.L2::evict_first.L2::256B.v8.b32 "
+    asm("ld.global.nc.L1::no_allocate.L2::evict_first.L2::128B.v8.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3]),
           "=r"(u.r[4]), "=r"(u.r[5]), "=r"(u.r[6]), "=r"(u.r[7])
