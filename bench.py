@@ -420,10 +420,11 @@ def variant_extras(vis32, opts, torch, cs, peak, steps=300, warmup=10):
         pw.process(v250, out=pw.alloc_outputs(250), stream=cs)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    wins = []
+    wins, ring = [], []
     e0.record(cs)
     for _ in range(steps):
         out = pw.alloc_outputs(250)
+        ring = (ring + [out])[-4:]          # a ring of 4 live output sets, as elsewhere
         wins.append(out["stats"].shape[-1])
         pw.process(v250, out=out, stream=cs)
     e1.record(cs)
@@ -552,15 +553,25 @@ def serving_extras(seconds, options, torch):
 
 
 def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler_index=None,
-                serial_steps=100):
+                serial_steps=100, n_out_sets=4):
     """Warm up, then time `steps` back-to-back launches with CUDA events on the launching
     stream around the whole run; returns the mean launch period (device time of the
     flagging kernel in a stream of calls, launch overlap included), the run's total and
-    the clock record.  Then `serial_steps` launches with an event pair around each one
-    (which keeps consecutive launches from overlapping): their mean duration, reported
-    beside it."""
-    for _ in range(warmup):
-        stream_obj.process(vis, out=out, stream=cuda_stream)
+    the clock record.  Step i reads vis[i % len(vis)] (vis: one tensor or a list) and
+    writes the (i % n_out_sets)-th of n_out_sets output sets, `out` and copies of it: a
+    ring of output buffers, as a pipeline keeps them (one set reused every step would let
+    the outputs stay in L2 and never reach DRAM).  Then `serial_steps` launches with an
+    event pair around each one (which keeps consecutive launches from overlapping): their
+    mean duration, reported beside it."""
+    vis_l = list(vis) if isinstance(vis, (list, tuple)) else [vis]
+    outs = [out] + [{k: torch.empty_like(x) for k, x in out.items()}
+                    for _ in range(n_out_sets - 1)]
+
+    def step(i):
+        stream_obj.process(vis_l[i % len(vis_l)], out=outs[i % len(outs)], stream=cuda_stream)
+
+    for i in range(warmup):
+        step(i)
     torch.cuda.synchronize()
     sampler = ClockSampler(sampler_index) if sampler_index is not None else None
     if sampler:
@@ -568,8 +579,8 @@ def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler
     t_all0 = torch.cuda.Event(enable_timing=True)
     t_all1 = torch.cuda.Event(enable_timing=True)
     t_all0.record(cuda_stream)
-    for _ in range(steps):
-        stream_obj.process(vis, out=out, stream=cuda_stream)
+    for i in range(steps):
+        step(i)
     t_all1.record(cuda_stream)
     torch.cuda.synchronize()
     if sampler:
@@ -577,11 +588,16 @@ def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler
     total = t_all0.elapsed_time(t_all1) * 1e-3
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(min(serial_steps, steps))]
-    for a, b in ev:
+    for i, (a, b) in enumerate(ev):
         a.record(cuda_stream)
-        stream_obj.process(vis, out=out, stream=cuda_stream)
+        step(i)
         b.record(cuda_stream)
     torch.cuda.synchronize()
+    # leave the results of the last launch in `out` for the caller
+    last = outs[(len(ev) - 1 if ev else steps - 1) % len(outs)]
+    if last is not out:
+        for k in out:
+            out[k].copy_(last[k])
     serial = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in ev) if ev else None
     return total / steps, total, serial, (sampler.summary() if sampler else None)
 
@@ -650,9 +666,12 @@ def main():
 
     if ws > 1:
         dist.barrier()
-    kern, total, kern_serial, clocks = time_kernel(st, vis_main, out, args.steps, args.warmup,
+    # two input blocks in turn (each larger than L2) and a ring of four output sets
+    kern, total, kern_serial, clocks = time_kernel(st, [vis_main, vis_main.clone()], out,
+                                                   args.steps, args.warmup,
                                                    torch, cs, sampler_index=local)
     samples = R * T
+    out_bytes = sum(x.numel() * x.element_size() for x in out.values())
     # every rank processes its own block (weak scaling): total samples of all ranks over
     # the slowest rank's time
     _, total, value = aggregate(samples * args.steps, total)
@@ -759,7 +778,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": main_dt,
             "data": "synthetic",
             "config": dict(WORKLOAD, dtype="complex64" if main_dt == "f32" else "complex32 (binary16)",
-                           l2=f"inputs {R * T * sbytes / 1e9:.2f} GB > 126 MB L2, no flush",
+                           l2=f"two input blocks of {R * T * sbytes / 1e9:.2f} GB (> 126 MB L2) in "
+                              f"turn, outputs into a ring of 4 sets ({4 * out_bytes / 1e6:.0f} MB), "
+                              "no flush",
                            options={k: st.options[k] for k in
                                     ("lanes_per_row", "warps_per_block", "prefetch_bytes",
                                      "prefetch_groups")}),

@@ -34,22 +34,24 @@ def candidates_p(M, dtype):
 
 def time_options(stations, channels, M, K, thr, dtype, vis, reps=30, warmup=5, **opts):
     """Launch period (s) of one option set on `vis` (device tensor): launches back to
-    back, as a stream of blocks runs them (consecutive launches may overlap), events
-    around each of three runs of reps/3 launches, the median run."""
+    back, as a stream of blocks runs them (consecutive launches may overlap), each into
+    the next of four output sets (a ring of output buffers, as a pipeline keeps them;
+    one set reused every launch would let the outputs stay in L2), events around each
+    of three runs of reps/3 launches, the median run."""
     import torch
     st = RfiStream(stations, channels, M, K, thr, dtype, **opts)
     T = vis.shape[-3]
-    out = st.alloc_outputs(T, device=vis.device)
+    outs = [st.alloc_outputs(T, device=vis.device) for _ in range(4)]
     n = max(1, reps // 3)
     try:
-        for _ in range(warmup):
-            st.process(vis, out=out)
+        for i in range(warmup):
+            st.process(vis, out=outs[i % 4])
         runs = []
         for _ in range(3):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            for _ in range(n):
-                st.process(vis, out=out)
+            for i in range(n):
+                st.process(vis, out=outs[i % 4])
             b.record()
             runs.append((a, b))
         torch.cuda.synchronize()
