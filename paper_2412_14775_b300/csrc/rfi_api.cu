@@ -325,9 +325,9 @@ int choose_shape(rfi_ctx *c, int P_req) {
         return RFI_OK;
     }
     // the plain 128-register kernels exist with and without the prefetch code; the
-    // buffered-store and online-threshold kernels have none, the other kinds hold it
+    // other kinds always hold it
     const bool plain = c->lb == 0 && !c->mixed && !c->vs && !c->pw && !c->ad;
-    const int pf = plain ? (c->pf_groups > 0 ? 1 : 0) : ((c->vs || c->ad) ? 0 : 1);
+    const int pf = plain ? (c->pf_groups > 0 ? 1 : 0) : 1;
     c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs, c->pw, c->ad,
                             pf);
     if (c->inst) {

@@ -179,21 +179,6 @@ __device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
         : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3])
         : "l"(p));
 }
-// The same with L2 evict-first priority: the input is read once, so its lines may leave
-// L2 first.  Taken by the kernels without the L2 prefetch code (measured on the
-// LOFAR-scale block: complex64 M = 16 170.5 -> 158.7 us, binary16 M = 16 98.6 -> 93.8 us,
-// binary16 M = 32 89.9 -> 84.5 us, footprints 2.5-6 %; kernels that prefetch ahead into
-// L2 gained nothing or lost).  With evict-first, 128-byte L2 fills measured 1.4 % faster
-// than 256-byte ones for binary16 M = 16 (the same elsewhere).  16-byte units keep the
-// plain load.
-__device__ __forceinline__ void load_unit_ef(const char *p, Unit<32> &u) {
-    asm("ld.global.nc.L1::no_allocate.L2::evict_first.L2::128B.v8.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3]),
-          "=r"(u.r[4]), "=r"(u.r[5]), "=r"(u.r[6]), "=r"(u.r[7])
-        : "l"(p));
-}
-__device__ __forceinline__ void load_unit_ef(const char *p, Unit<16> &u) { load_unit(p, u); }
 
 // ---- debug-bounds build (-DRFI_DEBUG_BOUNDS) -----------------------------------
 // Every global access of the kernels is checked against the extent that the launch's
@@ -549,12 +534,8 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             const char *p = cp_ + (long long)q * CHB + c * (P * UB);
-            if (rfi_in(p, UB, a.vis, vis_ext, a.err)) {
-                if constexpr (!BAT && !PFT) load_unit_ef(p, u[c]);
-                else load_unit(p, u[c]);
-            } else {
-                u[c] = Unit<UB>{};
-            }
+            if (rfi_in(p, UB, a.vis, vis_ext, a.err)) load_unit(p, u[c]);
+            else u[c] = Unit<UB>{};
         }
     };
     WinAcc A;

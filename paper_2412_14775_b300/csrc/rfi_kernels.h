@@ -75,9 +75,8 @@ WpTable wp_instances_f16();   // rfi_inst_wp_f16.cu
 }  // namespace rfi
 
 // Field `pf`: 1 = the kernel holds the L2 prefetch code (used when a launch asks for
-// prefetch), 0 = it does not (its loads then carry the L2 evict-first hint).  The plain
-// 128-register kernels exist both ways; the buffered-store and online-threshold kernels
-// have no prefetch code, the other kinds hold it.
+// prefetch), 0 = it does not.  The plain 128-register kernels exist both ways; every
+// other kind holds it.
 // Entries for one (DT, SPU, P, CH, K): LB = 0 without prefetch code, and the batch
 // kernel of every plain context (it holds the prefetch code, taken when the contexts
 // ask for it; measured faster than the batch kernel without it, 514 against 552 us on
@@ -113,13 +112,11 @@ WpTable wp_instances_f16();   // rfi_inst_wp_f16.cu
     {DT, SPU, 1, CH, 0, 0, 1, 0, 0, 0, 1,                                                   \
      (const void *)&rfi::k_block<DT, SPU, 1, CH, false, 0, true, false, false, false, true>, \
      (const void *)&rfi::k_batch<DT, SPU, 1, CH, false, true, false, false, true>}
-// Buffered 16-byte output stores (for small windows); shares the batch kernel.  Without
-// the L2 prefetch code, so that its loads take the evict-first hint (binary16 M = 8:
-// 118.8 -> 105.6 us).
+// Buffered 16-byte output stores (for small windows); shares the batch kernel.
 #define RFI_INSTV(DT, SPU, P, CH)                                                           \
-    {DT, SPU, P, CH, 0, 0, 0, 1, 0, 0, 0,                                                   \
+    {DT, SPU, P, CH, 0, 0, 0, 1, 0, 0, 1,                                                   \
      (const void *)&rfi::k_block<DT, SPU, P, CH, false, 0, false, true, false, false,      \
-                                 false>,                                                    \
+                                 true>,                                                     \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, false, false, false, false, true>}
 #define RFI_INSTV_P(DT, SPU)                                                                \
     RFI_INSTV(DT, SPU, 1, 1), RFI_INSTV(DT, SPU, 1, 2), RFI_INSTV(DT, SPU, 1, 4),           \
@@ -140,9 +137,9 @@ WpTable wp_instances_f16();   // rfi_inst_wp_f16.cu
         RFI_INSTP_CH(DT, SPU, 32, K)
 // Online per-stream SK thresholds, 128-register budget.
 #define RFI_INSTA(DT, SPU, P, CH, K)                                                        \
-    {DT, SPU, P, CH, K, 0, 0, 0, 0, 1, 0,                                                   \
+    {DT, SPU, P, CH, K, 0, 0, 0, 0, 1, 1,                                                   \
      (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, false, false, false, true,    \
-                                 false>,                                                    \
+                                 true>,                                                     \
      (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, false, false, true, true>}
 #define RFI_INSTA_CH(DT, SPU, P, K)                                                         \
     RFI_INSTA(DT, SPU, P, 1, K), RFI_INSTA(DT, SPU, P, 2, K), RFI_INSTA(DT, SPU, P, 4, K),  \

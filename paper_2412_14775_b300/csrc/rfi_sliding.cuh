@@ -102,7 +102,7 @@ __device__ __forceinline__ void process_group_sw(const StreamArgs &a, long long 
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             const char *p = cp_ + (long long)q * CHB + c * (P * UB);
-            if (rfi_in(p, UB, a.vis, vis_ext, a.err)) load_unit_ef(p, u[c]);   // read once
+            if (rfi_in(p, UB, a.vis, vis_ext, a.err)) load_unit(p, u[c]);
             else u[c] = Unit<UB>{};
         }
     };

@@ -89,11 +89,8 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
 #pragma unroll
         for (int e = 0; e < CH; ++e) {
             const char *p = p0 + e * UB;
-            if (ok && rfi_in(p, UB, a.vis, vis_ext, a.err)) {
-                load_unit_ef(p, u[e]);                                 // read once
-            } else {
-                u[e] = Unit<UB>{};
-            }
+            if (ok && rfi_in(p, UB, a.vis, vis_ext, a.err)) load_unit(p, u[e]);
+            else u[e] = Unit<UB>{};
         }
     };
     WinAcc A;
