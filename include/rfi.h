@@ -187,8 +187,7 @@ typedef enum {
  *                  stream's windows g with g mod P = j): no butterfly over the row's
  *                  lanes and one evaluation per window, for small windows and T x F
  *                  footprints, with P times shorter tasks than one lane per row.
- *                  lanes_per_row 2, 4 or 8 (P need not divide M), K/M a multiple of
- *                  lanes_per_row; the direct loader, the 128-register budget, plain
+ *                  lanes_per_row 2, 4 or 8 (P need not divide M), K/M >= lanes_per_row; the direct loader, the 128-register budget, plain
  *                  stores, no Kahan (precision = 1 with time-only windows: each window
  *                  still runs sample by sample in one lane, so its statistics and flags
  *                  equal those of the one-lane mixed kernel); excludes partial_windows,

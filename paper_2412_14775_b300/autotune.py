@@ -113,10 +113,10 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
                     stage1.append((run(o), o))
                 except B.RfiError:      # no such kernel, or it does not fit the shared memory
                     continue
-    # window-parallel lanes: the lanes of a row take whole windows in turn (bins must
-    # hold a multiple of lanes_per_row windows)
+    # window-parallel lanes: the lanes of a row take whole windows in turn (a bin must
+    # hold at least lanes_per_row windows)
     for P in (2, 4, 8):
-        if P * F > 32 or (K // M) % P:
+        if P * F > 32 or K // M < P:
             continue
         for wpb in (4, 8):
             o = dict(lanes_per_row=P, warps_per_block=wpb, max_registers=0, prefetch_groups=0,

@@ -264,9 +264,9 @@ int choose_shape(rfi_ctx *c, int P_req) {
         if (P * c->F > 32)
             return fail(RFI_EINVAL, "lanes_per_row (%d) x window_F (%d) must not exceed 32", P,
                         c->F);
-        if ((c->K / c->M) % P != 0)
-            return fail(RFI_EINVAL, "lane_split = 1 needs K/M = %d windows per bin to be a "
-                                    "multiple of lanes_per_row = %d", c->K / c->M, P);
+        if (c->K / c->M < P)
+            return fail(RFI_EINVAL, "lane_split = 1 needs at least lanes_per_row = %d windows "
+                                    "per averaging bin (K/M = %d)", P, c->K / c->M);
         c->P = P;
         c->spu = spu_w;
         c->S = c->M / spu_w;                   // load units per window, all in one lane
@@ -431,6 +431,7 @@ StreamArgs make_args(const rfi_ctx *c, const void *vis, int T, uint32_t *flags, 
     a.k_sigma = (float)c->adp.k_sigma;
     a.n_warm = (float)c->adp.n_warm;
     a.ovl_bytes = c->ovl;
+    a.wphase = c->wp ? (int)((c->n_seen / c->M) % c->P) : 0;
     a.hop = c->H;
     if (c->sw) {
         a.warm = (int)std::min<long long>(c->n_seen / c->H, c->M / c->H - 1);

@@ -76,6 +76,9 @@ struct StreamArgs {
     int hop, warm;
     float *sw_tot, *sw_pend;
     uint32_t *sw_hist;
+    // window-parallel lanes (rfi_wpar.cuh): the stream's window index of window 0 of
+    // this launch, mod lanes_per_row
+    int wphase;
 };
 
 struct BatchArgs {

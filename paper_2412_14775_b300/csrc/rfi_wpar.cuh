@@ -44,12 +44,10 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
 
     // windows of this launch are local indices 0..nwin-1, global g0 + i; lane j owns the
     // windows with g mod P = j.  Round k covers the P windows kP - s .. kP - s + P - 1
-    // (s = g0 mod P), lane j the window kP - s + j.
-    // s = g0 mod P: bins hold a multiple of P windows and start at a multiple of K, so
-    // the windows of the open bin before this launch give it
-    const int s = (a.bin_pos0 / a.M) % P;
+    // (s = g0 mod P, from the host), lane j the window kP - s + j.
+    const int s = a.wphase;
     const int NR = (a.nwin + s + P - 1) / P;                  // rounds
-    const int wpbin = a.K / a.M;                              // windows per bin (mult. of P)
+    const int wpbin = a.K / a.M;                              // windows per bin (>= P)
     int wib = a.bin_pos0 / a.M;                               // windows of the open bin seen
     int bin = 0;
 
@@ -183,19 +181,26 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
                 }
             }
         }
-        // flagged samples leave the average (end of Sec. 2.1); bins hold whole rounds
-        if (ok && !f) {
+        // flagged samples leave the average (end of Sec. 2.1).  The open bin needs
+        // wpbin - wib more windows: the round's windows [first, e) belong to it; if the
+        // bin closes in this round (at most once: a bin holds at least P windows), the
+        // rest open the next one
+        const bool add = ok && !f;
+        auto add_window = [&]() {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 acc[2 * c] += A.a[c].x;
                 acc[2 * c + 1] += A.a[c].y;
             }
             cnt += (float)a.M;
-        }
-        // windows of the open bin seen: this round's windows inside the launch
+        };
         const int first = max(k * P - s, 0), last = min(k * P - s + P, a.nwin);
-        wib += last - first;
-        if (wib == wpbin) {
+        const int e = first + (wpbin - wib);
+        if (last < e) {
+            if (add) add_window();
+            wib += last - first;
+        } else {
+            if (add && i < e) add_window();
             float tot[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
@@ -204,8 +209,9 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = 0.f;
             cnt = 0.f;
-            wib = 0;
             ++bin;
+            if (add && i >= e) add_window();
+            wib = last - e;
         }
         A.s = A.q = A.u = A.v = zero2;
 #pragma unroll

@@ -29,8 +29,13 @@ pytestmark = pytest.mark.gpu
     ("f16", 3, 12, 2, 1, [9, 15, 12]),          # odd M, one sample per 16-byte load
     ("f32", 64, 128, 2, 1, [128, 64]),          # long windows: 16 chunks per window
     ("f32", 4, 32, 8, 1, [40, 24]),
+    ("f16", 10, 250, 2, 2, [250, 250]),         # 25 windows per bin: rounds straddle bins
+    ("f32", 8, 24, 2, 1, [40, 56, 24]),         # 3 windows per bin
+    ("f16", 5, 15, 2, 4, [35, 45]),
+    ("f32", 4, 20, 4, 1, [28, 36]),             # 5 windows per bin, 4 lanes
 ], ids=["f16_5x4", "f32_5x4_straddle", "f32_5x4_P4", "f16_10x2", "f16_M8", "f16_M8_P4",
-        "f32_M16_P4", "f16_M3", "f32_M64", "f32_M4_P8"])
+        "f32_M16_P4", "f16_M3", "f32_M64", "f32_M4_P8", "f16_10x2_K250", "f32_M8_K3M",
+        "f16_5x4_K3M", "f32_M4_K5M_P4"])
 def test_window_parallel_matches_oracle(dtype, M, K, P, F, Ts):
     reps = _check_stream(7, 8, M, K, Ts, dtype, seed=91, lanes_per_row=P,
                          window_F=F, lane_split=1)
@@ -77,8 +82,8 @@ def test_window_parallel_option_checks():
                 dict(lane_split=1, lanes_per_row=4, window_F=16)):
         with pytest.raises(RfiError):
             RfiStream(4, 16, 8, 32, thr, "f32", **bad)
-    with pytest.raises(RfiError):            # K/M = 3 windows per bin, not a multiple of 2
-        RfiStream(4, 4, 8, 24, thr, "f32", lane_split=1)
+    with pytest.raises(RfiError):            # a bin of one window, fewer than 2 lanes' worth
+        RfiStream(4, 4, 8, 8, thr, "f32", lane_split=1)
     a = RfiStream(4, 4, 8, 32, thr, "f32", lane_split=1)
     b = RfiStream(4, 4, 8, 32, thr, "f32")
     with pytest.raises(RfiError):            # a batch does not mix lane splits
@@ -158,7 +163,7 @@ def test_window_parallel_random_combinations(seed):
         P = int(rng.choice([2, 4, 8]))
         if P * F > 32 or M * F < 2:
             continue
-        K = M * P * int(rng.integers(1, 4))
+        K = M * int(rng.integers(P, 3 * P + 1))
         Ts = [M * int(rng.integers(1, 3 * P + 1)) for _ in range(int(rng.integers(1, 4)))]
         _check_stream(int(rng.integers(2, 7)), F * int(rng.integers(1, 4)), M, K, Ts, dtype,
                       seed=int(rng.integers(1, 1 << 30)), lanes_per_row=P, window_F=F,
