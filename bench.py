@@ -266,10 +266,11 @@ def cpu_baseline(seconds_target=10.0):
                       f"{dt1:.1f} s single-threaded"}
 
 
-def footprint_extras(torch, cs, peak, steps=500, warmup=10):
+def footprint_extras(torch, cs, peak, steps=500, warmup=10, only=None):
     """The paper's time-frequency windows (10 x 2 and 5 x 4, W = 20) on the 62-station,
     64-channel geometry with blocks of T = 250 samples (a multiple of both time
-    extents), averaging 250 -> 1, complex64 and binary16."""
+    extents), averaging 250 -> 1, complex64 and binary16; only = (dtype, M, F) times
+    that one case."""
     import synth
     from paper_2412_14775_b300 import RfiStream, autotune, default_thresholds
     T, K = 250, 250
@@ -277,9 +278,13 @@ def footprint_extras(torch, cs, peak, steps=500, warmup=10):
     res = {}
     v32 = synth.generate.device_block(62, 64, T, seed=400, dtype="f32")
     for dtype in ("f32", "f16"):
+        if only and only[0] != dtype:
+            continue
         vis = v32 if dtype == "f32" else v32.half()
         sb = 32 if dtype == "f32" else 16
         for M, F in ((10, 2), (5, 4)):
+            if only and only[1:] != (M, F):
+                continue
             thr = default_thresholds(M * F)
             best, _ = autotune.tune(62, 64, M, K, thr, dtype, vis, fixed={"window_F": F},
                                     cache_path=autotune.TUNED_PATH, write_cache=False)
@@ -621,6 +626,9 @@ def main():
                     help="lanes_per_row,warps_per_block[,prefetch_groups,prefetch_bytes]")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16"],
                     help="input storage of the timed block (f16: same block in binary16)")
+    ap.add_argument("--footprint", default="", choices=["", "10x2", "5x4"],
+                    help="time only this T x F window footprint (blocks of 250 samples, "
+                         "--dtype storage) and print its figures")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -633,6 +641,14 @@ def main():
     import synth
     from paper_2412_14775_b300 import RfiStream, autotune, default_thresholds
     from paper_2412_14775_b300.shard import aggregate
+
+    if args.footprint:
+        import torch
+        M, F = (int(x) for x in args.footprint.split("x"))
+        res = footprint_extras(torch, torch.cuda.current_stream(), _peaks()[0], args.steps,
+                               args.warmup, only=(args.dtype, M, F))
+        print(json.dumps({"footprint": res}))
+        return
 
     ws, rank, local = _dist()
     if ws > 1:
