@@ -187,6 +187,33 @@ def test_lofar_scale_sampled_rows(dtype, M):
     st.close()
 
 
+@pytest.mark.parametrize("dtype,M,F", [("f32", 10, 2), ("f32", 5, 4), ("f16", 10, 2),
+                                       ("f16", 5, 4)])
+def test_footprints_full_size_sampled(dtype, M, F):
+    """The paper's 10 x 2 and 5 x 4 footprints on 62 stations, 64 channels, T = K = 250,
+    in the launch shape the bench times (the committed tuning table); the oracle checks
+    a seeded sample of 512 footprint rows (F adjacent channels of one baseline each)."""
+    T = K = 250
+    thr = default_thresholds(M * F)
+    d = synth.lofar_block(seed=4, T=T)
+    vis = to_device_rows(d["vis"], dtype)
+    best, _ = autotune.tune(62, 64, M, K, thr, dtype, vis, fixed={"window_F": F},
+                            cache_path=autotune.TUNED_PATH, write_cache=False)
+    st = RfiStream(62, 64, M, K, thr, dtype, **autotune.options_of(best))
+    g = run_gpu(st, vis)
+    del vis
+    groups = np.sort(np.random.default_rng(19).choice(st.R // F, size=512, replace=False))
+    rows = (groups[:, None] * F + np.arange(F)).ravel()
+    v = d["vis"].reshape(st.R, T, 4, 2)[rows]
+    o = oracle.OracleStream(len(rows), M, K, **thr, F=F).process(_oracle_input(v, dtype))
+    gs = {k: (val[groups] if k in ("tau", "r_re", "r_im") else val[rows])
+          for k, val in g.items()}
+    rep = compare(gs, o, thr, M, K, F=F)
+    print(f"footprint {M}x{F} {dtype}", autotune.options_of(best), rep)
+    binding.rfi_check(st.ctx)
+    st.close()
+
+
 def test_batched_uneven_full_size_sampled():
     """The batched workload at full size: 8 binary16 subbands (stations 24..76,
     channels 16..128, T = 256) in one persistent launch replayed from a CUDA graph, in
