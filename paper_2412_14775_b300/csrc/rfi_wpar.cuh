@@ -69,12 +69,10 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
     uint32_t *const fl_row = a.flags + rowc * a.Wpr;
     const bool lead = active && j == 0;
     const long long plane = a.stats_plane;
-    // flag words: 0 = windows tile a word, 1 = whole words per window, 3 = M < 32 and
-    // windows straddle words (bits pass through a 64-bit word), 2 = any other M
-    const int fmode = (32 % a.M == 0) ? 0 : ((a.M % 32 == 0) ? 1 : (a.M < 32 ? 3 : 2));
+    const int fmode = (32 % a.M == 0) ? 0 : ((a.M % 32 == 0) ? 1 : 2);
     const uint32_t wmask = a.M >= 32 ? FULL : ((1u << a.M) - 1u);
     const int words_per_window = a.M >> 5;
-    unsigned long long fword = 0;              // the open flag word in the low 32 bits
+    uint32_t fword = 0;
     const int nbits = a.T;
     const float2 eps2 = make_float2(a.eps, a.eps);
 
@@ -160,18 +158,8 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
                 if (fe) fword |= wmask << b0;
                 if (b0 + a.M == 32) {
                     if (lead && rfi_in(fl_row + ((wi * a.M) >> 5), 4, a.flags, flags_ext, a.err))
-                        fl_row[(wi * a.M) >> 5] = (uint32_t)fword;
+                        fl_row[(wi * a.M) >> 5] = fword;
                     fword = 0;
-                }
-            } else if (fmode == 3) {
-                // the window's bits may run past the open word into the next: write the
-                // open word once it is full and shift the next one down
-                const int lo = wi * a.M, b0 = lo & 31;
-                if (fe) fword |= (unsigned long long)wmask << b0;
-                if (b0 + a.M >= 32) {
-                    if (lead && rfi_in(fl_row + (lo >> 5), 4, a.flags, flags_ext, a.err))
-                        fl_row[lo >> 5] = (uint32_t)fword;
-                    fword >>= 32;
                 }
             } else if (fmode == 1) {
                 const int w0 = (wi * a.M) >> 5;
@@ -187,7 +175,7 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
                     lo += nb;
                     if ((lo & 31) == 0) {
                         if (lead && rfi_in(fl_row + ((lo - 1) >> 5), 4, a.flags, flags_ext, a.err))
-                            fl_row[(lo - 1) >> 5] = (uint32_t)fword;
+                            fl_row[(lo - 1) >> 5] = fword;
                         fword = 0;
                     }
                 }
@@ -250,7 +238,7 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
     }
     if (nbits & 31) {
         if (lead && rfi_in(fl_row + (nbits >> 5), 4, a.flags, flags_ext, a.err))
-            fl_row[nbits >> 5] = (uint32_t)fword;
+            fl_row[nbits >> 5] = fword;
     }
     if (wib != 0 && active && rfi_in(a.carry + (row * P + j) * 9, 36, a.carry, carry_ext, a.err)) {
         float *cp = a.carry + (row * P + j) * 9;
