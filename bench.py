@@ -629,6 +629,9 @@ def main():
     ap.add_argument("--footprint", default="", choices=["", "10x2", "5x4"],
                     help="time only this T x F window footprint (blocks of 250 samples, "
                          "--dtype storage) and print its figures")
+    ap.add_argument("--batched", action="store_true",
+                    help="time only the 8 uneven binary16 subbands (one persistent launch "
+                         "from a CUDA graph against 8 sequential launches) and print them")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -648,6 +651,18 @@ def main():
         res = footprint_extras(torch, torch.cuda.current_stream(), _peaks()[0], args.steps,
                                args.warmup, only=(args.dtype, M, F))
         print(json.dumps({"footprint": res}))
+        return
+
+    if args.batched:
+        import torch
+        import synth
+        from paper_2412_14775_b300 import autotune, default_thresholds
+        v16 = synth.generate.device_block(62, 64, 256, seed=2, dtype="f16")
+        best, _ = autotune.tune(62, 64, 16, 256, default_thresholds(16), "f16", v16,
+                                cache_path=autotune.TUNED_PATH, write_cache=False)
+        del v16
+        res = batched_extras(autotune.options_of(best), torch, args.steps, args.warmup)
+        print(json.dumps({"batched": res}))
         return
 
     ws, rank, local = _dist()
