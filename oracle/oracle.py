@@ -54,6 +54,13 @@ def _load():
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.oracle_process_block_tf.restype = ctypes.c_int
+        lib.oracle_process_block_given_flags.argtypes = [
+            ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_process_block_given_flags.restype = ctypes.c_int
         lib.oracle_window_stats_hop.argtypes = [
             ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
             ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -157,8 +164,12 @@ class OracleStream:
         """(windows completed, stream index of their first sample) for T samples."""
         return (self.pending.shape[1] + T) // self.M, self.n_seen
 
-    def process(self, vis):
-        """Process one block; vis is any layout accepted by to_f64_rows with R rows."""
+    def process(self, vis, wflag=None):
+        """Process one block; vis is any layout accepted by to_f64_rows with R rows.
+
+        wflag: optional window flags [R/F][windows of the block] to use instead of the
+        oracle's own (e.g. those of another arithmetic); flag bits and averages then
+        follow them.  Not with `partial`."""
         v = to_f64_rows(vis)
         R = v.shape[0]
         if R != self.R:
@@ -184,13 +195,19 @@ class OracleStream:
             wflag=np.zeros((G, nw), dtype=np.uint8),
             flagbits=np.zeros((R, nwords), dtype=np.uint32),
             avg=np.zeros((R, n_out, 8)), weight=np.zeros((R, n_out)))
-        rc = _load().oracle_process_block_tf(
-            v.ctypes.data, R, T, self.M, self.F, self.K, self.thr.ctypes.data,
-            int(self.compensated),
-            self.n_seen, self.carry_sum.ctypes.data, self.carry_cnt.ctypes.data,
-            out["tau"].ctypes.data, out["r_re"].ctypes.data, out["r_im"].ctypes.data,
-            out["wflag"].ctypes.data, out["flagbits"].ctypes.data,
-            out["avg"].ctypes.data, out["weight"].ctypes.data)
+        common = (v.ctypes.data, R, T, self.M, self.F, self.K, self.thr.ctypes.data,
+                  int(self.compensated),
+                  self.n_seen, self.carry_sum.ctypes.data, self.carry_cnt.ctypes.data)
+        outs = (out["tau"].ctypes.data, out["r_re"].ctypes.data, out["r_im"].ctypes.data,
+                out["wflag"].ctypes.data, out["flagbits"].ctypes.data,
+                out["avg"].ctypes.data, out["weight"].ctypes.data)
+        if wflag is None:
+            rc = _load().oracle_process_block_tf(*common, *outs)
+        else:
+            if self.partial:
+                raise ValueError("given window flags need whole windows (partial=False)")
+            given = np.ascontiguousarray(np.asarray(wflag).astype(np.uint8).reshape(G, nw))
+            rc = _load().oracle_process_block_given_flags(*common, given.ctypes.data, *outs)
         if rc != 0:
             raise ValueError("oracle rejected the block sizes")
         self.n_seen += T

@@ -146,11 +146,11 @@ long long oracle_outputs_for(long long n_seen, int T, int K)
  *   avg                     [R][n_out][8]    mean of unflagged samples of each completed bin
  *   weight                  [R][n_out]       unflagged count / K
  * Returns 0, or -1 on invalid sizes.  */
-int oracle_process_block_tf(const double *vis, int R, int T, int Mt, int F, int K,
-                            const double thr[5], int compensated, long long n_seen,
-                            double *carry_sum, double *carry_cnt,
-                            double *tau, double *r_re, double *r_im, uint8_t *wflag,
-                            uint32_t *flagbits, double *avg, double *weight)
+static int process_block_impl(const double *vis, int R, int T, int Mt, int F, int K,
+                              const double thr[5], int compensated, long long n_seen,
+                              double *carry_sum, double *carry_cnt, const uint8_t *given,
+                              double *tau, double *r_re, double *r_im, uint8_t *wflag,
+                              uint32_t *flagbits, double *avg, double *weight)
 {
     if (R < 0 || T < 0 || Mt < 1 || F < 1 || Mt * F < 2 || R % F != 0 || K < Mt ||
         T % Mt != 0 || K % Mt != 0 || n_seen % Mt != 0)
@@ -190,9 +190,11 @@ int oracle_process_block_tf(const double *vis, int R, int T, int Mt, int F, int 
             const double t  = oracle_sk_window(stokes, W, d, eps, compensated, 0, 0);
             const double rr = oracle_ds_window(stokes, W, 0, eps, compensated, 0);
             const double ri = oracle_ds_window(stokes, W, 1, eps, compensated, 0);
-            const int f = oracle_flag(t, rr, ri, s_low, s_high, gamma);
-
             const size_t o = (size_t)g * nwin + w;
+            /* the window's flag: from its statistics, or the caller's (the flags of
+             * another arithmetic, whose averages are wanted) */
+            const int f = given ? (given[o] != 0) : oracle_flag(t, rr, ri, s_low, s_high, gamma);
+
             tau[o] = t; r_re[o] = rr; r_im[o] = ri; wflag[o] = (uint8_t)f;
 
             const long long g_end = n_seen + (long long)(w + 1) * Mt;   /* stream index */
@@ -231,6 +233,31 @@ int oracle_process_block_tf(const double *vis, int R, int T, int Mt, int F, int 
     }
     free(stokes); free(bins); free(bins_n);
     return 0;
+}
+
+int oracle_process_block_tf(const double *vis, int R, int T, int Mt, int F, int K,
+                            const double thr[5], int compensated, long long n_seen,
+                            double *carry_sum, double *carry_cnt,
+                            double *tau, double *r_re, double *r_im, uint8_t *wflag,
+                            uint32_t *flagbits, double *avg, double *weight)
+{
+    return process_block_impl(vis, R, T, Mt, F, K, thr, compensated, n_seen, carry_sum,
+                              carry_cnt, 0, tau, r_re, r_im, wflag, flagbits, avg, weight);
+}
+
+/* As oracle_process_block_tf, with the window flags given by the caller (given
+ * [R/F][T/Mt], nonzero = flagged) instead of taken from the statistics: flag bits and
+ * averages follow them (Sec. 2.1: flagged samples leave the time average), and wflag
+ * echoes them; the statistics are still those of this oracle. */
+int oracle_process_block_given_flags(const double *vis, int R, int T, int Mt, int F, int K,
+                                     const double thr[5], int compensated, long long n_seen,
+                                     double *carry_sum, double *carry_cnt, const uint8_t *given,
+                                     double *tau, double *r_re, double *r_im, uint8_t *wflag,
+                                     uint32_t *flagbits, double *avg, double *weight)
+{
+    if (!given) return -1;
+    return process_block_impl(vis, R, T, Mt, F, K, thr, compensated, n_seen, carry_sum,
+                              carry_cnt, given, tau, r_re, r_im, wflag, flagbits, avg, weight);
 }
 
 /* Time-only windows of W samples per row (F = 1). */

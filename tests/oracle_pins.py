@@ -682,3 +682,38 @@ def pin_p13_sliding_windows(seed=14):
 
 
 ALL_PINS.append(pin_p13_sliding_windows)
+
+
+def pin_p6b_given_window_flags(seed=16):
+    """P6b: with window flags given by the caller (the flags of another arithmetic), the
+    flag bits and averages follow those flags: mean of the samples of unflagged windows
+    (numpy), weight n/K, bits over the flagged windows' samples; giving the oracle its
+    own flags changes nothing."""
+    rng = np.random.default_rng(seed)
+    for M, K, T, F in ((4, 8, 24, 1), (5, 10, 20, 2), (16, 32, 64, 1)):
+        R = 6 * F
+        v = rng.standard_normal((R, T, 4)) + 1j * rng.standard_normal((R, T, 4))
+        v[:, :M] *= 4.0
+        thr = (1.0, 0.3, 2.0, 0.5, EPS32)
+        own = OracleStream(R, M, K, *thr, F=F).process(v)
+        again = OracleStream(R, M, K, *thr, F=F).process(v, wflag=own["wflag"])
+        for k in own:
+            assert np.array_equal(own[k], again[k]), k
+        given = rng.integers(0, 2, size=(R // F, T // M)).astype(np.uint8)
+        out = OracleStream(R, M, K, *thr, F=F).process(v, wflag=given)
+        assert np.array_equal(out["wflag"], given)
+        for row in range(R):
+            keep = ~np.repeat(given[row // F], M).astype(bool)
+            for b in range(T // K):
+                sl = slice(b * K, (b + 1) * K)
+                x, kp = v[row, sl], keep[sl]
+                n = kp.sum()
+                want = x[kp].mean(axis=0) if n else np.zeros(4)
+                got = out["avg"][row, b].reshape(4, 2)
+                assert np.allclose(got[:, 0], want.real, rtol=1e-13, atol=1e-14)
+                assert np.allclose(got[:, 1], want.imag, rtol=1e-13, atol=1e-14)
+                assert out["weight"][row, b] == n / K
+            assert _bits(out["flagbits"][row], T) == [int(not k) for k in keep]
+
+
+ALL_PINS.append(pin_p6b_given_window_flags)

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from oracle import mixed
 from paper_2412_14775_b300 import RfiStream, default_thresholds
@@ -36,14 +37,12 @@ def test_mixed_kernel_matches_emulation(dtype, M, K, split):
     wf = expand_window_flags(g["flagbits"], M, T)
     assert np.array_equal(wf, o["wflag"].astype(bool))
     assert 0 < wf.mean() < 1
-    # averages: float32 sums of the unflagged samples, against float64 means
+    # averages: the FP64 oracle's means of the samples of the windows this arithmetic
+    # left unflagged (the emulation's flags, equal to the kernel's as checked above)
     R = rows.shape[0]
-    x = rows.astype(np.float64).reshape(R, T // K, K, 8)
-    keep = ~np.repeat(wf, M, axis=1).reshape(R, T // K, K)
-    n = keep.sum(axis=2)
-    want = np.where(n[..., None] > 0, (x * keep[..., None]).sum(axis=2) / np.maximum(n, 1)[..., None], 0)
-    assert np.all(rel_err(g["avg"], want, 1.0) <= 1e-5)
-    assert np.array_equal(g["weight"], (n / K).astype(np.float32).astype(np.float64))
+    ref = oracle.OracleStream(R, M, K, **thr).process(rows, wflag=o["wflag"])
+    assert np.all(rel_err(g["avg"], ref["avg"], 1.0) <= 1e-5)
+    assert np.array_equal(g["weight"], ref["weight"].astype(np.float32).astype(np.float64))
 
 
 def test_mixed_flags_close_to_float32_flags():

@@ -158,3 +158,64 @@ def test_sliding_window_pin_catches_mutant(name, monkeypatch):
     monkeypatch.setattr(oracle, "SlidingOracleStream", mod.SlidingOracleStream)
     with pytest.raises((AssertionError, ValueError, IndexError)):
         oracle_pins.pin_p13_sliding_windows()
+
+
+# The mixed-precision emulation (oracle/mixed.py, Tables 3 and 4): each group run at the
+# other precision, Table 3's groups 5 and 6 swapped, and mistakes in its formulas must
+# fail the exact-evaluation pin.  (Table 4's group 5 cannot change a result; see
+# tests/test_oracle_mixed.py.)
+_PREC_SITE = {
+    "sk": '"sk": {1: F32, 2: F32, 3: F32, 4: F32, 5: F16, 6: F32, 7: F16},',
+    "ds": '"ds": {1: F32, 2: F32, 3: F32, 4: F16, 5: F16, 6: F16, 7: F16},',
+}
+
+
+def _prec_flip(stat, group):
+    old = _PREC_SITE[stat]
+    fmt = "F16" if f"{group}: F32" in old else "F32"
+    other = "F32" if fmt == "F16" else "F16"
+    return old, old.replace(f"{group}: {other}", f"{group}: {fmt}")
+
+
+MIXED_MUTANTS = {f"mixed_{s}_g{g}_flipped": _prec_flip(s, g)
+                 for s in ("sk", "ds") for g in range(1, 8) if (s, g) != ("ds", 5)}
+MIXED_MUTANTS.update({
+    "mixed_sk_g5_g6_swapped": (_PREC_SITE["sk"], _PREC_SITE["sk"].replace(
+        "5: F16, 6: F32", "5: F32, 6: F16")),
+    "mixed_tau_minus_one_outside": ("tau = f7(lead) * (t - one7)", "tau = f7(lead) * t - one7"),
+    "mixed_eps16_is_callers_eps": ("return F16(2.0 ** -10) if fmt is F16 else F32(eps)",
+                                   "return fmt(eps)"),
+    "mixed_params_not_binary32": ("return fmt(F32(x))", "return fmt(x)"),
+    "mixed_sk_sums_reversed": ("for i in range(W):                               # g3, g4",
+                               "for i in reversed(range(W)):                    # g3, g4"),
+    "mixed_ds_sums_reversed": ("for i in range(W):                                # g4",
+                               "for i in reversed(range(W)):                     # g4"),
+    "mixed_r_without_sqrt": ("r = np.sqrt((qb.astype(f6) + ub.astype(f6)) + vb.astype(f6))",
+                             "r = ((qb.astype(f6) + ub.astype(f6)) + vb.astype(f6))"),
+    "mixed_p_eps_dropped": ("p = np.sqrt((a.astype(f2) + b.astype(f2)) + c.astype(f2)) + _eps(f2, eps)",
+                            "p = np.sqrt((a.astype(f2) + b.astype(f2)) + c.astype(f2))"),
+})
+
+
+@pytest.fixture(scope="module")
+def mixed_cases():
+    import test_oracle_mixed as T
+    cases = T._windows() + T._threshold_cases() + T._order_cases()
+    return cases, [T._exact(v, thr) for v, thr in cases]
+
+
+@pytest.mark.parametrize("name", sorted(MIXED_MUTANTS))
+def test_mixed_precision_pin_catches_mutant(name, mixed_cases):
+    import types
+    import oracle.mixed
+    import test_oracle_mixed as T
+    old, new = MIXED_MUTANTS[name]
+    with open(oracle.mixed.__file__) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mod = types.ModuleType("oracle._mixed_mutant")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(text.replace(old, new), "mixed_mutant.py", "exec"), mod.__dict__)
+    cases, exact = mixed_cases
+    with pytest.raises(AssertionError):
+        T.pin_emulation_exact(cases, exact, emulation=mod)
