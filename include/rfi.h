@@ -338,9 +338,12 @@ int rfi_batch_graph_destroy(rfi_batch_graph *g);
  * lanes_per_row = 1 and otherwise default options.
  *   - Limit: R * 36 bytes of carry must fit the array, i.e. at most
  *     RFI_NOALLOC_SCRATCH_BYTES / 36 = 116508 rows; larger streams get RFI_EINVAL.
- *   - The first call on each device looks up the array's device address with
- *     cudaGetSymbolAddress (which may load the module); make that first call before
- *     any stream capture.
+ *   - The first call made in each CUDA context (the device's primary context, or a
+ *     context the caller made current through the driver API; after cudaDeviceReset
+ *     the new primary context counts as another) looks up the array's device address
+ *     with cudaGetSymbolAddress (which may load the module) and keeps it for that
+ *     context; make that first call before any stream capture.
+ *   - Blocks with T * R > 2^40 samples get RFI_EINVAL, as for rfi_process_block.
  *   - Every call shares the array, and it keeps what the last call wrote.  A block
  *     that continues an open bin (n_seen % K != 0) reads the carry left by the
  *     previous call, so such blocks of one stream must follow each other with no

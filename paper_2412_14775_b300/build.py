@@ -36,8 +36,13 @@ DEBUG_LIB = os.path.join(HERE, "_lib", "librfi_debug.so")
 
 
 def build(force: bool = False, verbose: bool = False, debug_bounds: bool = False) -> str:
-    """Compile (if stale) and return the path of librfi.so (or of librfi_debug.so)."""
+    """Compile (if stale) and return the path of librfi.so (or of librfi_debug.so).
+
+    Objects are kept per build flavour; a translation unit is recompiled when it, or
+    any header of the library, is newer than its object."""
     lib = DEBUG_LIB if debug_bounds else LIB
+    headers = [f for f in _inputs() if not f.endswith(".cu")]
+    newest_header = max(os.path.getmtime(f) for f in headers)
     if not force and os.path.exists(lib):
         newest = max(os.path.getmtime(f) for f in _inputs())
         if os.path.getmtime(lib) >= newest:
@@ -46,22 +51,31 @@ def build(force: bool = False, verbose: bool = False, debug_bounds: bool = False
     objdir = os.path.join(HERE, "_lib", "obj_debug" if debug_bounds else "obj")
     os.makedirs(objdir, exist_ok=True)
     extra = ["-DRFI_DEBUG_BOUNDS"] if debug_bounds else []
-    # translation units compile in parallel, then one link step
-    procs, objs = [], []
+    # stale translation units compile in parallel, then one link step
+    procs, objs, tmps = [], [], []
     for src in SOURCES:
-        obj = os.path.join(objdir, src.replace(".cu", f".{os.getpid()}.o"))
-        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", "-o", obj, os.path.join(CSRC, src)]
+        path = os.path.join(CSRC, src)
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
+        objs.append(obj)
+        if (not force and not verbose and os.path.exists(obj) and
+                os.path.getmtime(obj) >= max(os.path.getmtime(path), newest_header)):
+            continue
+        tmp = obj + f".tmp{os.getpid()}"
+        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", "-o", tmp, path]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
-        procs.append(subprocess.Popen(cmd))
-        objs.append(obj)
-    failed = [p.wait() for p in procs]
-    if any(failed):
-        raise RuntimeError(f"nvcc failed for {[s for s, r in zip(SOURCES, failed) if r]}")
+        procs.append((src, subprocess.Popen(cmd)))
+        tmps.append((tmp, obj))
+    failed = [src for src, p in procs if p.wait()]
+    if failed:
+        for tmp, _ in tmps:
+            if os.path.exists(tmp):
+                os.remove(tmp)
+        raise RuntimeError(f"nvcc failed for {failed}")
+    for tmp, obj in tmps:
+        os.replace(tmp, obj)
     tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([NVCC, *ARCH, "--cudart", "static", "-shared", "-o", tmp, *objs])
-    for o in objs:
-        os.remove(o)
     os.replace(tmp, lib)
     return lib
 

@@ -14,26 +14,36 @@ so each test alone flags a fraction fa of clean windows.  d only scales tau (thr
 """
 import math
 
+import numpy as np
+
 
 def permissive(d=1.0, eps=2.0 ** -23):
     """Thresholds that flag nothing finite (for collecting statistics)."""
     return dict(d=d, s_low=-math.inf, s_high=math.inf, gamma=math.inf, eps=eps)
 
 
+def _host(x):
+    """A statistics buffer as a float64 numpy array [3, n] (a device tensor is copied to
+    host memory; torch is used only for that copy)."""
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.asarray(x, dtype=np.float64).reshape(3, -1)
+
+
 def thresholds_for_false_alarm(stats, fa=0.05, d=1.0, eps=2.0 ** -23):
-    """stats: tensor [3, ..., n_windows] (tau, r_Re, r_Im) from clean data, or a list of
-    them.  Returns a thresholds dict."""
-    import torch
+    """stats: array or device tensor [3, ..., n_windows] (tau, r_Re, r_Im) from clean
+    data, or a list of them.  Returns a thresholds dict."""
     if isinstance(stats, (list, tuple)):
-        stats = torch.cat([s.reshape(3, -1) for s in stats], dim=1)
-    s = stats.reshape(3, -1).float()
-    tau = s[0][torch.isfinite(s[0])]
-    r = torch.maximum(s[1], s[2])
-    r = r[torch.isfinite(r)]
+        s = np.concatenate([_host(x) for x in stats], axis=1)
+    else:
+        s = _host(stats)
+    tau = s[0][np.isfinite(s[0])]
+    r = np.maximum(s[1], s[2])
+    r = r[np.isfinite(r)]
 
     def q(x, p):
-        k = min(max(int(round(p * (x.numel() - 1))), 0), x.numel() - 1)
-        return float(torch.sort(x).values[k])
+        k = min(max(int(round(p * (x.size - 1))), 0), x.size - 1)
+        return float(np.partition(x, k)[k])
 
     return dict(d=d, s_low=q(tau, fa / 2), s_high=q(tau, 1 - fa / 2), gamma=q(r, 1 - fa),
                 eps=eps)

@@ -19,6 +19,7 @@
 #include "rfi_device.cuh"
 #include "rfi_internal.h"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,30 +34,89 @@ namespace {
 // The carry of the open averaging bin: float[R][1][9].
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RFI_NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch, looked up once per device (with that device
-// current).  In host code the symbol is only a host-side stand-in, never a device
-// address, so the kernel must receive the looked-up pointer.
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-void *g_scratch_addr[MAX_DEVICES] = {};
+// Device address of g_noalloc_scratch.  In host code the symbol is only a host-side
+// stand-in, never a device address, so the kernel must receive the looked-up pointer.
+// The address belongs to the CUDA context whose copy of this module it came from: the
+// device's primary context, or a context the caller made current with the driver API,
+// and after cudaDeviceReset a new primary context with a new copy.  So the lookup is
+// cached per context, keyed by the context's unique id (cuCtxGetId, never reused in a
+// process), and repeated for a context not seen before.
+typedef CUresult (*PFN_ctx_current)(CUcontext *);
+typedef CUresult (*PFN_ctx_id)(CUcontext, unsigned long long *);
 
-int scratch_for(int device, void **out) {
-    if (device < 0 || device >= MAX_DEVICES)
-        return rfi_internal_fail(RFI_EUNSUPPORTED, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[device]) {
+struct CtxFns {
+    PFN_ctx_current current = nullptr;
+    PFN_ctx_id id = nullptr;
+};
+
+const CtxFns &ctx_fns() {
+    static CtxFns f;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            char msg[200];
-            snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the no-alloc scratch failed: %s",
-                     cudaGetErrorString(e));
-            return rfi_internal_fail(RFI_ECUDA, msg);
-        }
-        g_scratch_addr[device] = p;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            f.current = reinterpret_cast<PFN_ctx_current>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            f.id = reinterpret_cast<PFN_ctx_id>(p);
+    });
+    return f;
+}
+
+// Id of the calling thread's current context; false when there is none yet (the
+// runtime creates the device's primary context on its first call that needs one).
+bool current_ctx_id(unsigned long long *id) {
+    const CtxFns &f = ctx_fns();
+    CUcontext c = nullptr;
+    return f.current && f.id && f.current(&c) == CUDA_SUCCESS && c != nullptr &&
+           f.id(c, id) == CUDA_SUCCESS;
+}
+
+constexpr int MAX_CONTEXTS = 64;
+std::mutex g_mu;
+unsigned long long g_ctx_id[MAX_CONTEXTS] = {};
+void *g_ctx_addr[MAX_CONTEXTS] = {};
+int g_n_ctx = 0;
+
+int lookup_symbol(void **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        char msg[200];
+        snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the no-alloc scratch failed: %s",
+                 cudaGetErrorString(e));
+        return rfi_internal_fail(RFI_ECUDA, msg);
     }
-    *out = g_scratch_addr[device];
+    *out = p;
+    return RFI_OK;
+}
+
+// The scratch's device address in the calling thread's current context (the current
+// device's primary context unless the caller made another current).
+int scratch_for_current_context(void **out) {
+    unsigned long long id = 0;
+    if (!current_ctx_id(&id)) {
+        // no context yet, or no way to tell contexts apart: look the address up (this
+        // also creates the primary context) and cache it under the context now current
+        int rc = lookup_symbol(out);
+        if (rc || !current_ctx_id(&id)) return rc;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int i = 0; i < g_n_ctx; ++i)
+        if (g_ctx_id[i] == id) {
+            *out = g_ctx_addr[i];
+            return RFI_OK;
+        }
+    void *p = nullptr;
+    if (int rc = lookup_symbol(&p)) return rc;
+    const int slot = g_n_ctx < MAX_CONTEXTS ? g_n_ctx++ : (int)(id % MAX_CONTEXTS);
+    g_ctx_id[slot] = id;
+    g_ctx_addr[slot] = p;
+    *out = p;
     return RFI_OK;
 }
 
@@ -109,6 +169,7 @@ extern "C" int rfi_process_block_noalloc(int stations, int channels, int window_
         return rfi_internal_fail(RFI_EINVAL, "invalid thresholds");
     const long long B = (long long)stations * (stations + 1) / 2;
     const long long R = B * channels;
+    if ((long long)T * R > (1ll << 40)) return rfi_internal_fail(RFI_EINVAL, "block too large");
     const unsigned long long carry_bytes = (unsigned long long)R * 9 * sizeof(float);
     if (carry_bytes > RFI_NOALLOC_SCRATCH_BYTES) {
         snprintf(msg, sizeof msg,
@@ -139,7 +200,7 @@ extern "C" int rfi_process_block_noalloc(int stations, int channels, int window_
          (rc = rfi_internal_check_dev(weight, (size_t)R * n_out * 4, 4, device, "weight"))))
         return rc;
     void *scratch = nullptr;
-    if ((rc = scratch_for(device, &scratch))) return rc;
+    if ((rc = scratch_for_current_context(&scratch))) return rc;
 
     // The kernel reads the carry only when this block continues an open bin
     // (n_seen % K != 0); that carry was written by the previous call for the same

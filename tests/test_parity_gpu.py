@@ -182,7 +182,7 @@ def test_lofar_scale_sampled_rows(dtype, M):
     if dtype == "f16":      # against the unrounded input: binary16 quantisation, reported
         o32 = oracle.OracleStream(len(rows), M, K, **thr).process(v)
         rep32 = compare(gs, o32, thr, M, K, stat_rtol=None, avg_rtol=None, check_flags=False)
-        assert rep32["flag_disagree_frac"] <= 2e-3, rep32
+        assert rep32["flag_disagree_frac"] <= 1e-3, rep32      # spec bound: 0.1 %
         print(f"lofar f16 M={M} vs float32 input", rep32)
     st.close()
 
