@@ -109,6 +109,18 @@ typedef enum {
  *                  binary32, every operation rounded in the tables' order, eps =
  *                  2^-10 inside binary16 groups; one lane per row, time-only windows,
  *                  no Kahan.  Statistics are then binary16 values.
+ *                  2 = binary16 arithmetic for binary16 input (RFI_C32H): the Stokes
+ *                  parameters are formed in binary16 (half2 adds, round to nearest even);
+ *                  every later product multiplies two binary16 values (exact in
+ *                  float32) and every sum is float32 (S1, S2 with Kahan as usual, the
+ *                  polarisation-vector sums, the averaging sums); the polarisation
+ *                  vector is normalised by 1/sqrt(q^2 + u^2 + v^2 + eps^2).  Each Stokes
+ *                  component carries one binary16 rounding (relative 2^-11), which
+ *                  bounds the statistics' error (|d tau| <~ 4 2^-11 (|tau| + (Md+1)/
+ *                  (M-1)), |d r| <~ 2 2^-11) and that of the averages (2^-11 of the
+ *                  magnitudes averaged).  Direct loader, 128-register budget, plain
+ *                  stores, no prefetch, partial windows or adaptive thresholds; any
+ *                  lanes_per_row, lane_split and window_F.
  *   loader         0 = direct 32-byte global loads (default).  1 = the rows are
  *                  staged in shared memory a few windows at a time by cp.async.bulk
  *                  (TMA) copies, one per row and stage issued by the row's first lane,

@@ -144,7 +144,10 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
         for pg in (1, 2):
             for pb in (512, 1024):
                 o = dict(base, prefetch_groups=pg, prefetch_bytes=pb)
-                t = run(o)
+                try:
+                    t = run(o)
+                except B.RfiError:      # a kernel variant without the prefetch code
+                    continue
                 if t < best_t:
                     best, best_t = o, t
     best = dict(best, seconds=best_t, **fixed)

@@ -17,7 +17,7 @@ SOURCES = ["rfi_api.cu", "rfi_inst_f32.cu", "rfi_inst_f16.cu", "rfi_inst_pw_f32.
            "rfi_inst_pw_f16.cu", "rfi_inst_ad_f32.cu", "rfi_inst_ad_f16.cu", "rfi_inst_pf_f32.cu",
            "rfi_inst_pf_f16.cu", "rfi_inst_tma_f32.cu", "rfi_inst_tma_f16.cu", "rfi_adapt.cu",
            "rfi_noalloc.cu", "rfi_inst_sw_f32.cu", "rfi_inst_sw_f16.cu",
-           "rfi_inst_wp_f32.cu", "rfi_inst_wp_f16.cu"]
+           "rfi_inst_wp_f32.cu", "rfi_inst_wp_f16.cu", "rfi_inst_h2.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

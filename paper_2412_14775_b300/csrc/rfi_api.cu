@@ -45,7 +45,7 @@ const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb,
                               int vs, int pw, int ad, int pf) {
     const InstanceTable tabs[] = {instances_f32(),    instances_f16(),    instances_f32_pw(),
                                   instances_f16_pw(), instances_f32_ad(), instances_f16_ad(),
-                                  instances_f32_pf(), instances_f16_pf()};
+                                  instances_f32_pf(), instances_f16_pf(), instances_f16_h2()};
     for (const InstanceTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const Instance &in = t.items[i];
@@ -81,7 +81,7 @@ const SwInstance *find_sw(int dt, int spu, int P, int ch, int L) {
 }
 
 const WpInstance *find_wp(int dt, int spu, int P, int ch, int mixed) {
-    const WpTable tabs[] = {wp_instances_f32(), wp_instances_f16()};
+    const WpTable tabs[] = {wp_instances_f32(), wp_instances_f16(), wp_instances_f16_h2()};
     for (const WpTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const WpInstance &in = t.items[i];
@@ -136,6 +136,8 @@ struct rfi_ctx {
     int wpb_auto;                       // warps_per_block was left to the library
     int F;                              // channels per window footprint
     int mixed;                          // 1: the paper's trained mixed precision
+    int prec;                           // precision option: 0, 1 (mixed) or 2 (binary16
+                                        // Stokes arithmetic)
     int loader;                         // 0: direct loads, 1: TMA staging in shared memory
     const void *tma_fn;
     int tma_G, tma_NS;                  // windows per stage, stages per warp
@@ -273,7 +275,7 @@ int choose_shape(rfi_ctx *c, int P_req) {
         c->ch = largest_chunk(c->S);
         if (c->mixed && c->F != 1)
             return fail(RFI_EINVAL, "precision = 1 supports time-only windows");
-        const WpInstance *wi = find_wp(dt, spu_w, P, c->ch, c->mixed);
+        const WpInstance *wi = find_wp(dt, spu_w, P, c->ch, c->prec);
         c->inst = nullptr;
         if (!wi) return fail(RFI_EUNSUPPORTED, "no window-parallel kernel for this shape");
         c->wp_fn = wi->fn;
@@ -326,9 +328,10 @@ int choose_shape(rfi_ctx *c, int P_req) {
     }
     // the plain 128-register kernels exist with and without the prefetch code; the
     // other kinds always hold it
-    const bool plain = c->lb == 0 && !c->mixed && !c->vs && !c->pw && !c->ad;
-    const int pf = plain ? (c->pf_groups > 0 ? 1 : 0) : 1;
-    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->mixed, c->vs, c->pw, c->ad,
+    const bool plain = c->lb == 0 && !c->prec && !c->vs && !c->pw && !c->ad;
+    // the binary16 Stokes kernels are built without the prefetch code
+    const int pf = plain ? (c->pf_groups > 0 ? 1 : 0) : (c->prec == 2 ? 0 : 1);
+    c->inst = find_instance(dt, spu, P, c->ch, c->kahan, c->lb, c->prec, c->vs, c->pw, c->ad,
                             pf);
     if (c->inst) {
         c->batch_fn = c->inst->batch_fn;
@@ -350,7 +353,7 @@ int choose_shape(rfi_ctx *c, int P_req) {
                                       "arithmetic, the 128-register budget, no Kahan, "
                                       "lanes_per_row <= 4 and 1, 2 or 4 load units per chunk");
     if (c->loader == 1) {
-        c->tma_fn = c->mixed ? nullptr : find_tma(dt, spu, P, c->ch, c->kahan, c->lb);
+        c->tma_fn = c->prec ? nullptr : find_tma(dt, spu, P, c->ch, c->kahan, c->lb);
         if (!c->tma_fn)
             return fail(RFI_EUNSUPPORTED, "no shared-memory loader for this shape (float32 "
                                           "arithmetic, lanes_per_row <= 8, Kahan only with "
@@ -734,7 +737,7 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
         o.compensated < -1 || o.compensated > 1 || o.prefetch_bytes < 0 ||
         o.prefetch_bytes % 16 != 0 || o.prefetch_groups > 64 ||
         (o.max_registers != 0 && o.max_registers < 64) || o.window_F < 0 || o.precision < 0 ||
-        o.precision > 1 || o.loader < 0 || o.loader > 1 || o.tma_stage_windows < 0 ||
+        o.precision > 2 || o.loader < 0 || o.loader > 1 || o.tma_stage_windows < 0 ||
         o.tma_stage_windows > 64 || o.tma_stages < 0 || o.tma_stages > 8 ||
         o.debug_inject_wait_timeout < 0 || o.debug_inject_wait_timeout > 1 ||
         o.overlap_bytes < -1 || (o.overlap_bytes > 0 && o.overlap_bytes % 128 != 0) ||
@@ -764,7 +767,8 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->wpb_auto = o.warps_per_block == 0;
     c->lb = o.max_registers == 0 || o.max_registers >= 128 ? 0 : (o.max_registers >= 80 ? 1 : 2);
     c->F = o.window_F ? o.window_F : 1;
-    c->mixed = o.precision;
+    c->mixed = o.precision == 1;
+    c->prec = o.precision;
     c->loader = o.loader;
     c->tma_G = o.tma_stage_windows ? o.tma_stage_windows : 1;
     c->tma_NS = o.tma_stages ? o.tma_stages : 2;
@@ -785,6 +789,15 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
             return fail(RFI_EINVAL, "precision = 1 has no Kahan or register-budget variants");
         }
         c->kahan = 0;
+    }
+    if (c->prec == 2 && (dtype != RFI_C32H || c->lb != 0 || o.loader != 0 ||
+                         o.buffered_stores != 0 || o.partial_windows != 0 || o.adaptive != 0 ||
+                         o.prefetch_groups > 0)) {
+        delete c;
+        return fail(RFI_EUNSUPPORTED, "precision = 2 needs binary16 input (RFI_C32H), the "
+                                      "direct loader and the 128-register budget, without "
+                                      "buffered stores, partial windows, adaptive thresholds "
+                                      "or prefetch");
     }
     if (c->F & (c->F - 1) || c->F > 32 || channels % c->F != 0 || c->M * c->F < 2) {
         delete c;
@@ -811,7 +824,7 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     }
     if (c->wp) c->kahan = 0;
     if (c->sw) {
-        if (c->F != 1 || c->mixed || c->loader != 0 || c->lb != 0 || c->vs || c->pw || c->ad ||
+        if (c->F != 1 || c->prec || c->loader != 0 || c->lb != 0 || c->vs || c->pw || c->ad ||
             o.compensated == 1) {
             delete c;
             return fail(RFI_EUNSUPPORTED, "overlapping windows need time-only windows, float32 "
@@ -936,7 +949,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->prefetch_groups = ctx->pf_groups;
     opt->max_registers = ctx->lb == 0 ? 128 : (ctx->lb == 1 ? 80 : 64);
     opt->window_F = ctx->F;
-    opt->precision = ctx->mixed;
+    opt->precision = ctx->prec;
     opt->loader = ctx->loader;
     opt->tma_stage_windows = ctx->tma_G;
     opt->tma_stages = ctx->tma_NS;
@@ -1181,7 +1194,7 @@ namespace {
 struct StateHeader {
     unsigned int magic, version;
     long long R, n_seen;
-    int P, M, K, F, dtype, pw, ad, hop, split, pad;
+    int P, M, K, F, dtype, pw, ad, hop, split, prec;
     rfi_thresholds thr;
     rfi_adaptation adp;
 };
@@ -1221,6 +1234,7 @@ int rfi_get_state(rfi_ctx *ctx, void *buf, size_t bytes, void *stream) {
     h.K = ctx->K;
     h.F = ctx->F;
     h.dtype = (int)ctx->dtype;
+    h.prec = ctx->prec;
     h.thr = ctx->thr;
     std::memcpy(buf, &h, sizeof h);
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
@@ -1252,7 +1266,7 @@ int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes) {
         return fail(RFI_EINVAL, "not a saved stream state");
     if (h.R != ctx->R || h.P != ctx->P || h.M != ctx->M || h.K != ctx->K || h.F != ctx->F ||
         h.pw != ctx->pw || h.ad != ctx->ad || h.dtype != (int)ctx->dtype || h.hop != ctx->H ||
-        h.split != ctx->wp)
+        h.split != ctx->wp || h.prec != ctx->prec)
         return fail(RFI_EINVAL, "saved state is for another geometry or launch shape "
                                 "(rows %lld, lanes %d, M %d, K %d, F %d, partial windows %d, "
                                 "adaptive %d, hop %d)",

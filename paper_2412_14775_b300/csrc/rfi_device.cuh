@@ -102,6 +102,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // L2 prefetch of the 128-byte line holding p: a per-thread hint (no register, no wait,
 // no memory clobber).  The bulk form (cp.async.bulk.prefetch.L2) takes warp-uniform
@@ -305,6 +310,52 @@ __device__ __forceinline__ void accumulate(WinAcc &A, const Stokes &x, float2 ep
     A.a[3] = add2(A.a[3], V);
 }
 
+// ---- binary16 Stokes arithmetic (precision = 2) ----------------------------------
+// The Stokes parameters of a binary16 sample are formed in binary16 (half2 adds and
+// subtracts, round to nearest even: Eq. IQUV in the input's own precision).  Every
+// product after that multiplies two binary16 values, which is exact in float32, and
+// every sum is float32: S1 and S2 (Table 1 groups 3-4, Kahan when enabled), the
+// polarisation-vector sums (Table 2 group 4) and the averaging sums.  The normalisation
+// is q / sqrt(q^2 + u^2 + v^2 + eps^2) (one reciprocal square root per part instead of
+// a square root, eps and a reciprocal; it differs from q / (sqrt(...) + eps) by a
+// relative eps / |(q, u, v)|, below binary16 rounding for vectors longer than 2^-12,
+// and a zero vector still contributes 0).  V is carried as (Re V, -Im V), the swapped
+// halves of yx - xy: r depends on the squares of the resultant's components only, and
+// a closed bin's averages undo the sign.
+__device__ __forceinline__ __half2 as_h2(uint32_t w) { return *reinterpret_cast<const __half2 *>(&w); }
+
+template <bool KAHAN>
+__device__ __forceinline__ void accumulate_h2(WinAcc &A, const uint32_t *w, float e2) {
+    const __half2 xx = as_h2(w[0]), xy = as_h2(w[1]), yx = as_h2(w[2]), yy = as_h2(w[3]);
+    const float2 I = __half22float2(__hadd2(xx, yy));
+    const float2 Q = __half22float2(__hsub2(xx, yy));
+    const float2 U = __half22float2(__hadd2(xy, yx));
+    const float2 V = __half22float2(__lowhigh2highlow(__hsub2(yx, xy)));   // (Re V, -Im V)
+    const float2 I2 = mul2(I, I);
+    const float y = I2.x + I2.y;                             // |I|^2
+    const float z = sqrt_approx(y);                          // |I|
+    if constexpr (KAHAN) {
+        const float2 yk = sub2(make_float2(z, y), A.c);
+        const float2 t = add2(A.s, yk);
+        A.c = sub2(sub2(t, A.s), yk);
+        A.s = t;
+    } else {
+        A.s = add2(A.s, make_float2(z, y));
+    }
+    float2 n = mul2(Q, Q);                                   // q^2 + u^2 + v^2 (+ eps^2)
+    n = fma2(U, U, n);
+    n = fma2(V, V, n);
+    n = add2(n, make_float2(e2, e2));
+    const float2 ip = make_float2(rsqrt_approx(n.x), rsqrt_approx(n.y));
+    A.q = fma2(Q, ip, A.q);
+    A.u = fma2(U, ip, A.u);
+    A.v = fma2(V, ip, A.v);
+    A.a[0] = add2(A.a[0], I);
+    A.a[1] = add2(A.a[1], Q);
+    A.a[2] = add2(A.a[2], U);
+    A.a[3] = add2(A.a[3], V);
+}
+
 // ---- paper-mixed precision (Tables 3 and 4) -----------------------------------
 // Binary16 values are carried in float registers; h16 rounds a float32 result to the
 // nearest binary16 (ties to even).  Binary32 groups use correctly rounded operations
@@ -405,8 +456,10 @@ __device__ __forceinline__ void store_bin(const StreamArgs &a, long long row, in
 // CH: load units issued together per lane; KAHAN: compensated S1, S2.
 // DB: double-buffered loads (two chunks in flight per lane) or one chunk at a time
 // (fewer registers, more resident warps).  The arithmetic is the same either way.
-// MIXED: the paper's trained mixed precision (Tables 3 and 4; one lane per row, no
-// footprint, no Kahan), else float32 arithmetic throughout.
+// PREC: 0 = float32 arithmetic throughout (binary16 input widened exactly); 1 = the
+// paper's trained mixed precision (Tables 3 and 4; one lane per row, no footprint, no
+// Kahan); 2 = binary16 Stokes parameters, exact products and float32 sums
+// (accumulate_h2; binary16 input).
 // TMA: every lane owns one row (P = 1) and reads it from shared memory, where the
 // warp's rows are staged a few windows at a time by cp.async.bulk copies (one per row,
 // issued by the row's lane) that complete on one mbarrier per stage.
@@ -429,11 +482,13 @@ __device__ __forceinline__ void store_bin(const StreamArgs &a, long long row, in
 // plain kernels come with and without it, since its mere presence changes how the
 // compiler schedules the window loop.
 // BAT: called from the persistent batch kernel (see the footprint sums below).
-template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, bool MIXED = false,
+template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, int PREC = 0,
           bool TMA = false, bool VS = false, bool PW = false, bool AD = false,
           bool PFT = false, bool BAT = false>
 __device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
+    constexpr bool MIXED = PREC == 1, H2 = PREC == 2;
     static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
+    static_assert(!H2 || DT == DT_F16, "binary16 Stokes arithmetic needs binary16 input");
     constexpr int RW = 32 / P;
     constexpr int SB = (DT == DT_F32) ? 32 : 16;   // bytes per sample
     constexpr int UB = SB * SPU;                   // bytes per load unit
@@ -510,6 +565,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
     int pf_next = a.pf_windows;
 
     const float2 eps2 = make_float2(a.eps, a.eps);
+    const float e2 = a.eps * a.eps;
     // The load units of a lane form one contiguous stream over the row: chunk q (CH
     // units) starts at rp + j*UB + q*CHB.  Two register buffers let the loads of chunk
     // q+1 be in flight while chunk q is consumed.
@@ -570,6 +626,8 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
             for (int k = 0; k < SPU; ++k) {
                 if constexpr (MIXED)
                     accumulate_mixed(A, stokes_of<DT, UB>(u[c], k), a.eps);
+                else if constexpr (H2)
+                    accumulate_h2<KAHAN>(A, &u[c].r[4 * k], e2);
                 else
                     accumulate<KAHAN>(A, stokes_of<DT, UB>(u[c], k), eps2);
             }
@@ -693,6 +751,7 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
 #pragma unroll
             for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
             const float n = allsum<P>(cnt);
+            if constexpr (H2) tot[7] = -tot[7];      // V was carried as (Re V, -Im V)
             if (lead) store_bin(a, row, bin, tot, n);
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = 0.f;
@@ -858,7 +917,7 @@ template <> struct Bounds<0> { static constexpr int threads = 512, blocks = 1; }
 template <> struct Bounds<1> { static constexpr int threads = 256, blocks = 3; };
 template <> struct Bounds<2> { static constexpr int threads = 256, blocks = 4; };
 
-template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, bool MIXED = false,
+template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, int PREC = 0,
           bool VS = false, bool PW = false, bool AD = false, bool PFT = false>
 __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_block(const __grid_constant__ StreamArgs a) {
@@ -868,7 +927,7 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     overlap_prologue<DT, P>(a, group);
     // the 128-register budget keeps two chunks in flight; tighter budgets load one
     // chunk at a time and rely on more resident warps instead
-    process_group<DT, SPU, P, CH, KAHAN, LB == 0, MIXED, false, VS, PW, AD, PFT>(a, group);
+    process_group<DT, SPU, P, CH, KAHAN, LB == 0, PREC, false, VS, PW, AD, PFT>(a, group);
 }
 
 // P lanes per row, rows staged in shared memory by TMA bulk copies; dynamic shared
@@ -920,12 +979,12 @@ __device__ __forceinline__ void run_batch_tasks(const BatchArgs &b, Task &&task)
     }
 }
 
-template <int DT, int SPU, int P, int CH, bool KAHAN, bool MIXED = false, bool PW = false,
+template <int DT, int SPU, int P, int CH, bool KAHAN, int PREC = 0, bool PW = false,
           bool AD = false, bool PFT = false>
 __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchArgs b) {
     run_batch_tasks(b, [](const StreamArgs &a, long long group) {
-        process_group<DT, SPU, P, CH, KAHAN, true, MIXED, false, false, PW, AD, PFT, true>(a,
-                                                                                       group);
+        process_group<DT, SPU, P, CH, KAHAN, true, PREC, false, false, PW, AD, PFT, true>(a,
+                                                                                      group);
     });
 }
 

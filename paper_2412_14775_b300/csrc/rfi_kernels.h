@@ -8,7 +8,7 @@
 namespace rfi {
 
 struct Instance {
-    int dt, spu, P, ch, kahan, lb, mixed, vs, pw, ad, pf;
+    int dt, spu, P, ch, kahan, lb, mixed, vs, pw, ad, pf;   // mixed: the precision mode
     const void *block_fn;   // k_block<...>
     const void *batch_fn;   // k_batch<...>; the register budget, the buffered stores and
                             // the prefetch do not change results, so all those share the
@@ -28,6 +28,7 @@ InstanceTable instances_f32_ad();     // online SK thresholds (rfi_inst_ad_f32.c
 InstanceTable instances_f16_ad();     // online SK thresholds (rfi_inst_ad_f16.cu)
 InstanceTable instances_f32_pf();     // plain kernels with L2 prefetch (rfi_inst_pf_f32.cu)
 InstanceTable instances_f16_pf();     // plain kernels with L2 prefetch (rfi_inst_pf_f16.cu)
+InstanceTable instances_f16_h2();     // binary16 Stokes arithmetic (rfi_inst_h2.cu)
 // State update of adaptive contexts after a flagging launch (rfi_adapt.cu): one thread
 // per footprint row; k_adapt takes a StreamArgs, k_adapt_batch a BatchArgs.
 const void *adapt_fn();
@@ -71,6 +72,7 @@ struct WpTable {
 };
 WpTable wp_instances_f32();   // rfi_inst_wp_f32.cu
 WpTable wp_instances_f16();   // rfi_inst_wp_f16.cu
+WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
 
 }  // namespace rfi
 
@@ -190,3 +192,19 @@ WpTable wp_instances_f16();   // rfi_inst_wp_f16.cu
 #define RFI_WPM_CH(DT, SPU, P)                                                              \
     RFI_WPM(DT, SPU, P, 1), RFI_WPM(DT, SPU, P, 2), RFI_WPM(DT, SPU, P, 4),                  \
         RFI_WPM(DT, SPU, P, 5)
+
+// Binary16 Stokes arithmetic (precision = 2; binary16 input), 128-register budget,
+// without the prefetch code; a batch of such contexts runs its own batch kernel.
+#define RFI_INSTH(DT, SPU, P, CH, K)                                                        \
+    {DT, SPU, P, CH, K, 0, 2, 0, 0, 0, 0,                                                   \
+     (const void *)&rfi::k_block<DT, SPU, P, CH, (bool)K, 0, 2>,                            \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, (bool)K, 2, false, false, true>}
+#define RFI_INSTH_CH(DT, SPU, P, K)                                                         \
+    RFI_INSTH(DT, SPU, P, 1, K), RFI_INSTH(DT, SPU, P, 2, K), RFI_INSTH(DT, SPU, P, 4, K),  \
+        RFI_INSTH(DT, SPU, P, 5, K)
+#define RFI_WPH(DT, SPU, P, CH)                                                             \
+    {DT, SPU, P, CH, 2, (const void *)&rfi::k_wpar<DT, SPU, P, CH, 2>,                      \
+     (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, 2>}
+#define RFI_WPH_CH(DT, SPU, P)                                                              \
+    RFI_WPH(DT, SPU, P, 1), RFI_WPH(DT, SPU, P, 2), RFI_WPH(DT, SPU, P, 4),                  \
+        RFI_WPH(DT, SPU, P, 5)

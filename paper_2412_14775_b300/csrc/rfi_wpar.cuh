@@ -19,12 +19,15 @@
 
 namespace rfi {
 
-// MIXED: the paper's trained mixed precision (Tables 3 and 4): each window is still
+// PREC 1: the paper's trained mixed precision (Tables 3 and 4): each window is still
 // summed sample by sample in one lane, in the tables' order, so statistics and flags
 // are those of the one-lane-per-row mixed kernel bit for bit (time-only windows).
-template <int DT, int SPU, int P, int CH, bool MIXED = false>
+// PREC 2: binary16 Stokes arithmetic (accumulate_h2), as in process_group.
+template <int DT, int SPU, int P, int CH, int PREC = 0>
 __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long group) {
+    constexpr bool MIXED = PREC == 1, H2 = PREC == 2;
     static_assert(P >= 2, "one lane per row is the plain kernel");
+    static_assert(!H2 || DT == DT_F16, "binary16 Stokes arithmetic needs binary16 input");
     constexpr int RW = 32 / P;
     constexpr int SB = (DT == DT_F32) ? 32 : 16;
     constexpr int UB = SB * SPU;
@@ -75,6 +78,7 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
     uint32_t fword = 0;
     const int nbits = a.T;
     const float2 eps2 = make_float2(a.eps, a.eps);
+    const float e2 = a.eps * a.eps;
 
     // the lane's load stream: chunk c of round k reads units c*CH .. c*CH + CH-1 of its
     // window kP - s + j (nothing for a window outside this launch)
@@ -103,6 +107,8 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
             for (int k = 0; k < SPU; ++k) {
                 if constexpr (MIXED)
                     accumulate_mixed(A, stokes_of<DT, UB>(u[c], k), a.eps);
+                else if constexpr (H2)
+                    accumulate_h2<false>(A, &u[c].r[4 * k], e2);
                 else
                     accumulate<false>(A, stokes_of<DT, UB>(u[c], k), eps2);
             }
@@ -205,6 +211,7 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
 #pragma unroll
             for (int c = 0; c < 8; ++c) tot[c] = allsum<P>(acc[c]);
             const float n = allsum<P>(cnt);
+            if constexpr (H2) tot[7] = -tot[7];      // V was carried as (Re V, -Im V)
             if (lead) store_bin(a, row, bin, tot, n);
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = 0.f;
@@ -248,20 +255,20 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
     }
 }
 
-template <int DT, int SPU, int P, int CH, bool MIXED = false>
+template <int DT, int SPU, int P, int CH, int PREC = 0>
 __global__ void __launch_bounds__(512, 1) k_wpar(const __grid_constant__ StreamArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     overlap_prologue<DT, P>(a, group);
-    process_group_wp<DT, SPU, P, CH, MIXED>(a, group);
+    process_group_wp<DT, SPU, P, CH, PREC>(a, group);
 }
 
 // The persistent batch over window-parallel contexts (same task loop as k_batch).
-template <int DT, int SPU, int P, int CH, bool MIXED = false>
+template <int DT, int SPU, int P, int CH, int PREC = 0>
 __global__ void __launch_bounds__(512, 1) k_batch_wp(const __grid_constant__ BatchArgs b) {
     run_batch_tasks(b, [](const StreamArgs &a, long long group) {
-        process_group_wp<DT, SPU, P, CH, MIXED>(a, group);
+        process_group_wp<DT, SPU, P, CH, PREC>(a, group);
     });
 }
 

@@ -125,3 +125,75 @@ def compare(gpu, orc, thr, M, K, n_seen=0, stat_rtol=STAT_RTOL, avg_rtol=AVG_RTO
             assert np.allclose(gpu["weight"][ok], orc["weight"][ok], rtol=1.2e-7, atol=0), \
                 "weights differ"
     return rep
+
+
+# ---- binary16 Stokes arithmetic (precision = 2) ----------------------------------
+# Each Stokes component is one binary16 rounding (relative u = 2^-11) of the exact sum
+# of two binary16 inputs; everything after it is exact products and float32 sums.  So:
+#   |I| is off by at most u relative, S1 by u and S2 by 2u, and t = W S2/S1^2 by 4u:
+#     |d tau| <= 4u (tau + c0) (tau + c0 = c0 t >= 0, c0 = (Wd+1)/(W-1));
+#   each unit polarisation vector moves by at most 2u (a relative u error per
+#     component), so |d r| <= 2u (plus the normalisation's eps^2 form, negligible for
+#     vectors longer than 2^-12, and the float32 terms);
+#   an averaged correlation xx = (I + Q)/2 is off by at most u (|I| + |Q|)/2 <=
+#     u (|xx| + |yy|) per re/im part per sample (xy, yx: u (|xy| + |yx|)).
+# The float32 path's own tolerance (STAT_RTOL, AVG_RTOL) is added to each bound.
+U16 = 2.0 ** -11
+
+
+def _pair_bound(vis_rows, keep, K, n_out):
+    """u * mean over a bin's unflagged samples of |a| + |b| for the pair of correlations
+    each output component mixes ((xx, yy) or (xy, yx), same re/im part): [R, n_out, 8]
+    (bins counted from the block's first sample)."""
+    x = np.abs(vis_rows)                                   # [R, T, 8]
+    pair = np.empty_like(x)
+    for a, b in ((0, 6), (1, 7), (2, 4), (3, 5)):
+        pair[..., a] = pair[..., b] = x[..., a] + x[..., b]
+    out = np.zeros((x.shape[0], n_out, 8))
+    for b in range(n_out):
+        k = keep[:, b * K:(b + 1) * K, None]
+        n = np.maximum(k.sum(axis=1), 1)
+        out[:, b] = U16 * (pair[:, b * K:(b + 1) * K] * k).sum(axis=1) / n
+    return out
+
+
+def compare_h2(gpu, orc, vis_rows, thr, M, K, F=1):
+    """Assert the bounds above for one block that starts a stream (n_seen = 0);
+    vis_rows [R, T, 8] are the binary16 input values as float64.  Returns the worst
+    errors relative to each bound and the flag disagreement."""
+    W = M * F
+    c0 = (W * thr["d"] + 1.0) / (W - 1.0)
+    rep = {}
+    b_tau = 4.02 * U16 * np.maximum(orc["tau"] + c0, 0.0) + STAT_RTOL * np.maximum(np.abs(orc["tau"]), 1.0)
+    b_r = {k: 2.5 * U16 + STAT_RTOL * np.maximum(orc[k], W ** -0.5) for k in ("r_re", "r_im")}
+    for key, bound in (("tau", b_tau), ("r_re", b_r["r_re"]), ("r_im", b_r["r_im"])):
+        err = np.abs(gpu[key] - orc[key])
+        rep[key + "_abs"] = float(err.max()) if err.size else 0.0
+        rep[key + "_of_bound"] = float((err / bound).max()) if err.size else 0.0
+        assert np.all(err <= bound), f"{key}: error {rep[key + '_abs']:.3g} beyond its bound"
+    T = gpu["tau"].shape[1] * M
+    wflag = expand_window_flags(gpu["flagbits"], M, T)
+    self_rule = np.repeat(flag_rule_f32(gpu["tau"], gpu["r_re"], gpu["r_im"], thr), F, axis=0)
+    assert np.array_equal(wflag, self_rule), "packed flags disagree with the GPU's own statistics"
+    # windows whose oracle statistic lies within its bound of a threshold may flip
+    near = ((np.abs(orc["tau"] - thr["s_low"]) <= b_tau) | (np.abs(orc["tau"] - thr["s_high"]) <= b_tau) |
+            (np.abs(orc["r_re"] - thr["gamma"]) <= b_r["r_re"]) |
+            (np.abs(orc["r_im"] - thr["gamma"]) <= b_r["r_im"]))
+    near = np.repeat(near, F, axis=0)
+    diff = wflag != np.repeat(orc["wflag"].astype(bool), F, axis=0)
+    assert not (diff & ~near).any(), "window flags differ outside the error bounds"
+    rep["flag_disagree_frac"] = float(diff.mean()) if diff.size else 0.0
+    n_out = gpu["weight"].shape[1]
+    rep["avg_of_bound"] = 0.0
+    if n_out:
+        keep = ~np.repeat(np.repeat(orc["wflag"].astype(bool), F, axis=0), M, axis=1)
+        bnd = _pair_bound(vis_rows, keep, K, n_out) + AVG_RTOL * np.maximum(np.abs(orc["avg"]), 1.0)
+        wpb = K // M
+        ok = np.ones((wflag.shape[0], n_out), bool)
+        for b in range(n_out):
+            ok[:, b] = ~(near[:, b * wpb:(b + 1) * wpb].any(axis=1) | diff[:, b * wpb:(b + 1) * wpb].any(axis=1))
+        err = np.abs(gpu["avg"] - orc["avg"])
+        assert np.all(err[ok] <= bnd[ok]), "averages beyond their bound"
+        rep["avg_of_bound"] = float((err[ok] / bnd[ok]).max()) if ok.any() else 0.0
+        assert np.allclose(gpu["weight"][ok], orc["weight"][ok], rtol=1.2e-7, atol=0)
+    return rep
