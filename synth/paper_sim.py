@@ -18,7 +18,10 @@ One baseline, a time x frequency block (the paper uses 2000 x 512, about 1 s x
 * the interference is scaled so that its total power over the block divided by the
   total power of the sky signal (noise plus sources) equals the requested INR.
 
-Returns float32 visibilities [channels, T, 4, 2] and the boolean truth mask [channels, T].
+Returns float32 visibilities [channels, T, 4, 2], the boolean truth mask [channels, T]
+and the drawn parameters (receiver-noise scale, baseline u, v, w, source positions and
+fluxes, the per-channel source coherence, every interferer's footprint and J, the
+interference scale).
 """
 import math
 
@@ -53,7 +56,8 @@ def simulate_block(seed, T=2000, C=512, inr=100.0, polarised=True, n_broadband=5
     xp = _cgauss(rng, (C, T, 2))
     xq = _cgauss(rng, (C, T, 2))
     recv = xp[..., :, None] * np.conj(xq[..., None, :])          # [C, T, 2, 2]
-    sky = recv * (100.0 * rng.uniform()) + _cgauss(rng, (C, T, 2, 2))
+    recv_scale = 100.0 * rng.uniform()
+    sky = recv * recv_scale + _cgauss(rng, (C, T, 2, 2))
     # point sources (unpolarised, constant in time)
     u, v, w = 300.0 * rng.standard_normal(3)
     l = rng.uniform(-0.5, 0.5, n_sources)
@@ -68,11 +72,14 @@ def simulate_block(seed, T=2000, C=512, inr=100.0, polarised=True, n_broadband=5
     # interference
     rfi = np.zeros_like(sky)
     truth = np.zeros((C, T), bool)
+    emitters = []          # (kind, channel span, time span, J) of every interferer
     for _ in range(n_broadband):
         t0 = int(rng.integers(0, T)); t1 = min(T, t0 + int(rng.integers(2, max(3, T // 20))))
         c0 = int(rng.integers(0, C)); c1 = min(C, c0 + int(rng.integers(1, max(2, C // 8))))
-        rfi[c0:c1, t0:t1] += _polarisation(rng, polarised)
+        J = _polarisation(rng, polarised)
+        rfi[c0:c1, t0:t1] += J
         truth[c0:c1, t0:t1] = True
+        emitters.append(("broadband", (c0, c1), (t0, t1), J))
     for k in range(n_narrow):
         J = _polarisation(rng, polarised)
         if k % 2 == 0:     # narrowband: one channel, a complex exponential over a time span
@@ -82,6 +89,7 @@ def simulate_block(seed, T=2000, C=512, inr=100.0, polarised=True, n_broadband=5
             tt = np.arange(t0, t1)
             rfi[c, t0:t1] += np.exp(2j * np.pi * tt / period)[:, None, None] * J
             truth[c, t0:t1] = True
+            emitters.append(("narrowband", (c, c + 1), (t0, t1), J))
         else:              # narrow duration: one time, a complex exponential over channels
             t = int(rng.integers(0, T))
             c0 = int(rng.integers(0, C)); c1 = min(C, c0 + int(rng.integers(C // 10, C // 2)))
@@ -89,6 +97,7 @@ def simulate_block(seed, T=2000, C=512, inr=100.0, polarised=True, n_broadband=5
             cc = np.arange(c0, c1)
             rfi[c0:c1, t] += np.exp(2j * np.pi * cc / period)[:, None, None] * J
             truth[c0:c1, t] = True
+            emitters.append(("narrow_duration", (c0, c1), (t, t + 1), J))
     p_rfi = float(np.sum(np.abs(rfi) ** 2))
     p_sky = float(np.sum(np.abs(sky) ** 2))
     if p_rfi > 0:
@@ -98,4 +107,6 @@ def simulate_block(seed, T=2000, C=512, inr=100.0, polarised=True, n_broadband=5
     out[..., 0] = vis.real
     out[..., 1] = vis.imag
     return dict(vis=out, truth=truth, inr=inr, rfi_power=float(np.sum(np.abs(rfi) ** 2)),
-                sky_power=p_sky)
+                sky_power=p_sky, recv_scale=recv_scale, uvw=(u, v, w), l=l, m=m, flux=flux,
+                freqs=freqs, source_coherence=coh, emitters=emitters,
+                rfi_scale=math.sqrt(inr * p_sky / p_rfi) if p_rfi > 0 else 0.0)
