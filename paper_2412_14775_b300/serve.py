@@ -1,23 +1,31 @@
 """Continuous-batching serving loop over many correlator streams.
 
 Streams (subbands of different station and channel counts) deliver blocks at their
-own Poisson rates.  Each stream owns a flagging context whose state (averaging
-carry, thresholds) stays on the device between blocks.  The loop
+own Poisson rates.  Each stream owns a flagging context whose state (averaging carry,
+thresholds, open windows) stays on the device between blocks.  The loop
 
-  * queues every arrived block (blocks of one stream are processed in order, one at
-    a time, because each block continues the previous block's averaging bin);
-  * admits queued blocks while the HBM budget for blocks in flight (input + outputs)
-    and the batch slots allow, oldest arrival first;
-  * launches each batch of admitted blocks as ONE persistent kernel
-    (rfi_process_batch) on one of several CUDA streams, so batches admitted while
-    others are still running overlap on the device;
-  * retires batches as their CUDA events complete, releasing memory and streams.
+  * allocates, once, a device block pool sized from the GPU's free memory (minus a
+    headroom) and the caller's budget; every admitted block takes one slot of it
+    (input block + its outputs, first fit, 256-byte aligned) until it retires;
+  * queues every arrived block (blocks of one stream are processed in order, one at a
+    time, because each block continues the previous block's averaging bin);
+  * admits queued blocks, oldest arrival first, while pool slots and batch slots
+    allow;
+  * per batch, on one of several CUDA streams: copies each admitted block into its
+    slot (from pinned host memory, `source="host"`, or from the producer's device
+    buffer, `source="device"`, as a correlator that writes its output on the GPU),
+    runs ONE persistent kernel over all of them (rfi_process_batch), and copies each
+    block's flags, averages and weights (one contiguous range of its slot) back to
+    pinned host memory (the per-window statistics stay on the device); batches
+    admitted while others run overlap on the device;
+  * retires batches as their CUDA events complete, releasing their slots.
 
-Block latency = device completion time - arrival time (both on the loop's clock:
-the device clock is tied to the host clock by an event recorded at start).
-Everything computed runs in the library's kernels; this module only schedules.
+Block latency = completion of the batch's last copy (device clock) - arrival time
+(host clock), the clocks tied by an event recorded at start.  Everything computed runs
+in the library's kernels; this module schedules, copies and keeps the books.
 """
 import collections
+import math
 import statistics
 import time
 
@@ -26,68 +34,131 @@ import numpy as np
 from . import binding as B
 from .stream import RfiStream
 
+_ALIGN = 256
+
+
+class DevicePool:
+    """One device allocation carved into slots: first fit over a sorted free list,
+    neighbours merged on release, every slot aligned to 256 bytes."""
+
+    def __init__(self, nbytes, device):
+        import torch
+        self.nbytes = int(nbytes) // _ALIGN * _ALIGN
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.free = [(0, self.nbytes)]           # (offset, size), sorted by offset
+        self.used = 0
+        self.peak = 0
+
+    @staticmethod
+    def rounded(n):
+        return (int(n) + _ALIGN - 1) // _ALIGN * _ALIGN
+
+    def alloc(self, n):
+        n = self.rounded(n)
+        for i, (off, size) in enumerate(self.free):
+            if size >= n:
+                if size == n:
+                    del self.free[i]
+                else:
+                    self.free[i] = (off + n, size - n)
+                self.used += n
+                self.peak = max(self.peak, self.used)
+                return off
+        return None
+
+    def release(self, off, n):
+        n = self.rounded(n)
+        self.used -= n
+        i = 0
+        while i < len(self.free) and self.free[i][0] < off:
+            i += 1
+        self.free.insert(i, (off, n))
+        # merge with the right, then the left neighbour
+        if i + 1 < len(self.free) and off + n == self.free[i + 1][0]:
+            self.free[i] = (off, n + self.free[i + 1][1])
+            del self.free[i + 1]
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == off:
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            del self.free[i]
+
+    def view(self, off, nbytes, dtype, shape):
+        return self.buf[off:off + nbytes].view(dtype).view(shape)
+
 
 class _Stream:
-    def __init__(self, idx, cfg, M, K, T, thr, dtype, options, blocks):
+    def __init__(self, idx, cfg, M, K, T, thr, dtype, options, sources):
+        import torch
         self.idx = idx
         self.T = T
         self.cfg = cfg
         self.st = RfiStream(cfg["stations"], cfg["channels"], M, K, thr, dtype, **options)
-        self.blocks = blocks                      # device input blocks, used round robin
+        self.sources = sources                    # arriving blocks (host pinned or device)
         self.queue = collections.deque()          # (arrival_time, seq)
         self.busy = False
         self.done = 0
-        # outputs: a block completes between floor(T/K) and floor(T/K) + 1 averaging
-        # bins and, with partial windows, between floor(T/M) and floor((T + M - 1)/M)
-        # windows (with overlapping windows at most T/H, each adding H flag bits); the
-        # storage is sized for the larger counts and viewed at this block's exact ones
+        R, F = self.st.R, self.st.F
+        bits = self.st.bits_per_window
+        # a block completes between floor(T/K) and floor(T/K) + 1 averaging bins and,
+        # with partial windows, up to ceil(T/M) windows (overlapping windows: T/H, each
+        # adding H flag bits); a slot is sized for the larger counts
+        n_out_max = T // K + 1
+        n_win_max = (T + M - 1) // bits
+        words_max = (n_win_max * bits + 31) // 32
+        src = sources[0]
+        self.in_shape, self.in_dtype = tuple(src.shape), src.dtype
+        # slot layout: input, then the outputs returned to the host (flags, averages,
+        # weights: one contiguous range), then the statistics
+        self.parts = [("vis", src.numel() * src.element_size()),
+                      ("flags", 4 * R * words_max), ("avg", 4 * R * n_out_max * 8),
+                      ("weight", 4 * R * n_out_max), ("stats", 4 * 3 * (R // F) * n_win_max)]
+        self.offsets = {}
+        o = 0
+        for name, n in self.parts:
+            self.offsets[name] = o
+            o += DevicePool.rounded(n)
+        self.slot_bytes = o
+        self.ret_lo, self.ret_hi = self.offsets["flags"], self.offsets["stats"]
+        self.out_host = torch.empty(self.ret_hi - self.ret_lo, dtype=torch.uint8, pin_memory=True)
+
+    def slot_views(self, pool, off):
+        """The block's input and outputs inside its pool slot, shaped for its numbers
+        of completed windows and bins."""
         import torch
         R, F = self.st.R, self.st.F
-        B = self.st.bits_per_window
-        self.n_out_max = T // K + 1
-        self.n_win_max = (T + M - 1) // B
-        words_max = (self.n_win_max * B + 31) // 32
-        dev = blocks[0].device
-        self.out_pool = []
-        for _ in range(2):
-            self.out_pool.append(dict(
-                flags_store=torch.empty(R * words_max, dtype=torch.int32, device=dev),
-                stats_store=torch.empty(3 * (R // F) * self.n_win_max, device=dev),
-                avg_store=torch.empty(R * self.n_out_max * 8, device=dev),
-                weight_store=torch.empty(R * self.n_out_max, device=dev)))
-        self.out_next = 0
-        self.bytes_in = blocks[0].numel() * blocks[0].element_size()
-        self.bytes_out = sum(v.numel() * v.element_size() for v in self.out_pool[0].values())
-
-    def outputs(self):
-        """Output buffers for the next block, shaped for its numbers of completed
-        windows and bins."""
-        o = self.out_pool[self.out_next]
-        self.out_next = (self.out_next + 1) % len(self.out_pool)
-        R, F, M = self.st.R, self.st.F, self.st.M
         n = self.st.outputs_for(self.T)
         nw = self.st.windows_for(self.T)[0]
         words = (nw * self.st.bits_per_window + 31) // 32
-        return dict(flags=o["flags_store"][:R * words].view(R, words),
-                    stats=o["stats_store"][:3 * (R // F) * nw].view(3, R // F, nw),
-                    avg=o["avg_store"][:R * n * 8].view(R, n, 4, 2),
-                    weight=o["weight_store"][:R * n].view(R, n))
+        shapes = {"vis": (self.in_dtype, self.in_shape), "flags": (torch.int32, (R, words)),
+                  "stats": (torch.float32, (3, R // F, nw)),
+                  "avg": (torch.float32, (R, n, 4, 2)), "weight": (torch.float32, (R, n))}
+        out = {}
+        for name, (dt, shape) in shapes.items():
+            out[name] = pool.view(off + self.offsets[name], math.prod(shape) * dt.itemsize, dt,
+                                  shape)
+        return out
 
 
 class ServingLoop:
     def __init__(self, stream_cfgs, M=16, K=256, T=256, thresholds=None, dtype="f16",
                  options=None, hbm_budget_bytes=8 << 30, max_batch=32, cuda_streams=3,
                  block_seconds=0.128, pool_blocks=2, seed=5, record_outputs=False,
-                 blocks=None):
+                 blocks=None, source="device", headroom_bytes=2 << 30, results_to_host=True):
+        """source: "device" (blocks arrive in device memory, as from a GPU correlator,
+        and are copied into the pool) or "host" (blocks arrive in pinned host memory and
+        are copied to the device).  The block pool takes min(hbm_budget_bytes, free
+        device memory - headroom_bytes), measured once here."""
         import torch
         from .thresholds import default_thresholds
         import synth
         self.torch = torch
         self.M, self.K, self.T = M, K, T
         self.block_seconds = block_seconds
-        self.budget = int(hbm_budget_bytes)
         self.max_batch = min(int(max_batch), 64)
         self.record = record_outputs
+        self.source = source
+        self.results_to_host = results_to_host
+        if source not in ("device", "host"):
+            raise ValueError("source is 'device' or 'host'")
         thr = thresholds or default_thresholds(M)
         opts = dict(options or {})
         self.streams = []
@@ -98,9 +169,26 @@ class ServingLoop:
                 bl = [synth.generate.device_block(cfg["stations"], cfg["channels"], T,
                                                   seed=seed * 1000 + i * 10 + k, dtype=dtype)
                       for k in range(pool_blocks)]
+            if source == "host":
+                bl = [b.cpu().pin_memory() for b in bl]
             self.streams.append(_Stream(i, cfg, M, K, T, thr, dtype, opts, bl))
+        torch.cuda.synchronize()
+        free, total = torch.cuda.mem_get_info()
+        self.free_at_start = int(free)
+        self.pool_request = int(hbm_budget_bytes)
+        nbytes = max(0, min(int(hbm_budget_bytes), int(free) - int(headroom_bytes)))
+        biggest = max(s.slot_bytes for s in self.streams)
+        if nbytes < biggest:
+            raise MemoryError(f"free device memory ({free / 2**30:.1f} GiB less the headroom) "
+                              f"does not hold one block of the largest stream "
+                              f"({biggest / 2**20:.0f} MiB)")
+        self.pool = DevicePool(nbytes, "cuda")
         self.cuda_streams = [torch.cuda.Stream() for _ in range(cuda_streams)]
         self.outputs = collections.defaultdict(list)     # stream -> [(seq, numpy dict)]
+
+    @property
+    def budget(self):
+        return self.pool.nbytes
 
     def _schedule(self, duration, rng):
         arr = []
@@ -115,6 +203,27 @@ class ServingLoop:
         arr.sort()
         return arr
 
+    def _launch(self, items, cs):
+        """Copy the blocks into their slots, run one batch, copy the results out; all on
+        CUDA stream cs."""
+        torch = self.torch
+        with torch.cuda.stream(cs):
+            for s, _, k, off, views in items:
+                views["vis"].copy_(s.sources[k % len(s.sources)], non_blocking=True)
+        B.rfi_process_batch([s.st.ctx for s, *_ in items], [v["vis"] for *_, v in items],
+                            [self.T] * len(items), [v["flags"] for *_, v in items],
+                            [v["avg"] if v["avg"].numel() else None for *_, v in items],
+                            [v["weight"] if v["weight"].numel() else None for *_, v in items],
+                            [v["stats"] for *_, v in items], stream=cs)
+        if self.results_to_host:
+            with torch.cuda.stream(cs):
+                for s, _, _, off, _ in items:
+                    s.out_host.copy_(self.pool.buf[off + s.ret_lo:off + s.ret_hi],
+                                     non_blocking=True)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(cs)
+        return ev
+
     def run(self, duration, seed=0, arrivals=None):
         """Serve Poisson arrivals for `duration` seconds of wall time (then drain).
         Returns latency and throughput statistics."""
@@ -122,10 +231,10 @@ class ServingLoop:
         rng = np.random.default_rng(seed)
         arrivals = arrivals if arrivals is not None else self._schedule(duration, rng)
         ai = 0
-        free_bytes = self.budget
-        inflight = []                 # (event, [(stream, arrival, seq, out)], cuda_stream, bytes)
+        inflight = []                 # (event, items, cuda_stream)
         free_cs = list(self.cuda_streams)
-        lat, samples, nbatches, batch_sizes = [], 0, 0, []
+        lat, samples, nbatches, batch_sizes, waits = [], 0, 0, [], 0
+        h2d = d2h = 0
         torch.cuda.synchronize()
         ref = torch.cuda.Event(enable_timing=True)
         ref.record()
@@ -137,56 +246,49 @@ class ServingLoop:
                 ta, si, k = arrivals[ai]
                 self.streams[si].queue.append((ta, k))
                 ai += 1
-            # retire finished batches
+            # retire finished batches and release their slots
             still = []
-            for ev, items, cs, nb in inflight:
+            for ev, items, cs in inflight:
                 if ev.query():
                     tdone = ref.elapsed_time(ev) * 1e-3
-                    for s, ta, k, out in items:
+                    for s, ta, k, off, views in items:
                         lat.append(tdone - ta)
                         samples += s.st.R * self.T
                         s.busy = False
                         s.done += 1
                         if self.record:
                             self.outputs[s.idx].append(
-                                (k, {n: v.cpu().numpy().copy() for n, v in out.items()}))
-                    free_bytes += nb
+                                (k, {n: v.cpu().numpy().copy() for n, v in views.items()
+                                     if n != "vis"}))
+                        self.pool.release(off, s.slot_bytes)
                     free_cs.append(cs)
                 else:
-                    still.append((ev, items, cs, nb))
+                    still.append((ev, items, cs))
             inflight = still
-            # admit: oldest head-of-queue first, while memory and batch slots allow
+            # admit: oldest head-of-queue first, while pool slots and batch slots allow
             if free_cs:
                 ready = sorted((s.queue[0][0], s.idx) for s in self.streams
                                if s.queue and not s.busy)
-                items, nb = [], 0
+                items = []
                 for _, si in ready:
                     s = self.streams[si]
-                    need = s.bytes_in + s.bytes_out
-                    if len(items) >= self.max_batch or nb + need > free_bytes:
+                    if len(items) >= self.max_batch:
+                        break
+                    off = self.pool.alloc(s.slot_bytes)
+                    if off is None:           # the pool is full: wait for a retirement
+                        waits += 1
                         break
                     ta, k = s.queue.popleft()
-                    out = s.outputs()
                     s.busy = True
-                    items.append((s, ta, k, out))
-                    nb += need
+                    items.append((s, ta, k, off, s.slot_views(self.pool, off)))
                 if items:
                     cs = free_cs.pop()
-                    vis = [s.blocks[k % len(s.blocks)] for s, _, k, _ in items]
-                    B.rfi_process_batch([s.st.ctx for s, _, _, _ in items], vis,
-                                        [self.T] * len(items),
-                                        [o["flags"] for _, _, _, o in items],
-                                        [o["avg"] if o["avg"].numel() else None
-                                         for _, _, _, o in items],
-                                        [o["weight"] if o["weight"].numel() else None
-                                         for _, _, _, o in items],
-                                        [o["stats"] for _, _, _, o in items], stream=cs)
-                    ev = torch.cuda.Event(enable_timing=True)
-                    ev.record(cs)
-                    inflight.append((ev, items, cs, nb))
-                    free_bytes -= nb
+                    inflight.append((self._launch(items, cs), items, cs))
                     nbatches += 1
                     batch_sizes.append(len(items))
+                    for s, *_ in items:
+                        h2d += s.parts[0][1] if self.source == "host" else 0
+                        d2h += (s.ret_hi - s.ret_lo) if self.results_to_host else 0
             if ai >= len(arrivals) and not inflight and all(not s.queue for s in self.streams):
                 break
             if not inflight and ai < len(arrivals):
@@ -197,9 +299,11 @@ class ServingLoop:
                 time.sleep(2e-5)
         wall = time.perf_counter() - t0
         lat_arr = np.array(lat) if lat else np.zeros(1)
+        hist = collections.Counter(batch_sizes)
         return {
             "blocks": len(lat), "batches": nbatches,
             "mean_batch": statistics.mean(batch_sizes) if batch_sizes else 0.0,
+            "batch_size_hist": {str(k): hist[k] for k in sorted(hist)},
             "p50_latency_s": float(np.percentile(lat_arr, 50)),
             "p99_latency_s": float(np.percentile(lat_arr, 99)),
             "max_latency_s": float(lat_arr.max()),
@@ -207,8 +311,12 @@ class ServingLoop:
             "p99_over_block": float(np.percentile(lat_arr, 99)) / self.block_seconds,
             "samples_per_s": samples / wall, "wall_s": wall,
             "offered_real_time_streams": sum(s.cfg.get("rho", 1.0) for s in self.streams),
+            "source": self.source, "h2d_bytes": h2d, "d2h_bytes": d2h,
+            "pool_gb": self.pool.nbytes / 1e9, "pool_peak_gb": self.pool.peak / 1e9,
+            "free_gb_at_start": self.free_at_start / 1e9, "admission_waits": waits,
         }
 
     def close(self):
         for s in self.streams:
             s.st.close()
+        self.pool = None

@@ -6,7 +6,7 @@ import torch
 
 import synth
 from paper_2412_14775_b300 import RfiStream, default_thresholds
-from paper_2412_14775_b300.serve import ServingLoop
+from paper_2412_14775_b300.serve import DevicePool, ServingLoop
 
 pytestmark = pytest.mark.gpu
 
@@ -56,14 +56,43 @@ def test_serving_mix_equals_solo(options, T):
 
 
 def test_serving_admission_respects_memory_budget():
-    """With a budget that fits one block at a time, batches hold a single block and
-    every block is still served."""
+    """With a block pool that holds one block at a time, batches hold a single block
+    and every block is still served."""
     M, K, T = 16, 16, 32
     cfgs = [dict(stations=6, channels=8, rho=4.0), dict(stations=6, channels=8, rho=4.0)]
+    s = DevicePool.rounded(1)
     loop = ServingLoop(cfgs, M=M, K=K, T=T, dtype="f16", block_seconds=0.01, max_batch=8,
                        pool_blocks=1)
-    s0 = loop.streams[0]
-    loop.budget = s0.bytes_in + s0.bytes_out        # room for exactly one block
+    slot = loop.streams[0].slot_bytes
+    loop.pool = DevicePool(slot + s, "cuda")          # room for exactly one block
     stats = loop.run(0.3, seed=1)
     assert stats["blocks"] > 0 and stats["mean_batch"] == 1.0
+    assert stats["admission_waits"] > 0 and loop.pool.used == 0
+    loop.close()
+
+
+def test_serving_host_fed_equals_solo():
+    """Blocks arriving in pinned host memory, copied into the device pool per batch,
+    results copied back: the same bits as the blocks processed alone."""
+    M, K, T = 16, 32, 48
+    cfgs = [dict(stations=n, channels=c, rho=r) for n, c, r in
+            ((5, 4, 3.0), (9, 8, 2.0), (7, 16, 4.0))]
+    thr = default_thresholds(M)
+    blocks = [[synth.generate.device_block(c["stations"], c["channels"], T, seed=200 + 7 * i + k)
+               for k in range(2)] for i, c in enumerate(cfgs)]
+    loop = ServingLoop(cfgs, M=M, K=K, T=T, thresholds=thr, dtype="f16", block_seconds=0.01,
+                       max_batch=4, record_outputs=True, blocks=blocks, source="host")
+    stats = loop.run(0.5, seed=4)
+    assert stats["blocks"] > 50 and stats["h2d_bytes"] > 0 and stats["d2h_bytes"] > 0
+    opts = loop.streams[0].st.options
+    for i, cfg in enumerate(cfgs):
+        solo = RfiStream(cfg["stations"], cfg["channels"], M, K, thr, "f16",
+                         lanes_per_row=opts["lanes_per_row"],
+                         warps_per_block=opts["warps_per_block"])
+        for k, mixed in sorted(loop.outputs[i], key=lambda t: t[0]):
+            o = solo.process(blocks[i][k % 2].contiguous())
+            torch.cuda.synchronize()
+            for name in ("flags", "avg", "weight", "stats"):
+                assert np.array_equal(o[name].cpu().numpy(), mixed[name]), (i, k, name)
+        solo.close()
     loop.close()
