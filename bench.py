@@ -239,9 +239,10 @@ def oracle_threads(rows, M, K, thr, threads):
         return time.perf_counter() - t0
 
 
-def cpu_baseline(seconds_target=10.0):
-    """The oracle as it stands on a bounded sample of the block: single-threaded, and
-    over row ranges on every host core (the reported value)."""
+def cpu_baseline(passes=10, warm=2):
+    """The oracle as it stands on the whole LOFAR-scale float32 block: over row ranges
+    on every host core (the reported value: `warm` untimed passes, then `passes` timed
+    ones, as the reference arm times its steps), and one pass single-threaded."""
     import oracle
     import synth
     from paper_2412_14775_b300.thresholds import default_thresholds
@@ -250,20 +251,19 @@ def cpu_baseline(seconds_target=10.0):
     d = synth.lofar_block(seed=2)
     R = d["vis"].shape[0] * d["vis"].shape[1]
     rows = d["vis"].reshape(R, T, 4, 2)
-    t0 = time.perf_counter()
-    oracle.OracleStream(256, M, K, **thr).process(rows[:256])
-    per_row = (time.perf_counter() - t0) / 256
-    n = int(min(R, max(256, seconds_target / max(per_row, 1e-9))))
-    t0 = time.perf_counter()
-    oracle.OracleStream(n, M, K, **thr).process(rows[:n])
-    dt1 = time.perf_counter() - t0
     cores = host_threads()
-    dtn = oracle_threads(rows[:n], M, K, thr, cores)
-    return {"value": n * T / dtn, "unit": "samples/s", "cores": cores, "kind": "oracle",
-            "single_thread_value": n * T / dt1, "cpu_model": cpu_model(),
-            "sample": f"first {n} of {R} rows x {T} samples of the FP32 block: "
-                      f"{dtn:.2f} s on {cores} threads (row ranges), "
-                      f"{dt1:.1f} s single-threaded"}
+    for _ in range(warm):
+        oracle_threads(rows, M, K, thr, cores)
+    dtn = sum(oracle_threads(rows, M, K, thr, cores) for _ in range(passes))
+    oracle.OracleStream(256, M, K, **thr).process(rows[:256])
+    t0 = time.perf_counter()
+    oracle.OracleStream(R, M, K, **thr).process(rows)
+    dt1 = time.perf_counter() - t0
+    return {"value": passes * R * T / dtn, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "single_thread_value": R * T / dt1, "cpu_model": cpu_model(),
+            "sample": f"all {R} rows x {T} samples of the float32 block, {passes} timed passes "
+                      f"after {warm} warm-up passes: {dtn:.2f} s on {cores} threads (row "
+                      f"ranges); one pass single-threaded: {dt1:.1f} s"}
 
 
 def footprint_extras(torch, cs, peak, steps=500, warmup=10, only=None):
@@ -303,7 +303,8 @@ def footprint_extras(torch, cs, peak, steps=500, warmup=10, only=None):
     return res
 
 
-def detection_experiment(torch, realizations=8, inrs=(0.01, 0.1, 1.0, 10.0, 100.0), fa=0.05):
+def detection_experiment(torch, realizations=8, inrs=(0.01, 0.1, 1.0, 10.0, 100.0), fa=0.05,
+                         n_cal=16):
     """False-alarm and missed-detection probabilities against the interference-to-noise
     ratio for SK only, DS only and both, with polarised and with unpolarised
     interference, on blocks simulated as in the paper's Section 4.2 (2000 x 512, one
@@ -329,7 +330,7 @@ def detection_experiment(torch, realizations=8, inrs=(0.01, 0.1, 1.0, 10.0, 100.
     # the simulated blocks differ in receiver-noise scale, so the clean calibration set
     # spans several blocks
     stats = [run(cal, paper_sim.simulate_block(9000 + k, inr=0.0, n_broadband=0, n_narrow=0)
-                 ["vis"])["stats"].clone() for k in range(16)]
+                 ["vis"])["stats"].clone() for k in range(n_cal)]
     thr = thresholds_for_false_alarm(stats, fa=fa)
     modes = {"SK": dict(thr, gamma=math.inf),
              "DS": dict(thr, s_low=-math.inf, s_high=math.inf),
@@ -354,6 +355,65 @@ def detection_experiment(torch, realizations=8, inrs=(0.01, 0.1, 1.0, 10.0, 100.
                                             "missed": a[2] / max(a[3], 1)}
                                         for m, a in acc.items()}})
         res["polarised" if pol else "unpolarised"] = rows
+    return res
+
+
+def _stat_errors(torch, got, ref, M, thr):
+    """Worst statistic errors of `got` against `ref` (stats tensors [3, R, n]) with the
+    parity floors (1 for tau, M^-1/2 for r) and the fraction of windows whose flag
+    differs (the flag rule on each side's own statistics)."""
+    g, r = got.double(), ref.double()
+    e_tau = ((g[0] - r[0]).abs() / r[0].abs().clamp(min=1.0)).max().item()
+    fl = M ** -0.5
+    e_r = max(((g[k] - r[k]).abs() / r[k].abs().clamp(min=fl)).max().item() for k in (1, 2))
+
+    def flags(s):
+        return (~((s[0] >= thr["s_low"]) & (s[0] <= thr["s_high"])) | ~(s[1] <= thr["gamma"]) |
+                ~(s[2] <= thr["gamma"]))
+    dis = (flags(got) != flags(ref)).float().mean().item()
+    return {"tau_err": e_tau, "r_err": e_r, "flag_disagree": dis}
+
+
+def fp16_extras(vis32, vis16, tuned, torch, cs, peak, dev, steps, warmup):
+    """Binary16 storage of the LOFAR-scale block, windows M = 8, 16, 32, 64 (K = 256), in
+    both binary16 modes: float32 arithmetic on exactly widened values (`storage`) and
+    binary16 Stokes arithmetic (`h2`, precision = 2).  Per mode: launch time, throughput
+    and fraction of the copy bandwidth; statistic error and flag disagreement against the
+    float32 kernel run on the same binary16 values widened to float32 (`arith_*`: the
+    mode's arithmetic alone; the float32 kernel is within 1e-5 of the FP64 oracle, see the
+    parity tests) and on the original float32 block (`total_*`: with the input's
+    quantisation)."""
+    from paper_2412_14775_b300 import RfiStream, default_thresholds
+    R, T = vis32.shape[0], vis32.shape[1]
+    vis16w = vis16.float()
+    res = {}
+    for Mw in (8, 16, 32, 64):
+        thr = default_thresholds(Mw)
+        refs = {}
+        for name, v in (("arith", vis16w), ("total", vis32)):
+            f32 = RfiStream(62, 64, Mw, 256, thr, "f32")
+            refs[name] = f32.process(v, stream=cs)["stats"]
+            torch.cuda.synchronize()
+            f32.close()
+        b16 = algo_bytes(R, T, Mw, 256, 1, 16)
+        entry = {}
+        for mode, fixed in (("storage", {}), ("h2", {"precision": 2})):
+            o16opts = tuned(Mw, "f16", vis16, fixed)
+            s16 = RfiStream(62, 64, Mw, 256, thr, "f16", **o16opts)
+            o16 = s16.alloc_outputs(T, device=dev)
+            k16, _, _, _ = time_kernel(s16, vis16, o16, steps, warmup, torch, cs)
+            e = {"kernel_us": k16 * 1e6, "samples_per_s": R * T / k16,
+                 "achieved_gbs": b16 / k16 / 1e9, "frac": b16 / k16 / 1e9 / peak,
+                 "options": o16opts}
+            for name, ref in refs.items():
+                for k, val in _stat_errors(torch, o16["stats"], ref, Mw, thr).items():
+                    e[f"{name}_{k}"] = val
+            entry[mode] = e
+            s16.close()
+        # the main entry keeps the storage mode's figures at its top level
+        res[f"M{Mw}"] = dict(entry["storage"], h2=entry["h2"])
+        del refs
+    del vis16w
     return res
 
 
@@ -519,30 +579,39 @@ def batched_extras(options, torch, steps=300, warmup=10):
 
 
 def serving_extras(seconds, options, torch):
-    """The serving loop: 32 mixed FP16 streams at 1-4x real time, then the 62-station,
-    64-channel stream offered at 50x real time."""
+    """The serving loop (binary16, M = 16, K = 256, blocks of 256 samples = 128 ms): the
+    32 mixed streams at 1-4x real time, the same at 4x that rate (4-16x real time per
+    stream, 340 real-time streams offered, so batches fill), the 62-station, 64-channel stream at 50x real time and
+    backlogged, all with blocks arriving in device memory (a GPU correlator's output),
+    and that stream fed from pinned host memory at 10x real time (the host link carries
+    512 MB per block).  Every admitted block is copied into a slot of the device block
+    pool and its results are copied back to pinned host memory."""
     import synth
     from paper_2412_14775_b300.serve import ServingLoop
     res = {}
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(0.5 * free, 32 << 30))
     cfgs = synth.serving_streams(seed=5, n=32)
-    loop = ServingLoop(cfgs, M=16, K=256, T=256, dtype="f16", options=options,
-                       hbm_budget_bytes=budget, max_batch=32, cuda_streams=3)
-    res["mix32"] = dict(loop.run(seconds, seed=11), hbm_budget_gb=budget / 1e9, streams=32)
-    loop.close()
-    torch.cuda.empty_cache()
-    # one 62-station, 64-channel stream delivering a block every 1/50 of a block time
-    one = [dict(stations=62, channels=64, rho=50.0)]
-    loop = ServingLoop(one, M=16, K=256, T=256, dtype="f16", options=options,
-                       hbm_budget_bytes=budget, max_batch=1, cuda_streams=2)
-    dur = max(2.0, seconds / 2)
-    period = BLOCK_SECONDS / 50.0
-    r = loop.run(dur, arrivals=[(k * period, 0, k) for k in range(int(dur / period))])
+    for name, scale in (("mix32", 1.0), ("mix32_x4", 4.0)):
+        c = [dict(x, rho=x["rho"] * scale) for x in cfgs]
+        loop = ServingLoop(c, M=16, K=256, T=256, dtype="f16", options=options,
+                           hbm_budget_bytes=budget, max_batch=32, cuda_streams=3)
+        res[name] = dict(loop.run(seconds / 2, seed=11), streams=32, rho_scale=scale)
+        loop.close()
+        torch.cuda.empty_cache()
     R = 1953 * 64
-    r["real_time_factor"] = r["samples_per_s"] / (R * 256 / BLOCK_SECONDS)
-    res["lofar_50x"] = r
-    loop.close()
+    # one 62-station, 64-channel stream delivering a block every 1/rate of a block time
+    for name, rate, source in (("lofar_50x", 50.0, "device"), ("lofar_host_10x", 10.0, "host")):
+        loop = ServingLoop([dict(stations=62, channels=64, rho=rate)], M=16, K=256, T=256,
+                           dtype="f16", options=options, hbm_budget_bytes=budget, max_batch=1,
+                           cuda_streams=2, source=source)
+        dur = max(2.0, seconds / 4)
+        period = BLOCK_SECONDS / rate
+        r = loop.run(dur, arrivals=[(k * period, 0, k) for k in range(int(dur / period))])
+        r["real_time_factor"] = r["samples_per_s"] / (R * 256 / BLOCK_SECONDS)
+        res[name] = r
+        loop.close()
+        torch.cuda.empty_cache()
     # the same stream backlogged (3000 blocks queued at once): the rate the loop
     # sustains for one stream, whose blocks must run one after another
     loop = ServingLoop([dict(stations=62, channels=64, rho=1.0)], M=16, K=256, T=256,
@@ -550,7 +619,8 @@ def serving_extras(seconds, options, torch):
                        cuda_streams=2)
     r = loop.run(0.0, arrivals=[(0.0, 0, k) for k in range(3000)])
     r["real_time_factor"] = r["samples_per_s"] / (R * 256 / BLOCK_SECONDS)
-    r.pop("p50_latency_s"); r.pop("p99_latency_s"); r.pop("max_latency_s"); r.pop("p99_over_block")
+    for k in ("p50_latency_s", "p99_latency_s", "max_latency_s", "p99_over_block"):
+        r.pop(k)
     res["lofar_backlogged"] = r
     loop.close()
     torch.cuda.empty_cache()
@@ -607,6 +677,72 @@ def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler
     return total / steps, total, serial, (sampler.summary() if sampler else None)
 
 
+def _r(x, n=4):
+    """x rounded to n significant digits (None stays None)."""
+    if x is None:
+        return None
+    if x == 0 or not math.isfinite(x):
+        return x
+    return round(x, -int(math.floor(math.log10(abs(x)))) + n - 1)
+
+
+def summarize(line):
+    """The line's figures in a compact form (kept under ~1.3 KB so that a reader keeping
+    only the end of the line has them all): launch time (us) and fraction of the measured
+    copy bandwidth per kernel, the binary16 modes' errors, serving and the detection
+    experiment."""
+    g = line.get
+    out = {"main": [_r(line["roofline"]["kernel_us"]), _r(line["roofline"]["frac"], 3)]}
+    if g("fp16"):
+        # per M: storage us, frac; h2 us, frac; h2 arithmetic error of tau and r and its
+        # flag disagreement; flag disagreement against the float32 input (storage, h2)
+        out["fp16"] = "us,frac,h2us,h2frac,h2tau,h2r,h2flag,flag32,h2flag32"
+        for k, e in line["fp16"].items():
+            h = e["h2"]
+            out[k] = [_r(e["kernel_us"]), _r(e["frac"], 3), _r(h["kernel_us"]), _r(h["frac"], 3),
+                      _r(h["arith_tau_err"], 2), _r(h["arith_r_err"], 2),
+                      _r(h["arith_flag_disagree"], 2), _r(e["total_flag_disagree"], 2),
+                      _r(h["total_flag_disagree"], 2)]
+    if g("mixed_precision"):
+        m = line["mixed_precision"]["f32"]
+        out["mixed"] = [_r(m["flag_difference_vs_float32"], 3), _r(m["kernel_us"]), _r(m["frac"], 3)]
+    if g("variants"):
+        short = {"online_thresholds": "online", "partial_windows_T250": "partial",
+                 "sliding_windows_hop8": "sliding"}
+        for k, v in line["variants"].items():
+            out[short.get(k, k)] = [_r(v["kernel_us"]), _r(v["frac"], 3)]
+    if g("footprints"):
+        for k, v in line["footprints"].items():
+            out[k] = [_r(v["kernel_us"]), _r(v["frac"], 3)]
+    if g("batched"):
+        b = line["batched"]
+        out["batch8"] = [_r(b["graph_persistent"]["us_per_step"]),
+                         _r(b["graph_persistent"]["achieved_gbs"]),
+                         _r(b["sequential_launches"]["us_per_step"])]
+    if g("serving"):
+        # per run: mean batch, p50 and p99 latency (ms), real-time factor
+        out["serve"] = "batch,p50ms,p99ms,rtf"
+        for k, v in line["serving"].items():
+            if isinstance(v, dict):
+                out[k] = [_r(v.get("mean_batch", 0), 3),
+                          _r(1e3 * v["p50_latency_s"], 3) if "p50_latency_s" in v else None,
+                          _r(1e3 * v["p99_latency_s"], 3) if "p99_latency_s" in v else None,
+                          _r(v.get("real_time_factor") or v.get("offered_real_time_streams"), 3)]
+    if g("detection"):
+        # per INR: (false alarm, missed) for SK, DS, both
+        d = line["detection"]
+        for pol in ("polarised", "unpolarised"):
+            if pol in d:
+                out["det_" + pol[:5]] = {str(row["inr"]): [_r(row[m][x], 2) for m in ("SK", "DS", "BOTH")
+                                                           for x in ("false_alarm", "missed")]
+                                         for row in d[pol]}
+    if g("cpu_baseline"):
+        out["cpu"] = _r(line["cpu_baseline"]["value"], 3)
+    if g("e2e"):
+        out["e2e"] = _r(line["e2e"]["value"], 3)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -621,7 +757,11 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="wall time of the serving-loop run (0 = skip)")
     ap.add_argument("--detection", action="store_true",
-                    help="also run the false-alarm / missed-detection experiment")
+                    help="run the full false-alarm / missed-detection experiment (8 "
+                         "realisations, 5 INRs; the default line carries a reduced one)")
+    ap.add_argument("--no-detection", action="store_true")
+    ap.add_argument("--cpu-baseline-only", action="store_true",
+                    help="print the CPU baseline (the FP64 oracle on the host cores) and exit")
     ap.add_argument("--tile", default="",
                     help="lanes_per_row,warps_per_block[,prefetch_groups,prefetch_bytes]")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16"],
@@ -637,6 +777,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.cpu_baseline_only:
+        print(json.dumps(cpu_baseline()), flush=True)
+        return
 
     import torch
     import torch.distributed as dist
@@ -678,13 +821,13 @@ def main():
     host32 = torch.from_numpy(d["vis"].reshape(R, T, 4, 2))
     vis32 = host32.to(dev)
 
-    def tuned(Mw, dtype, vis):
-        if args.tile:
+    def tuned(Mw, dtype, vis, fixed=None):
+        if args.tile and not fixed:
             f = [int(x) for x in args.tile.split(",")]
             keys = ["lanes_per_row", "warps_per_block", "prefetch_groups", "prefetch_bytes"]
             return dict(zip(keys, f))
         best, _ = autotune.tune(62, 64, Mw, K, default_thresholds(Mw), dtype, vis,
-                                cache_path=autotune.TUNED_PATH, write_cache=False)
+                                cache_path=autotune.TUNED_PATH, write_cache=False, fixed=fixed)
         return autotune.options_of(best)
 
     main_dt = args.dtype
@@ -723,23 +866,16 @@ def main():
         extras["variants"] = variant_extras(vis32, opts, torch, cs, peak)
         if args.detection:
             extras["detection"] = detection_experiment(torch)
-        # FP16 storage (same geometry), window sweep
-        fp16 = {}
-        vis16 = vis_main if main_dt == "f16" else vis32.half()
-        del vis32, vis_main
-        for Mw in (8, 16, 32, 64):
-            o16opts = tuned(Mw, "f16", vis16)
-            s16 = RfiStream(62, 64, Mw, 256, default_thresholds(Mw), "f16", **o16opts)
-            o16 = s16.alloc_outputs(T, device=dev)
-            k16, _, _, _ = time_kernel(s16, vis16, o16, max(200, args.steps // 4), args.warmup,
-                                       torch, cs)
-            b16 = algo_bytes(R, T, Mw, 256, 1, 16)
-            fp16[f"M{Mw}"] = {"samples_per_s": samples / k16,
-                              "kernel_us": k16 * 1e6, "achieved_gbs": b16 / k16 / 1e9,
-                              "frac": b16 / k16 / 1e9 / peak, "options": o16opts}
-            s16.close()
-        extras["fp16"] = fp16
-        del vis16
+        elif not args.no_detection:
+            # a reduced table (the full one: --detection)
+            extras["detection"] = detection_experiment(torch, realizations=6,
+                                                       inrs=(0.01, 1.0, 100.0))
+        del vis_main
+        vis16 = vis32.half()
+        extras["fp16"] = fp16_extras(vis32, vis16, tuned, torch, cs, peak, dev,
+                                     max(200, args.steps // 4), args.warmup)
+        fp16 = extras["fp16"]
+        del vis32, vis16
         torch.cuda.empty_cache()
         extras["batched"] = batched_extras(fp16["M16"]["options"], torch)
         extras["footprints"] = footprint_extras(torch, cs, peak)
@@ -800,7 +936,11 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        # in a fresh process without CUDA, as the reference arm runs (timed inside this
+        # process after the GPU work, the same oracle ran about half as fast)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only"],
+                           capture_output=True, text=True, timeout=600)
+        cpu = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
 
     if rank == 0:
         line = {
@@ -831,6 +971,8 @@ def main():
             "flag_fractions": flag_fractions,
         }
         line.update(extras)
+        # last, so that a reader keeping only the end of the line still has the figures
+        line["summary"] = summarize(line)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
