@@ -44,7 +44,8 @@ def _peaks():
         return 6400.0, "fallback"
 
 
-KERNEL_SOURCES = ("rfi_device.cuh", "rfi_inst_f16.cu", "rfi_inst_f32.cu", "rfi_inst_pf_f16.cu",
+KERNEL_SOURCES = ("rfi_device.cuh", "rfi_inst_f16.cu", "rfi_inst_f32.cu", "rfi_inst_h2.cu",
+                  "rfi_inst_pf_f16.cu",
                   "rfi_inst_pf_f32.cu", "rfi_kernels.h")
 
 
@@ -61,8 +62,8 @@ def kernel_source_hash():
 
 
 def _profile(dtype):
-    """Header fields of profiles/k_block_lofar_block_<dtype>.md, or {} when the kernel
-    sources changed after that capture."""
+    """Header fields of profiles/k_block_lofar_block_<dtype>.md (dtype f32, f16 or f16_h2),
+    or {} when the kernel sources changed after that capture."""
     path = os.path.join(ROOT, "profiles", f"k_block_lofar_block_{dtype}.md")
     try:
         kv = {}
@@ -239,10 +240,11 @@ def oracle_threads(rows, M, K, thr, threads):
         return time.perf_counter() - t0
 
 
-def cpu_baseline(passes=10, warm=2):
-    """The oracle as it stands on the whole LOFAR-scale float32 block: over row ranges
-    on every host core (the reported value: `warm` untimed passes, then `passes` timed
-    ones, as the reference arm times its steps), and one pass single-threaded."""
+def cpu_baseline(rows_per_step=8192, seconds=15.0, warm=5):
+    """The oracle as it stands on the LOFAR-scale float32 block, stepped the way the
+    reference arm steps it: contiguous ranges of `rows_per_step` rows in turn, each over
+    row ranges on every host core; `warm` untimed steps, then about `seconds` of timed
+    ones (the reported value), and one pass over the whole block single-threaded."""
     import oracle
     import synth
     from paper_2412_14775_b300.thresholds import default_thresholds
@@ -252,18 +254,24 @@ def cpu_baseline(passes=10, warm=2):
     R = d["vis"].shape[0] * d["vis"].shape[1]
     rows = d["vis"].reshape(R, T, 4, 2)
     cores = host_threads()
-    for _ in range(warm):
-        oracle_threads(rows, M, K, thr, cores)
-    dtn = sum(oracle_threads(rows, M, K, thr, cores) for _ in range(passes))
+    n = min(R, rows_per_step)
+
+    def step(i):
+        a = (i * n) % R
+        return oracle_threads(rows[a:a + n], M, K, thr, cores)
+
+    probe = sum(step(i) for i in range(warm)) / max(warm, 1)
+    steps = int(min(2000, max(10, seconds / max(probe, 1e-6))))
+    dtn = sum(step(warm + i) for i in range(steps))
     oracle.OracleStream(256, M, K, **thr).process(rows[:256])
     t0 = time.perf_counter()
     oracle.OracleStream(R, M, K, **thr).process(rows)
     dt1 = time.perf_counter() - t0
-    return {"value": passes * R * T / dtn, "unit": "samples/s", "cores": cores, "kind": "oracle",
+    return {"value": steps * n * T / dtn, "unit": "samples/s", "cores": cores, "kind": "oracle",
             "single_thread_value": R * T / dt1, "cpu_model": cpu_model(),
-            "sample": f"all {R} rows x {T} samples of the float32 block, {passes} timed passes "
-                      f"after {warm} warm-up passes: {dtn:.2f} s on {cores} threads (row "
-                      f"ranges); one pass single-threaded: {dt1:.1f} s"}
+            "sample": f"{steps} steps of {n} of the block's {R} rows x {T} samples (float32 "
+                      f"block) after {warm} warm-up steps: {dtn:.1f} s on {cores} threads (row "
+                      f"ranges); one pass over the whole block single-threaded: {dt1:.1f} s"}
 
 
 def footprint_extras(torch, cs, peak, steps=500, warmup=10, only=None):
@@ -286,17 +294,21 @@ def footprint_extras(torch, cs, peak, steps=500, warmup=10, only=None):
             if only and only[1:] != (M, F):
                 continue
             thr = default_thresholds(M * F)
-            best, _ = autotune.tune(62, 64, M, K, thr, dtype, vis, fixed={"window_F": F},
-                                    cache_path=autotune.TUNED_PATH, write_cache=False)
-            opts = autotune.options_of(best)
-            st = RfiStream(62, 64, M, K, thr, dtype, **opts)
-            out = st.alloc_outputs(T)
-            k, _, _, _ = time_kernel(st, vis, out, steps, warmup, torch, cs)
-            nbytes = R * (T * sb + 4 * math.ceil(T / 32) + 12 * (T // M) // F + 36)
-            res[f"{dtype}_{M}x{F}"] = {"kernel_us": k * 1e6, "samples_per_s": R * T / k,
-                                       "achieved_gbs": nbytes / k / 1e9,
-                                       "frac": nbytes / k / 1e9 / peak, "options": opts}
-            st.close()
+            # binary16 input: float32 arithmetic, and binary16 arithmetic (precision = 2)
+            for prec in ((0, 2) if dtype == "f16" else (0,)):
+                fixed = {"window_F": F, **({"precision": 2} if prec else {})}
+                best, _ = autotune.tune(62, 64, M, K, thr, dtype, vis, fixed=fixed,
+                                        cache_path=autotune.TUNED_PATH, write_cache=False)
+                opts = autotune.options_of(best)
+                st = RfiStream(62, 64, M, K, thr, dtype, **opts)
+                out = st.alloc_outputs(T)
+                k, _, _, _ = time_kernel(st, vis, out, steps, warmup, torch, cs)
+                nbytes = R * (T * sb + 4 * math.ceil(T / 32) + 12 * (T // M) // F + 36)
+                res[f"{dtype}_{M}x{F}" + ("_h2" if prec else "")] = {
+                    "kernel_us": k * 1e6, "samples_per_s": R * T / k,
+                    "achieved_gbs": nbytes / k / 1e9, "frac": nbytes / k / 1e9 / peak,
+                    "options": opts}
+                st.close()
         del vis
     del v32
     torch.cuda.empty_cache()
@@ -766,6 +778,9 @@ def main():
                     help="lanes_per_row,warps_per_block[,prefetch_groups,prefetch_bytes]")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16"],
                     help="input storage of the timed block (f16: same block in binary16)")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 2],
+                    help="arithmetic of the timed block with --dtype f16: 0 = float32 on "
+                         "exactly widened values, 2 = binary16 Stokes arithmetic")
     ap.add_argument("--footprint", default="", choices=["", "10x2", "5x4"],
                     help="time only this T x F window footprint (blocks of 250 samples, "
                          "--dtype storage) and print its figures")
@@ -833,7 +848,10 @@ def main():
     main_dt = args.dtype
     sbytes = 32 if main_dt == "f32" else 16
     vis_main = vis32 if main_dt == "f32" else vis32.half()
-    opts = tuned(M, main_dt, vis_main)
+    if args.precision and main_dt != "f16":
+        ap.error("--precision 2 needs --dtype f16")
+    opts = tuned(M, main_dt, vis_main, {"precision": 2} if args.precision else None)
+    prof_key = main_dt + ("_h2" if args.precision else "")
     st = RfiStream(62, 64, M, K, thr, main_dt, **opts)
     out = st.alloc_outputs(T, device=dev)
     cs = torch.cuda.current_stream(dev)
@@ -957,8 +975,8 @@ def main():
                                      "prefetch_groups")}),
             "hbm_gbs": achieved * ws,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(main_dt),
-                         "ncu_dram_gbs": profiled_dram_gbs(main_dt),
+                         "frac": achieved / peak, "traffic": profiled_traffic(prof_key),
+                         "ncu_dram_gbs": profiled_dram_gbs(prof_key),
                          "peak_kind": peak_kind, "kernel_us": kern * 1e6,
                          "kernel_us_serialised": kern_serial * 1e6,
                          "algorithmic_bytes_per_launch": bytes_launch},
