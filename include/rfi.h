@@ -95,8 +95,10 @@ typedef enum {
  *   prefetch_groups  how many such groups each row keeps requested ahead of the
  *                  window being loaded; 0 or -1 = no prefetch (default).
  *   max_registers  register budget per thread of the single-stream kernel: 0 or 128
- *                  (default), 80 or 64 (more resident warps; at most 8 warps per
- *                  block; lanes_per_row <= 8).  Results do not depend on it.
+ *                  (default), 96 (20 resident warps per SM, two chunks of at most 2
+ *                  load units in flight per lane; at most 4 warps per block), 80 or
+ *                  64 (one chunk in flight, more resident warps; at most 8 warps per
+ *                  block); below 128: lanes_per_row <= 8.  Results do not depend on it.
  *   window_F       channels per window footprint (0 = 1): a window is M consecutive
  *                  samples of F adjacent channels of one baseline, W = M F samples
  *                  (the time-frequency windows of Sections 3.2 and 4).  A power of two

@@ -90,7 +90,7 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
         return t
 
     # stage 1: launch shape without prefetch; stage 2: prefetch for the three best
-    shapes = [(4, 0), (8, 0), (16, 0), (4, 80), (8, 80), (4, 64), (8, 64)]
+    shapes = [(4, 0), (8, 0), (16, 0), (4, 96), (2, 96), (4, 80), (8, 80), (4, 64), (8, 64)]
     stage1 = []
     F = fixed.get("window_F", 1)
     for P in [p for p in candidates_p(M, dtype) if p * F <= 32]:

@@ -314,6 +314,7 @@ int choose_shape(rfi_ctx *c, int P_req) {
     c->spu = spu;
     c->S = U / (P * spu);
     c->ch = largest_chunk(c->S);
+    if (c->lb == 3) c->ch = c->S % 2 == 0 ? 2 : 1;   // two chunks of <= 2 units in 96 registers
     if (c->sw) {
         // overlapping windows: their own kernels, single-stream calls only
         c->ch = c->S % 4 == 0 ? 4 : (c->S % 2 == 0 ? 2 : 1);
@@ -765,7 +766,9 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->kahan = o.compensated == 1 || (o.compensated == 0 && window_M >= 64);
     c->wpb = o.warps_per_block ? o.warps_per_block : 8;
     c->wpb_auto = o.warps_per_block == 0;
-    c->lb = o.max_registers == 0 || o.max_registers >= 128 ? 0 : (o.max_registers >= 80 ? 1 : 2);
+    c->lb = o.max_registers == 0 || o.max_registers >= 128
+                ? 0
+                : (o.max_registers >= 96 ? 3 : (o.max_registers >= 80 ? 1 : 2));
     c->F = o.window_F ? o.window_F : 1;
     c->mixed = o.precision == 1;
     c->prec = o.precision;
@@ -790,12 +793,12 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
         }
         c->kahan = 0;
     }
-    if (c->prec == 2 && (dtype != RFI_C32H || c->lb != 0 || o.loader != 0 ||
+    if (c->prec == 2 && (dtype != RFI_C32H || (c->lb != 0 && c->lb != 3) || o.loader != 0 ||
                          o.buffered_stores != 0 || o.partial_windows != 0 || o.adaptive != 0 ||
                          o.prefetch_groups > 0)) {
         delete c;
         return fail(RFI_EUNSUPPORTED, "precision = 2 needs binary16 input (RFI_C32H), the "
-                                      "direct loader and the 128-register budget, without "
+                                      "direct loader and the 128- or 96-register budget, without "
                                       "buffered stores, partial windows, adaptive thresholds "
                                       "or prefetch");
     }
@@ -807,6 +810,13 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     if (c->lb > 0 && c->wpb > 8) {
         delete c;
         return fail(RFI_EINVAL, "max_registers below 128 allows at most 8 warps per block");
+    }
+    if (c->lb == 3 && c->wpb > 4) {
+        if (!c->wpb_auto) {
+            delete c;
+            return fail(RFI_EINVAL, "max_registers = 96 allows at most 4 warps per block");
+        }
+        c->wpb = 4;
     }
     c->pf_bytes = o.prefetch_bytes ? o.prefetch_bytes : 1024;
     c->pf_groups = o.prefetch_groups > 0 ? o.prefetch_groups : 0;

@@ -910,12 +910,14 @@ __device__ __forceinline__ void overlap_prologue(const StreamArgs &a, long long 
 
 // LB selects the register budget through the launch bounds: 0 -> at most 128
 // registers (blocks up to 512 threads), 1 -> 80 (256 threads, 3 blocks per SM),
-// 2 -> 64 (256 threads, 4 blocks per SM).  The arithmetic, hence every result, is the
-// same for all budgets; only residency changes.
+// 2 -> 64 (256 threads, 4 blocks per SM), 3 -> 96 (128 threads, 5 blocks per SM: 20
+// resident warps with two chunks of at most 2 load units in flight per lane).  The
+// arithmetic, hence every result, is the same for all budgets; only residency changes.
 template <int LB> struct Bounds;
 template <> struct Bounds<0> { static constexpr int threads = 512, blocks = 1; };
 template <> struct Bounds<1> { static constexpr int threads = 256, blocks = 3; };
 template <> struct Bounds<2> { static constexpr int threads = 256, blocks = 4; };
+template <> struct Bounds<3> { static constexpr int threads = 128, blocks = 5; };
 
 template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0, int PREC = 0,
           bool VS = false, bool PW = false, bool AD = false, bool PFT = false>
@@ -925,9 +927,10 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     overlap_prologue<DT, P>(a, group);
-    // the 128-register budget keeps two chunks in flight; tighter budgets load one
-    // chunk at a time and rely on more resident warps instead
-    process_group<DT, SPU, P, CH, KAHAN, LB == 0, PREC, false, VS, PW, AD, PFT>(a, group);
+    // the 128- and 96-register budgets keep two chunks in flight; tighter budgets load
+    // one chunk at a time and rely on more resident warps instead
+    process_group<DT, SPU, P, CH, KAHAN, LB == 0 || LB == 3, PREC, false, VS, PW, AD, PFT>(a,
+                                                                                       group);
 }
 
 // P lanes per row, rows staged in shared memory by TMA bulk copies; dynamic shared

@@ -17,6 +17,9 @@ static const Instance k_table[] = {
     RFI_INSTB_CH(DT_F16, 1, 1, 1),
     RFI_INSTB_CH(DT_F16, 1, 1, 2),
     RFI_INSTV_P(DT_F16, 2),
+    RFI_INST3_P(DT_F16, 2),
+    RFI_INST3(DT_F16, 1, 1, 1),
+    RFI_INST3(DT_F16, 1, 1, 2),
 };
 
 InstanceTable instances_f16() { return {k_table, (int)(sizeof(k_table) / sizeof(k_table[0]))}; }

@@ -11,6 +11,7 @@ static const Instance k_table[] = {
     RFI_INSTB_P(DT_F32, 1, 1),
     RFI_INSTB_P(DT_F32, 1, 2),
     RFI_INSTV_P(DT_F32, 1),
+    RFI_INST3_P(DT_F32, 1),
 };
 
 InstanceTable instances_f32() { return {k_table, (int)(sizeof(k_table) / sizeof(k_table[0]))}; }

@@ -12,6 +12,9 @@ static const Instance k_table[] = {
     RFI_INSTH_CH(DT_F16, 2, 8, 0), RFI_INSTH_CH(DT_F16, 2, 1, 1), RFI_INSTH_CH(DT_F16, 2, 2, 1),
     RFI_INSTH_CH(DT_F16, 2, 4, 1), RFI_INSTH_CH(DT_F16, 2, 8, 1), RFI_INSTH_CH(DT_F16, 1, 1, 0),
     RFI_INSTH_CH(DT_F16, 1, 1, 1),
+    RFI_INST3H_P(DT_F16, 2),
+    RFI_INST3H(DT_F16, 1, 1, 1),
+    RFI_INST3H(DT_F16, 1, 1, 2),
 };
 
 static const WpInstance wp_table[] = {

@@ -208,3 +208,23 @@ WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
 #define RFI_WPH_CH(DT, SPU, P)                                                              \
     RFI_WPH(DT, SPU, P, 1), RFI_WPH(DT, SPU, P, 2), RFI_WPH(DT, SPU, P, 4),                  \
         RFI_WPH(DT, SPU, P, 5)
+
+// The 96-register budget (LB = 3: 128-thread blocks, 5 per SM), two chunks of 1 or 2
+// load units in flight per lane; float32 arithmetic with the prefetch code (like the
+// other budgets), binary16 arithmetic without; plain batch kernels.
+#define RFI_INST3(DT, SPU, P, CH)                                                           \
+    {DT, SPU, P, CH, 0, 3, 0, 0, 0, 0, 1,                                                   \
+     (const void *)&rfi::k_block<DT, SPU, P, CH, false, 3, 0, false, false, false, true>,  \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, false, 0, false, false, true>}
+#define RFI_INST3H(DT, SPU, P, CH)                                                          \
+    {DT, SPU, P, CH, 0, 3, 2, 0, 0, 0, 0,                                                   \
+     (const void *)&rfi::k_block<DT, SPU, P, CH, false, 3, 2>,                              \
+     (const void *)&rfi::k_batch<DT, SPU, P, CH, false, 2, false, false, true>}
+#define RFI_INST3_P(DT, SPU)                                                                \
+    RFI_INST3(DT, SPU, 1, 1), RFI_INST3(DT, SPU, 1, 2), RFI_INST3(DT, SPU, 2, 1),           \
+        RFI_INST3(DT, SPU, 2, 2), RFI_INST3(DT, SPU, 4, 1), RFI_INST3(DT, SPU, 4, 2),       \
+        RFI_INST3(DT, SPU, 8, 1), RFI_INST3(DT, SPU, 8, 2)
+#define RFI_INST3H_P(DT, SPU)                                                               \
+    RFI_INST3H(DT, SPU, 1, 1), RFI_INST3H(DT, SPU, 1, 2), RFI_INST3H(DT, SPU, 2, 1),        \
+        RFI_INST3H(DT, SPU, 2, 2), RFI_INST3H(DT, SPU, 4, 1), RFI_INST3H(DT, SPU, 4, 2),    \
+        RFI_INST3H(DT, SPU, 8, 1), RFI_INST3H(DT, SPU, 8, 2)

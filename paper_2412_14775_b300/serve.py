@@ -120,13 +120,30 @@ class _Stream:
         self.ret_lo, self.ret_hi = self.offsets["flags"], self.offsets["stats"]
         self.out_host = torch.empty(self.ret_hi - self.ret_lo, dtype=torch.uint8, pin_memory=True)
 
-    def slot_views(self, pool, off):
+        # contexts whose blocks always complete T/M windows: counts kept here, without a
+        # call into the library per block
+        o = self.st.options
+        self.plain = not o.get("partial_windows") and not o.get("window_hop")
+        self.n_seen = 0
+
+    def next_counts(self):
+        """(averaging bins, windows) the next block completes; advances the stream."""
+        if self.plain:
+            K = self.st.K
+            n = (self.n_seen + self.T) // K - self.n_seen // K
+            nw = self.T // self.st.M
+        else:
+            n = self.st.outputs_for(self.T)
+            nw = self.st.windows_for(self.T)[0]
+        self.n_seen += self.T
+        return n, nw
+
+    def slot_views(self, pool, off, counts):
         """The block's input and outputs inside its pool slot, shaped for its numbers
-        of completed windows and bins."""
+        of completed bins and windows."""
         import torch
         R, F = self.st.R, self.st.F
-        n = self.st.outputs_for(self.T)
-        nw = self.st.windows_for(self.T)[0]
+        n, nw = counts
         words = (nw * self.st.bits_per_window + 31) // 32
         shapes = {"vis": (self.in_dtype, self.in_shape), "flags": (torch.int32, (R, words)),
                   "stats": (torch.float32, (3, R // F, nw)),
@@ -205,16 +222,22 @@ class ServingLoop:
 
     def _launch(self, items, cs):
         """Copy the blocks into their slots, run one batch, copy the results out; all on
-        CUDA stream cs."""
+        CUDA stream cs.  The batch receives addresses inside the pool (no tensor views
+        on this path)."""
         torch = self.torch
+        buf, base = self.pool.buf, self.pool.buf.data_ptr()
         with torch.cuda.stream(cs):
-            for s, _, k, off, views in items:
-                views["vis"].copy_(s.sources[k % len(s.sources)], non_blocking=True)
-        B.rfi_process_batch([s.st.ctx for s, *_ in items], [v["vis"] for *_, v in items],
-                            [self.T] * len(items), [v["flags"] for *_, v in items],
-                            [v["avg"] if v["avg"].numel() else None for *_, v in items],
-                            [v["weight"] if v["weight"].numel() else None for *_, v in items],
-                            [v["stats"] for *_, v in items], stream=cs)
+            for s, _, k, off, _ in items:
+                src = s.sources[k % len(s.sources)].reshape(-1)
+                n = s.parts[0][1]
+                buf[off:off + n].view(src.dtype).copy_(src, non_blocking=True)
+        ptr = {name: [base + off + s.offsets[name] for s, _, _, off, _ in items]
+               for name in ("vis", "flags", "avg", "weight", "stats")}
+        has_out = [c[0] > 0 for *_, c in items]
+        B.rfi_process_batch([s.st.ctx for s, *_ in items], ptr["vis"], [self.T] * len(items),
+                            ptr["flags"], [p if h else None for p, h in zip(ptr["avg"], has_out)],
+                            [p if h else None for p, h in zip(ptr["weight"], has_out)],
+                            ptr["stats"], stream=cs)
         if self.results_to_host:
             with torch.cuda.stream(cs):
                 for s, _, _, off, _ in items:
@@ -251,12 +274,13 @@ class ServingLoop:
             for ev, items, cs in inflight:
                 if ev.query():
                     tdone = ref.elapsed_time(ev) * 1e-3
-                    for s, ta, k, off, views in items:
+                    for s, ta, k, off, counts in items:
                         lat.append(tdone - ta)
                         samples += s.st.R * self.T
                         s.busy = False
                         s.done += 1
                         if self.record:
+                            views = s.slot_views(self.pool, off, counts)
                             self.outputs[s.idx].append(
                                 (k, {n: v.cpu().numpy().copy() for n, v in views.items()
                                      if n != "vis"}))
@@ -280,7 +304,7 @@ class ServingLoop:
                         break
                     ta, k = s.queue.popleft()
                     s.busy = True
-                    items.append((s, ta, k, off, s.slot_views(self.pool, off)))
+                    items.append((s, ta, k, off, s.next_counts()))
                 if items:
                     cs = free_cs.pop()
                     inflight.append((self._launch(items, cs), items, cs))

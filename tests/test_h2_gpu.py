@@ -29,6 +29,8 @@ SHAPES = [  # (stations, channels, M, K, T, options)
     (6, 16, 10, 20, 200, dict(window_F=2)),                      # the paper's 10 x 2
     (6, 16, 5, 20, 200, dict(window_F=4, lane_split=1, lanes_per_row=2)),   # 5 x 4
     (6, 16, 8, 64, 256, dict(lane_split=1, lanes_per_row=4)),
+    (6, 16, 16, 64, 256, dict(lanes_per_row=2, max_registers=96)),
+    (6, 16, 32, 64, 256, dict(lanes_per_row=4, max_registers=96)),
 ]
 
 

@@ -104,6 +104,11 @@ SHAPES = [
     ("f32", 5, 6, 16, 32, [64, 32], {"lanes_per_row": 4, "max_registers": 64}),
     ("f16", 5, 6, 20, 40, [40, 80], {"lanes_per_row": 2, "max_registers": 80}),
     ("f16", 4, 5, 5, 10, [10, 20], {"max_registers": 64}),
+    # the 96-register budget (two chunks of at most 2 load units in flight)
+    ("f32", 5, 6, 16, 64, [64, 192], {"lanes_per_row": 4, "max_registers": 96}),
+    ("f32", 4, 5, 10, 20, [40, 20], {"lanes_per_row": 1, "max_registers": 96}),
+    ("f16", 5, 6, 16, 32, [64, 96], {"lanes_per_row": 2, "max_registers": 96}),
+    ("f16", 4, 5, 5, 10, [10, 20], {"max_registers": 96}),
     # time-frequency footprints: the paper's 10 x 2 and 5 x 4 windows (W = 20)
     ("f32", 5, 4, 10, 20, [20, 40, 60], {"window_F": 2}),
     ("f16", 5, 4, 10, 30, [40, 20, 60], {"window_F": 2}),
