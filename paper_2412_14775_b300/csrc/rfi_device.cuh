@@ -187,6 +187,18 @@ __device__ __forceinline__ void load_unit(const char *p, Unit<16> &u) {
         : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3])
         : "l"(p));
 }
+// The window-parallel kernels give each lane whole windows, so with 16-byte units (odd
+// binary16 windows: 80 bytes for M = 5) one warp instruction reads 16 bytes of each of
+// 32 windows: half of every 32-byte sector.  Allocating those loads in L1 serves the
+// other half to the lane's next load from L1 instead of L2 (binary16 5 x 4 footprints
+// 136.8 -> 126.6 us, M = 5 216.2 -> 182.1 us, measured A/B).  32-byte units read whole
+// sectors and stream past L1 as elsewhere.
+__device__ __forceinline__ void load_unit_wp(const char *p, Unit<16> &u) {
+    asm("ld.global.nc.L2::256B.v4.b32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(u.r[0]), "=r"(u.r[1]), "=r"(u.r[2]), "=r"(u.r[3])
+        : "l"(p));
+}
+__device__ __forceinline__ void load_unit_wp(const char *p, Unit<32> &u) { load_unit(p, u); }
 
 // ---- debug-bounds build (-DRFI_DEBUG_BOUNDS) -----------------------------------
 // Every global access of the kernels is checked against the extent that the launch's

@@ -91,7 +91,7 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
 #pragma unroll
         for (int e = 0; e < CH; ++e) {
             const char *p = p0 + e * UB;
-            if (ok && rfi_in(p, UB, a.vis, vis_ext, a.err)) load_unit(p, u[e]);
+            if (ok && rfi_in(p, UB, a.vis, vis_ext, a.err)) load_unit_wp(p, u[e]);
             else u[e] = Unit<UB>{};
         }
     };
