@@ -43,22 +43,26 @@ def build(force: bool = False, verbose: bool = False, debug_bounds: bool = False
     lib = DEBUG_LIB if debug_bounds else LIB
     headers = [f for f in _inputs() if not f.endswith(".cu")]
     newest_header = max(os.path.getmtime(f) for f in headers)
-    if not force and os.path.exists(lib):
-        newest = max(os.path.getmtime(f) for f in _inputs())
-        if os.path.getmtime(lib) >= newest:
-            return lib
-    os.makedirs(os.path.dirname(lib), exist_ok=True)
     objdir = os.path.join(HERE, "_lib", "obj_debug" if debug_bounds else "obj")
+    objs = [os.path.join(objdir, src.replace(".cu", ".o")) for src in SOURCES]
+
+    def fresh(src, obj):
+        return (os.path.exists(obj) and os.path.getmtime(obj) >=
+                max(os.path.getmtime(os.path.join(CSRC, src)), newest_header))
+
+    # up to date: every object newer than its sources (a source edited while an earlier
+    # build ran leaves its object stale) and the library newer than every object
+    if (not force and os.path.exists(lib) and all(fresh(s, o) for s, o in zip(SOURCES, objs))
+            and os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs)):
+        return lib
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
     os.makedirs(objdir, exist_ok=True)
     extra = ["-DRFI_DEBUG_BOUNDS"] if debug_bounds else []
     # stale translation units compile in parallel, then one link step
-    procs, objs, tmps = [], [], []
-    for src in SOURCES:
+    procs, tmps = [], []
+    for src, obj in zip(SOURCES, objs):
         path = os.path.join(CSRC, src)
-        obj = os.path.join(objdir, src.replace(".cu", ".o"))
-        objs.append(obj)
-        if (not force and not verbose and os.path.exists(obj) and
-                os.path.getmtime(obj) >= max(os.path.getmtime(path), newest_header)):
+        if not force and not verbose and fresh(src, obj):
             continue
         tmp = obj + f".tmp{os.getpid()}"
         cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", "-o", tmp, path]

@@ -957,7 +957,7 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->compensated = ctx->kahan ? 1 : -1;
     opt->prefetch_bytes = ctx->pf_bytes;
     opt->prefetch_groups = ctx->pf_groups;
-    opt->max_registers = ctx->lb == 0 ? 128 : (ctx->lb == 1 ? 80 : 64);
+    opt->max_registers = ctx->lb == 0 ? 128 : (ctx->lb == 1 ? 80 : (ctx->lb == 3 ? 96 : 64));
     opt->window_F = ctx->F;
     opt->precision = ctx->prec;
     opt->loader = ctx->loader;

@@ -43,6 +43,7 @@ def test_h2_against_oracle(N, C, M, K, T, opts):
     data = synth.tiny_block(seed=41 + M, stations=N, channels=C, T=T, duty=0.08)["vis"]
     st = RfiStream(N, C, M, K, thr, "f16", precision=2, **opts)
     assert st.options["precision"] == 2
+    assert st.options["max_registers"] == opts.get("max_registers", 128)
     g = run_gpu(st, to_device_rows(data, "f16"))
     R = st.R
     v16 = data.reshape(R, T, 4, 2).astype(np.float16)
