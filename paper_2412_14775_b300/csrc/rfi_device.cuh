@@ -443,6 +443,18 @@ __device__ __forceinline__ float rowsum(float v, int PF) {
     return v;
 }
 
+// Packed pairs: both halves shuffled, then one f32x2 addition (the same additions, in
+// the same order, as two scalar reductions).
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(FULL, v.x, o), __shfl_xor_sync(FULL, v.y, o));
+}
+template <int P>
+__device__ __forceinline__ float2 allsum2(float2 v) {
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) v = add2(v, shfl_xor2(v, o));
+    return v;
+}
+
 // The averaged output of one closed bin of one row (end of Sec. 2.1): tot holds the
 // sums of (I, Q, U, V), re and im, over its unflagged samples and n their count; the
 // correlations are xx = (I + Q)/2, yy = (I - Q)/2, xy = (U - jV)/2, yx = (U + jV)/2, and
