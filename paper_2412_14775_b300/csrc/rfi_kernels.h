@@ -63,6 +63,7 @@ SwTable sw_instances_f16();   // rfi_inst_sw_f16.cu
 // Window-parallel lanes (rfi_wpar.cuh): the P lanes of a row take whole windows in turn.
 struct WpInstance {
     int dt, spu, P, ch, mixed;
+    int fs;                 // 1: the whole-round flag-bit path of straddling windows
     const void *fn;         // k_wpar<...>
     const void *batch_fn;   // k_batch_wp<...>
 };
@@ -182,13 +183,20 @@ WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
     RFI_SW(DT, SPU, P, 1, L), RFI_SW(DT, SPU, P, 2, L), RFI_SW(DT, SPU, P, 4, L)
 
 #define RFI_WP(DT, SPU, P, CH)                                                              \
-    {DT, SPU, P, CH, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH>,                         \
+    {DT, SPU, P, CH, 0, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH>,                      \
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH>}
 #define RFI_WPM(DT, SPU, P, CH)                                                             \
-    {DT, SPU, P, CH, 1, (const void *)&rfi::k_wpar<DT, SPU, P, CH, true>,                   \
+    {DT, SPU, P, CH, 1, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH, true>,                \
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, true>}
 #define RFI_WP_CH(DT, SPU, P)                                                               \
     RFI_WP(DT, SPU, P, 1), RFI_WP(DT, SPU, P, 2), RFI_WP(DT, SPU, P, 4), RFI_WP(DT, SPU, P, 5)
+// straddling windows (P M <= 32; 2 lanes per row, the footprints' split)
+#define RFI_WPS(DT, SPU, P, CH, PREC)                                                       \
+    {DT, SPU, P, CH, PREC, 1, (const void *)&rfi::k_wpar<DT, SPU, P, CH, PREC, true>,       \
+     (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, PREC, true>}
+#define RFI_WPS_CH(DT, SPU, PREC)                                                           \
+    RFI_WPS(DT, SPU, 2, 1, PREC), RFI_WPS(DT, SPU, 2, 2, PREC), RFI_WPS(DT, SPU, 2, 4, PREC), \
+        RFI_WPS(DT, SPU, 2, 5, PREC)
 #define RFI_WPM_CH(DT, SPU, P)                                                              \
     RFI_WPM(DT, SPU, P, 1), RFI_WPM(DT, SPU, P, 2), RFI_WPM(DT, SPU, P, 4),                  \
         RFI_WPM(DT, SPU, P, 5)
@@ -203,7 +211,7 @@ WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
     RFI_INSTH(DT, SPU, P, 1, K), RFI_INSTH(DT, SPU, P, 2, K), RFI_INSTH(DT, SPU, P, 4, K),  \
         RFI_INSTH(DT, SPU, P, 5, K)
 #define RFI_WPH(DT, SPU, P, CH)                                                             \
-    {DT, SPU, P, CH, 2, (const void *)&rfi::k_wpar<DT, SPU, P, CH, 2>,                      \
+    {DT, SPU, P, CH, 2, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH, 2>,                   \
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, 2>}
 #define RFI_WPH_CH(DT, SPU, P)                                                              \
     RFI_WPH(DT, SPU, P, 1), RFI_WPH(DT, SPU, P, 2), RFI_WPH(DT, SPU, P, 4),                  \

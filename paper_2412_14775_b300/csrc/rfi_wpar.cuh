@@ -25,7 +25,10 @@ namespace rfi {
 // summed sample by sample in one lane, in the tables' order, so statistics and flags
 // are those of the one-lane-per-row mixed kernel bit for bit (time-only windows).
 // PREC 2: binary16 Stokes arithmetic (accumulate_h2), as in process_group.
-template <int DT, int SPU, int P, int CH, int PREC = 0>
+// FS: windows that straddle flag words (M neither divides 32 nor is a multiple of it)
+// with P M <= 32: a whole round's flag bits are placed with one shift (the host picks
+// these instances for such windows only; the code costs the other shapes 2-3 %).
+template <int DT, int SPU, int P, int CH, int PREC = 0, bool FS = false>
 __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long group) {
     constexpr bool MIXED = PREC == 1, H2 = PREC == 2;
     static_assert(P >= 2, "one lane per row is the plain kernel");
@@ -153,38 +156,64 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
         // the row's P window flags of this round, in window order, to its lead lane
         const unsigned fb = __ballot_sync(FULL, ok && f);
         const unsigned rowbits = (fb >> (r * P)) & ((1u << P) - 1u);
+        auto flag_each = [&]() {
 #pragma unroll
-        for (int e = 0; e < P; ++e) {
-            const int wi = k * P - s + e;            // window of lane e of the row
-            if (wi < 0 || wi >= a.nwin) continue;
-            const bool fe = (rowbits >> e) & 1u;
-            if (fmode == 0) {
-                const int b0 = (wi * a.M) & 31;
-                if (fe) fword |= wmask << b0;
-                if (b0 + a.M == 32) {
-                    if (lead && rfi_in(fl_row + ((wi * a.M) >> 5), 4, a.flags, flags_ext, a.err))
-                        fl_row[(wi * a.M) >> 5] = fword;
-                    fword = 0;
-                }
-            } else if (fmode == 1) {
-                const int w0 = (wi * a.M) >> 5;
-                if (lead && rfi_in(fl_row + w0, 4ll * words_per_window, a.flags, flags_ext, a.err))
-                    for (int q = 0; q < words_per_window; ++q) fl_row[w0 + q] = fe ? FULL : 0u;
-            } else {
-                int lo = wi * a.M;
-                const int hi = lo + a.M;
-                while (lo < hi) {
-                    const int b0 = lo & 31;
-                    const int nb = min(hi - lo, 32 - b0);
-                    if (fe) fword |= (nb == 32 ? FULL : ((1u << nb) - 1u)) << b0;
-                    lo += nb;
-                    if ((lo & 31) == 0) {
-                        if (lead && rfi_in(fl_row + ((lo - 1) >> 5), 4, a.flags, flags_ext, a.err))
-                            fl_row[(lo - 1) >> 5] = fword;
+            for (int e = 0; e < P; ++e) {
+                const int wi = k * P - s + e;            // window of lane e of the row
+                if (wi < 0 || wi >= a.nwin) continue;
+                const bool fe = (rowbits >> e) & 1u;
+                if (fmode == 0) {
+                    const int b0 = (wi * a.M) & 31;
+                    if (fe) fword |= wmask << b0;
+                    if (b0 + a.M == 32) {
+                        uint32_t *w = fl_row + ((wi * a.M) >> 5);
+                        if (lead && rfi_in(w, 4, a.flags, flags_ext, a.err)) *w = fword;
                         fword = 0;
+                    }
+                } else if (fmode == 1) {
+                    const int w0 = (wi * a.M) >> 5;
+                    if (lead &&
+                        rfi_in(fl_row + w0, 4ll * words_per_window, a.flags, flags_ext, a.err))
+                        for (int q = 0; q < words_per_window; ++q) fl_row[w0 + q] = fe ? FULL : 0u;
+                } else {
+                    int lo = wi * a.M;
+                    const int hi = lo + a.M;
+                    while (lo < hi) {
+                        const int b0 = lo & 31;
+                        const int nb = min(hi - lo, 32 - b0);
+                        if (fe) fword |= (nb == 32 ? FULL : ((1u << nb) - 1u)) << b0;
+                        lo += nb;
+                        if ((lo & 31) == 0) {
+                            uint32_t *w = fl_row + ((lo - 1) >> 5);
+                            if (lead && rfi_in(w, 4, a.flags, flags_ext, a.err)) *w = fword;
+                            fword = 0;
+                        }
                     }
                 }
             }
+        };
+        if constexpr (FS) {
+            if (k * P - s >= 0 && k * P - s + P <= a.nwin) {
+                // a whole round of windows: its P M <= 32 bits, spread from the P
+                // flags, straddle at most one word boundary
+                uint32_t m = 0;
+#pragma unroll
+                for (int e = 0; e < P; ++e)
+                    if ((rowbits >> e) & 1u) m |= wmask << (e * a.M);
+                const int lo = (k * P - s) * a.M;
+                const int b0 = lo & 31;
+                const unsigned long long m64 = (unsigned long long)m << b0;
+                fword |= (uint32_t)m64;
+                if (b0 + P * a.M >= 32) {
+                    if (lead && rfi_in(fl_row + (lo >> 5), 4, a.flags, flags_ext, a.err))
+                        fl_row[lo >> 5] = fword;
+                    fword = (uint32_t)(m64 >> 32);
+                }
+            } else {
+                flag_each();
+            }
+        } else {
+            flag_each();
         }
         // flagged samples leave the average (end of Sec. 2.1).  The open bin needs
         // wpbin - wib more windows: the round's windows [first, e) belong to it; if the
@@ -258,20 +287,20 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
     }
 }
 
-template <int DT, int SPU, int P, int CH, int PREC = 0>
+template <int DT, int SPU, int P, int CH, int PREC = 0, bool FS = false>
 __global__ void __launch_bounds__(512, 1) k_wpar(const __grid_constant__ StreamArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
     overlap_prologue<DT, P>(a, group);
-    process_group_wp<DT, SPU, P, CH, PREC>(a, group);
+    process_group_wp<DT, SPU, P, CH, PREC, FS>(a, group);
 }
 
 // The persistent batch over window-parallel contexts (same task loop as k_batch).
-template <int DT, int SPU, int P, int CH, int PREC = 0>
+template <int DT, int SPU, int P, int CH, int PREC = 0, bool FS = false>
 __global__ void __launch_bounds__(512, 1) k_batch_wp(const __grid_constant__ BatchArgs b) {
     run_batch_tasks(b, [](const StreamArgs &a, long long group) {
-        process_group_wp<DT, SPU, P, CH, PREC>(a, group);
+        process_group_wp<DT, SPU, P, CH, PREC, FS>(a, group);
     });
 }
 
