@@ -44,14 +44,15 @@ def _peaks():
         return 6400.0, "fallback"
 
 
-KERNEL_SOURCES = ("rfi_device.cuh", "rfi_inst_f16.cu", "rfi_inst_f32.cu", "rfi_inst_h2.cu",
-                  "rfi_inst_pf_f16.cu",
-                  "rfi_inst_pf_f32.cu", "rfi_kernels.h")
+# The main flagging kernel (k_block) and every helper it calls are defined in
+# rfi_device.cuh; the instance tables only name template arguments, which the profile
+# records in the kernel's name.
+KERNEL_SOURCES = ("rfi_device.cuh",)
 
 
 def kernel_source_hash():
-    """Hash of the device code (kernel templates and their instances); a profile's
-    traffic figure is used only while the code it was taken from is unchanged."""
+    """Hash of the main kernel's device code; a profile's traffic figure is used only
+    while the code it was taken from is unchanged."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2412_14775_b300", "csrc")
     h = hashlib.sha256()

@@ -201,13 +201,17 @@ typedef enum {
  *                  stream's windows g with g mod P = j): no butterfly over the row's
  *                  lanes and one evaluation per window, for small windows and T x F
  *                  footprints, with P times shorter tasks than one lane per row.
- *                  lanes_per_row 2, 4 or 8 (P need not divide M), K/M >= lanes_per_row; the direct loader, the 128-register budget, plain
- *                  stores, no Kahan (precision = 1 with time-only windows: each window
- *                  still runs sample by sample in one lane, so its statistics and flags
- *                  equal those of the one-lane mixed kernel); excludes partial_windows,
- *                  adaptive and window_hop; a batch takes it with contexts of the same split and
- *                  shape.  Results differ from the default split only in the order in
- *                  which a bin's sums are added.
+ *                  lanes_per_row 2, 4 or 8 (P need not divide M), K/M >= lanes_per_row;
+ *                  the direct loader, the 128-register budget (or max_registers = 96
+ *                  for binary16 windows of odd length with 2 lanes: more resident
+ *                  warps, the same results, batched with the 128-register kernel),
+ *                  plain stores, no Kahan (precision = 1 with time-only windows: each
+ *                  window still runs sample by sample in one lane, so its statistics
+ *                  and flags equal those of the one-lane mixed kernel); excludes
+ *                  partial_windows, adaptive and window_hop; a batch takes it with
+ *                  contexts of the same split and shape.  Results differ from the
+ *                  default split only in the order in which a bin's sums are added
+ *                  (and the last bit of r's sum of squares).
  * The reduction order of a window depends only on (M, P, load unit), so two
  * contexts with the same shape give bit-identical results for the same data,
  * whether launched alone or inside a batch. */

@@ -118,9 +118,9 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
     for P in (2, 4, 8):
         if P * F > 32 or K // M < P:
             continue
-        for wpb in (4, 8):
-            o = dict(lanes_per_row=P, warps_per_block=wpb, max_registers=0, prefetch_groups=0,
-                     prefetch_bytes=1024, lane_split=1)
+        for wpb, regs in ((4, 0), (8, 0), (4, 96)):     # 96: binary16 odd windows only
+            o = dict(lanes_per_row=P, warps_per_block=wpb, max_registers=regs,
+                     prefetch_groups=0, prefetch_bytes=1024, lane_split=1)
             try:
                 stage1.append((run(o), o))
             except B.RfiError:

@@ -80,13 +80,13 @@ const SwInstance *find_sw(int dt, int spu, int P, int ch, int L) {
     return nullptr;
 }
 
-const WpInstance *find_wp(int dt, int spu, int P, int ch, int mixed, int fs) {
+const WpInstance *find_wp(int dt, int spu, int P, int ch, int mixed, int fs, int lb) {
     const WpTable tabs[] = {wp_instances_f32(), wp_instances_f16(), wp_instances_f16_h2()};
     for (const WpTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const WpInstance &in = t.items[i];
             if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.mixed == mixed &&
-                in.fs == fs)
+                in.fs == fs && in.lb == lb)
                 return &in;
         }
     return nullptr;
@@ -280,9 +280,13 @@ int choose_shape(rfi_ctx *c, int P_req) {
         // with the whole-round flag path (measured 3-5 % faster there, slower elsewhere)
         const bool straddle = 32 % c->M != 0 && c->M % 32 != 0 && P * c->M <= 32;
         const WpInstance *wi =
-            straddle && c->prec != 1 ? find_wp(dt, spu_w, P, c->ch, c->prec, 1) : nullptr;
-        if (!wi) wi = find_wp(dt, spu_w, P, c->ch, c->prec, 0);
+            straddle && c->prec != 1 ? find_wp(dt, spu_w, P, c->ch, c->prec, 1, c->lb) : nullptr;
+        if (!wi) wi = find_wp(dt, spu_w, P, c->ch, c->prec, 0, c->lb);
         c->inst = nullptr;
+        if (!wi && c->lb != 0)
+            return fail(RFI_EUNSUPPORTED, "lane_split = 1 with max_registers = 96 is built for "
+                                          "binary16 odd windows that straddle flag words, 2 "
+                                          "lanes per row");
         if (!wi) return fail(RFI_EUNSUPPORTED, "no window-parallel kernel for this shape");
         c->wp_fn = wi->fn;
         c->batch_fn = wi->batch_fn;
@@ -830,13 +834,13 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->H = hop;
     c->sw = hop != window_M;
     c->wp = o.lane_split == 1;
-    if (c->wp && (c->sw || c->loader != 0 || c->lb != 0 || c->vs || c->pw || c->ad ||
-                  o.compensated == 1)) {
+    if (c->wp && (c->sw || c->loader != 0 || (c->lb != 0 && c->lb != 3) || c->vs || c->pw ||
+                  c->ad || o.compensated == 1)) {
         delete c;
-        return fail(RFI_EUNSUPPORTED, "lane_split = 1 needs the direct loader, the "
-                                      "128-register budget, plain stores and no Kahan "
-                                      "summation, and excludes partial_windows, adaptive and "
-                                      "window_hop");
+        return fail(RFI_EUNSUPPORTED, "lane_split = 1 needs the direct loader, the 128- "
+                                      "(or, for binary16 odd windows, 96-) register budget, "
+                                      "plain stores and no Kahan summation, and excludes "
+                                      "partial_windows, adaptive and window_hop");
     }
     if (c->wp) c->kahan = 0;
     if (c->sw) {

@@ -64,6 +64,7 @@ SwTable sw_instances_f16();   // rfi_inst_sw_f16.cu
 struct WpInstance {
     int dt, spu, P, ch, mixed;
     int fs;                 // 1: the whole-round flag-bit path of straddling windows
+    int lb;                 // register budget (0: 128, 3: 96); batches take the 128 kernel
     const void *fn;         // k_wpar<...>
     const void *batch_fn;   // k_batch_wp<...>
 };
@@ -183,20 +184,28 @@ WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
     RFI_SW(DT, SPU, P, 1, L), RFI_SW(DT, SPU, P, 2, L), RFI_SW(DT, SPU, P, 4, L)
 
 #define RFI_WP(DT, SPU, P, CH)                                                              \
-    {DT, SPU, P, CH, 0, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH>,                      \
+    {DT, SPU, P, CH, 0, 0, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH>,                   \
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH>}
 #define RFI_WPM(DT, SPU, P, CH)                                                             \
-    {DT, SPU, P, CH, 1, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH, true>,                \
+    {DT, SPU, P, CH, 1, 0, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH, true>,             \
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, true>}
 #define RFI_WP_CH(DT, SPU, P)                                                               \
     RFI_WP(DT, SPU, P, 1), RFI_WP(DT, SPU, P, 2), RFI_WP(DT, SPU, P, 4), RFI_WP(DT, SPU, P, 5)
 // straddling windows (P M <= 32; 2 lanes per row, the footprints' split)
 #define RFI_WPS(DT, SPU, P, CH, PREC)                                                       \
-    {DT, SPU, P, CH, PREC, 1, (const void *)&rfi::k_wpar<DT, SPU, P, CH, PREC, true>,       \
+    {DT, SPU, P, CH, PREC, 1, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH, PREC, true>,    \
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, PREC, true>}
 #define RFI_WPS_CH(DT, SPU, PREC)                                                           \
     RFI_WPS(DT, SPU, 2, 1, PREC), RFI_WPS(DT, SPU, 2, 2, PREC), RFI_WPS(DT, SPU, 2, 4, PREC), \
         RFI_WPS(DT, SPU, 2, 5, PREC)
+// the 96-register budget for binary16 odd windows (one sample per 16-byte unit) with
+// the whole-round flag path, 2 lanes per row; batches run the 128-register kernel
+#define RFI_WPS3(DT, P, CH, PREC)                                                           \
+    {DT, 1, P, CH, PREC, 1, 3, (const void *)&rfi::k_wpar<DT, 1, P, CH, PREC, true, 3>,     \
+     (const void *)&rfi::k_batch_wp<DT, 1, P, CH, PREC, true>}
+#define RFI_WPS3_CH(DT, PREC)                                                               \
+    RFI_WPS3(DT, 2, 1, PREC), RFI_WPS3(DT, 2, 2, PREC), RFI_WPS3(DT, 2, 4, PREC),            \
+        RFI_WPS3(DT, 2, 5, PREC)
 #define RFI_WPM_CH(DT, SPU, P)                                                              \
     RFI_WPM(DT, SPU, P, 1), RFI_WPM(DT, SPU, P, 2), RFI_WPM(DT, SPU, P, 4),                  \
         RFI_WPM(DT, SPU, P, 5)
@@ -211,7 +220,7 @@ WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
     RFI_INSTH(DT, SPU, P, 1, K), RFI_INSTH(DT, SPU, P, 2, K), RFI_INSTH(DT, SPU, P, 4, K),  \
         RFI_INSTH(DT, SPU, P, 5, K)
 #define RFI_WPH(DT, SPU, P, CH)                                                             \
-    {DT, SPU, P, CH, 2, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH, 2>,                   \
+    {DT, SPU, P, CH, 2, 0, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH, 2>,                \
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, 2>}
 #define RFI_WPH_CH(DT, SPU, P)                                                              \
     RFI_WPH(DT, SPU, P, 1), RFI_WPH(DT, SPU, P, 2), RFI_WPH(DT, SPU, P, 4),                  \

@@ -287,8 +287,11 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
     }
 }
 
-template <int DT, int SPU, int P, int CH, int PREC = 0, bool FS = false>
-__global__ void __launch_bounds__(512, 1) k_wpar(const __grid_constant__ StreamArgs a) {
+// LB: the register budget (Bounds in rfi_device.cuh): 0 = 128 registers, 3 = 96 (20
+// resident warps per SM; built for the binary16 odd windows, which fit it unspilled).
+template <int DT, int SPU, int P, int CH, int PREC = 0, bool FS = false, int LB = 0>
+__global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
+    k_wpar(const __grid_constant__ StreamArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together

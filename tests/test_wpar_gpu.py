@@ -73,6 +73,39 @@ def test_window_parallel_splits_bit_identical():
         one.close(); st.close()
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_window_parallel_96_registers_bit_identical(prec):
+    """The 96-register budget of binary16 odd windows changes residency only: the bits
+    of the 128-register kernel, alone and in a batch with it."""
+    M, K, T = 5, 20, 200
+    thr = default_thresholds(5 * 4)
+    d = synth.tiny_block(seed=94, stations=8, channels=8, T=T, duty=0.08)["vis"]
+    v = to_device_rows(d, "f16")
+    opts = dict(lanes_per_row=2, window_F=4, lane_split=1, precision=prec, warps_per_block=4)
+    a = RfiStream(8, 8, M, K, thr, "f16", **opts)
+    b = RfiStream(8, 8, M, K, thr, "f16", max_registers=96, **opts)
+    assert b.options["max_registers"] == 96
+    x, y = a.process(v), b.process(v)
+    torch.cuda.synchronize()
+    for key in ("flags", "avg", "weight", "stats"):
+        assert torch.equal(x[key], y[key]), key
+    outs = [s.alloc_outputs(T) for s in (a, b)]
+    binding.rfi_process_batch([a.ctx, b.ctx], [v, v], [T, T], [o["flags"] for o in outs],
+                              [o["avg"] for o in outs], [o["weight"] for o in outs],
+                              [o["stats"] for o in outs])
+    c = RfiStream(8, 8, M, K, thr, "f16", **opts)
+    c.process(v)
+    z = c.process(v)
+    torch.cuda.synchronize()
+    for o in outs:
+        for key in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(o[key], z[key]), key
+    with pytest.raises(RfiError):            # built for binary16 odd windows only
+        RfiStream(8, 8, 8, 32, default_thresholds(8), "f16", lanes_per_row=2, lane_split=1,
+                  max_registers=96)
+    a.close(); b.close(); c.close()
+
+
 def test_window_parallel_option_checks():
     thr = default_thresholds(8)
     for bad in (dict(lane_split=1, lanes_per_row=1), dict(lane_split=1, lanes_per_row=16),
