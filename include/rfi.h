@@ -133,7 +133,14 @@ typedef enum {
  *                  rfi_check.  Needs float32 arithmetic and lanes_per_row <= 8 (all
  *                  register budgets; Kahan with 128); results equal the direct loader's
  *                  with the same lanes_per_row.  Single-stream calls only: batches run
- *                  the direct loader (bit-identical results).
+ *                  the direct loader (bit-identical results).  2 = the same staging
+ *                  with one TMA tensor-tile copy (cp.async.bulk.tensor.2d) per warp
+ *                  and stage instead of one copy per row: the block's rows as a 2-D
+ *                  tensor map of 8-byte elements (encoded per launch), a tile of the
+ *                  warp's rows x the padded row pitch (the extra bytes are the next
+ *                  samples, or zeros past the row; rows past the last read as zeros).
+ *                  lanes_per_row <= 4 (a tile's 128-byte aligned destination), at
+ *                  most 2048 bytes of a row per stage, no Kahan; the same results.
  *   tma_stage_windows  windows of every row per stage (0 = 1).
  *   tma_stages     stages in flight per warp (0 = 2); shared memory per block must
  *                  stay within 227 KB.

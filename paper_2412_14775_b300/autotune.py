@@ -113,6 +113,14 @@ def tune(stations, channels, M, K, thr, dtype, vis, cache_path=None, reps=30, ve
                     stage1.append((run(o), o))
                 except B.RfiError:      # no such kernel, or it does not fit the shared memory
                     continue
+        # the same staging with one tensor tile per warp and stage (lanes_per_row <= 4)
+        for G, NS in ((2, 2), (1, 3)):
+            o = dict(lanes_per_row=P, warps_per_block=4, max_registers=0, prefetch_groups=0,
+                     prefetch_bytes=1024, loader=2, tma_stage_windows=G, tma_stages=NS)
+            try:
+                stage1.append((run(o), o))
+            except B.RfiError:
+                continue
     # window-parallel lanes: the lanes of a row take whole windows in turn (a bin must
     # hold at least lanes_per_row windows)
     for P in (2, 4, 8):

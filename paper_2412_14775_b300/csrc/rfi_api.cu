@@ -57,16 +57,35 @@ const Instance *find_instance(int dt, int spu, int P, int ch, int kahan, int lb,
     return nullptr;
 }
 
-const void *find_tma(int dt, int spu, int P, int ch, int kahan, int lb) {
+const void *find_tma(int dt, int spu, int P, int ch, int kahan, int lb, int tile) {
     const TmaTable tabs[] = {tma_instances_f32(), tma_instances_f16()};
     for (const TmaTable &t : tabs)
         for (int i = 0; i < t.n; ++i) {
             const TmaInstance &in = t.items[i];
             if (in.dt == dt && in.spu == spu && in.P == P && in.ch == ch && in.kahan == kahan &&
                 in.lb == lb)
-                return in.fn;
+                return tile ? in.fn2 : in.fn;
         }
     return nullptr;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+typedef CUresult (*PFN_encode)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                               const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                               const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+PFN_encode get_encode_fn() {
+    static PFN_encode fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encode>(p);
+    });
+    return fn;
 }
 
 const SwInstance *find_sw(int dt, int spu, int P, int ch, int L) {
@@ -140,6 +159,8 @@ struct rfi_ctx {
     int prec;                           // precision option: 0, 1 (mixed) or 2 (binary16
                                         // Stokes arithmetic)
     int loader;                         // 0: direct loads, 1: TMA staging in shared memory
+                                        // (bulk copy per row), 2: the same with one tensor
+                                        // tile per warp
     const void *tma_fn;
     int tma_G, tma_NS;                  // windows per stage, stages per warp
     unsigned tma_pitch;
@@ -363,12 +384,19 @@ int choose_shape(rfi_ctx *c, int P_req) {
         return fail(RFI_EUNSUPPORTED, "buffered_stores needs the direct loader, float32 "
                                       "arithmetic, the 128-register budget, no Kahan, "
                                       "lanes_per_row <= 4 and 1, 2 or 4 load units per chunk");
-    if (c->loader == 1) {
-        c->tma_fn = c->prec ? nullptr : find_tma(dt, spu, P, c->ch, c->kahan, c->lb);
+    if (c->loader == 1 || c->loader == 2) {
+        c->tma_fn =
+            c->prec ? nullptr : find_tma(dt, spu, P, c->ch, c->kahan, c->lb, c->loader == 2);
         if (!c->tma_fn)
             return fail(RFI_EUNSUPPORTED, "no shared-memory loader for this shape (float32 "
                                           "arithmetic, lanes_per_row <= 8, Kahan only with "
-                                          "the 128-register budget)");
+                                          "the 128-register budget and the row copies)");
+        if (c->loader == 2 && !get_encode_fn())
+            return fail(RFI_EUNSUPPORTED, "loader = 2 needs cuTensorMapEncodeTiled");
+        // a tile copy's shared-memory destination (stage * rows * pitch, the pitch 16
+        // mod 128 bytes) is 128-byte aligned only for a multiple of 8 rows per warp
+        if (c->loader == 2 && (32 / P) % 8 != 0)
+            return fail(RFI_EUNSUPPORTED, "loader = 2 needs lanes_per_row <= 4");
         const unsigned SR = (unsigned)(c->tma_G * c->M * (dt == DT_F32 ? 32 : 16));
         // row pitch = 16 mod 128 bytes: consecutive rows start 4 banks apart, so the
         // lanes' 16-byte shared-memory reads spread over all banks
@@ -380,6 +408,9 @@ int choose_shape(rfi_ctx *c, int P_req) {
         if (c->wpb_auto)      // the largest block that fits the shared memory
             while (c->wpb > 1 && smem_for(c->wpb) > 227 * 1024) c->wpb >>= 1;
         c->tma_smem = smem_for(c->wpb);
+        if (c->loader == 2 && c->tma_pitch / 8 > 256)
+            return fail(RFI_EINVAL, "loader = 2 copies at most 2048 bytes of a row per stage "
+                                    "(%u): fewer windows per stage", c->tma_pitch);
         if (c->tma_smem > 227 * 1024)
             return fail(RFI_EINVAL, "shared-memory staging needs %zu bytes per block (max "
                                     "232448): fewer warps, stages or windows per stage",
@@ -569,7 +600,29 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
     void *args[] = {const_cast<StreamArgs *>(&a)};
     const void *fn = c->sw ? c->sw_fn : (c->wp ? c->wp_fn : (c->inst ? c->inst->block_fn : nullptr));
     cudaError_t e;
-    if (c->loader == 1) {
+    if (c->loader == 2) {
+        // the launch's rows as a 2-D tensor of 8-byte elements; one tile = the pitch of
+        // a stage row (its G windows and the rest of the pitch) x the warp's rows
+        const size_t SB = sample_bytes(c->dtype);
+        alignas(64) CUtensorMap tmap;
+        const cuuint64_t dims[2] = {(cuuint64_t)a.T * SB / 8, (cuuint64_t)a.R};
+        const cuuint64_t strides[1] = {(cuuint64_t)a.T * SB};
+        const cuuint32_t box[2] = {c->tma_pitch / 8, (cuuint32_t)RW};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = get_encode_fn()(
+            &tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(a.vis), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return fail(RFI_EINVAL, "tensor map for the block (error %d): rows of %lld bytes "
+                                    "must be a multiple of 16",
+                        (int)r, (long long)(a.T * SB));
+        void *args2[] = {const_cast<StreamArgs *>(&a), &tmap};
+        e = allow_smem(c->tma_fn, c->tma_smem);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args2,
+                                 c->tma_smem, st);
+    } else if (c->loader == 1) {
         e = allow_smem(c->tma_fn, c->tma_smem);
         if (e == cudaSuccess)
             e = cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args,
@@ -748,7 +801,7 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
         o.compensated < -1 || o.compensated > 1 || o.prefetch_bytes < 0 ||
         o.prefetch_bytes % 16 != 0 || o.prefetch_groups > 64 ||
         (o.max_registers != 0 && o.max_registers < 64) || o.window_F < 0 || o.precision < 0 ||
-        o.precision > 2 || o.loader < 0 || o.loader > 1 || o.tma_stage_windows < 0 ||
+        o.precision > 2 || o.loader < 0 || o.loader > 2 || o.tma_stage_windows < 0 ||
         o.tma_stage_windows > 64 || o.tma_stages < 0 || o.tma_stages > 8 ||
         o.debug_inject_wait_timeout < 0 || o.debug_inject_wait_timeout > 1 ||
         o.overlap_bytes < -1 || (o.overlap_bytes > 0 && o.overlap_bytes % 128 != 0) ||
@@ -1320,6 +1373,12 @@ int rfi_check(rfi_ctx *ctx, void *stream) {
         e = cudaMemcpy(&err, reinterpret_cast<int *>(ctx->counter + 2), sizeof(int),
                        cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "rfi_check");
+    if (err & 4) {
+        ctx->status = RFI_ESTATE;
+        return fail(RFI_ESTATE, "a tensor tile's shared-memory destination was not 128-byte "
+                                "aligned and its copy was skipped (error word %d); rfi_reset "
+                                "clears it", err);
+    }
     if (err & 1) {
         ctx->status = RFI_ETIMEOUT;
         return fail(RFI_ETIMEOUT, "a bounded wait in the kernel gave up (error word %d); "

@@ -19,6 +19,7 @@
 // block is kept per lane in the context's carry, so splitting a stream into blocks
 // at multiples of M gives bit-identical results.
 #pragma once
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -50,7 +51,9 @@ struct StreamArgs {
     unsigned pitch;         // bytes per row in a stage (G*M*SB padded to an odd x 16)
     unsigned tx_extra;      // extra bytes expected per stage (fault injection only)
     long long wait_limit;   // cycles a stage wait may take before it gives up
-    int *err;               // device error word: 1 = a bounded wait gave up
+    int *err;               // device error word: 1 = a bounded wait gave up, 2 = an
+                            // access outside its buffer (debug-bounds build), 4 = a
+                            // tensor tile copy skipped (unaligned destination)
     float c0;               // (W d + 1)/(W - 1), W = M F, Table 1 group 5
     float s_low, s_high, gamma, eps;
     float fM;               // W = M F as float (samples in one window)
@@ -162,6 +165,18 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
             "r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// One 2-D tile of a tensor map (rows x bytes of a row; 8-byte elements) into shared
+// memory, completed on an mbarrier.  x (elements) times 8 is a multiple of 16 bytes by
+// construction (the tile starts at a window boundary); rows and bytes beyond the
+// tensor are filled with zeros and still counted.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() {
@@ -507,9 +522,10 @@ __device__ __forceinline__ void store_bin(const StreamArgs &a, long long row, in
 // compiler schedules the window loop.
 // BAT: called from the persistent batch kernel (see the footprint sums below).
 template <int DT, int SPU, int P, int CH, bool KAHAN, bool DB = true, int PREC = 0,
-          bool TMA = false, bool VS = false, bool PW = false, bool AD = false,
+          int TMA = 0, bool VS = false, bool PW = false, bool AD = false,
           bool PFT = false, bool BAT = false>
-__device__ __forceinline__ void process_group(const StreamArgs &a, long long group) {
+__device__ __forceinline__ void process_group(const StreamArgs &a, long long group,
+                                              const void *tmap = nullptr) {
     constexpr bool MIXED = PREC == 1, H2 = PREC == 2;
     static_assert(!MIXED || (P == 1 && !KAHAN), "mixed precision runs one lane per row");
     static_assert(!H2 || DT == DT_F16, "binary16 Stokes arithmetic needs binary16 input");
@@ -824,6 +840,25 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
         auto issue = [&](int g) {
             const int st = g % NS;
             const int w0 = g * G;
+            if constexpr (TMA == 2) {
+                // one tile for the warp's RW rows: each row's G windows and the rest of
+                // its pitch (the next samples, or zeros past the row), the whole box
+                // counted whatever lies outside the tensor.  A tile copy needs a 128-byte
+                // aligned destination (RW * pitch is one for RW a multiple of 8, which
+                // the host requires); one that is not is skipped and flagged, and its
+                // stage wait then gives up
+                if (lane == 0) {
+                    unsigned char *dst = wbuf + (size_t)st * RW * a.pitch;
+                    mbar_arrive_expect_tx(&bars[st], RW * a.pitch + a.tx_extra);
+                    if ((smem_u32(dst) & 127u) == 0)
+                        tma_load_2d(dst, tmap, w0 * a.M * (SB / 8), (int)(group * RW),
+                                    &bars[st]);
+                    else
+                        atomicOr(a.err, 4);
+                }
+                __syncwarp();
+                return;
+            }
             const unsigned bytes = (unsigned)(min(G, a.nwin - w0) * a.M * SB);
             if (lane == 0) mbar_arrive_expect_tx(&bars[st], bytes * n_active + a.tx_extra);
             __syncwarp();
@@ -966,7 +1001,25 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_tma(const __grid_constant__ StreamArgs a) {
     const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (group * (32 / P) >= a.R) return;     // whole warp leaves together
-    process_group<DT, SPU, P, CH, KAHAN, false, false, true>(a, group);
+    process_group<DT, SPU, P, CH, KAHAN, false, false, 1>(a, group);
+}
+
+// The same staged loader with one TMA tile copy per warp and stage (tmap: the block's
+// rows as a 2-D tensor of 8-byte elements, box = pitch bytes x 32/P rows), instead of
+// one bulk copy per row; the same shared-memory layout, so the same results.
+template <int DT, int SPU, int P, int CH, bool KAHAN, int LB = 0>
+__global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
+    k_tma2(const __grid_constant__ StreamArgs a, const __grid_constant__ CUtensorMap tmap) {
+    const long long group = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (group * (32 / P) >= a.R) return;     // whole warp leaves together
+    process_group<DT, SPU, P, CH, KAHAN, false, false, 2>(a, group, &tmap);
+}
+
+// The tile-copy variant of an instance of the staged loader (built without Kahan).
+template <int DT, int SPU, int P, int CH, int K, int LB>
+inline const void *tma2_fn() {
+    if constexpr (K == 0) return (const void *)&k_tma2<DT, SPU, P, CH, false, LB>;
+    else return nullptr;
 }
 
 // Persistent batch: every warp takes (stream, row group) tasks from a device counter

@@ -37,7 +37,8 @@ const void *adapt_batch_fn();
 // The shared-memory (TMA) loader for one stream (batches use the direct loader).
 struct TmaInstance {
     int dt, spu, P, ch, kahan, lb;
-    const void *fn;         // k_tma<...>
+    const void *fn;         // k_tma<...>: one bulk copy per row and stage
+    const void *fn2;        // k_tma2<...>: one tensor tile per warp and stage (no Kahan)
 };
 struct TmaTable {
     const TmaInstance *items;
@@ -167,7 +168,8 @@ WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
     RFI_INSTB_CH(DT, SPU, 1, LB), RFI_INSTB_CH(DT, SPU, 2, LB), RFI_INSTB_CH(DT, SPU, 4, LB), \
         RFI_INSTB_CH(DT, SPU, 8, LB)
 #define RFI_TMA(DT, SPU, P, CH, K, LB)                                                      \
-    {DT, SPU, P, CH, K, LB, (const void *)&rfi::k_tma<DT, SPU, P, CH, (bool)K, LB>}
+    {DT, SPU, P, CH, K, LB, (const void *)&rfi::k_tma<DT, SPU, P, CH, (bool)K, LB>,         \
+     rfi::tma2_fn<DT, SPU, P, CH, K, LB>()}
 #define RFI_TMA_CH(DT, SPU, P, K, LB)                                                       \
     RFI_TMA(DT, SPU, P, 1, K, LB), RFI_TMA(DT, SPU, P, 2, K, LB),                           \
         RFI_TMA(DT, SPU, P, 4, K, LB), RFI_TMA(DT, SPU, P, 5, K, LB)

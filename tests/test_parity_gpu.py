@@ -130,6 +130,17 @@ SHAPES = [
                                      "tma_stage_windows": 2}),
     ("f16", 5, 4, 32, 64, [128, 64], {"loader": 1, "lanes_per_row": 8, "tma_stages": 3}),
     ("f32", 5, 4, 10, 20, [20, 40], {"loader": 1, "lanes_per_row": 2, "window_F": 2}),
+    # the same with one TMA tensor tile per warp and stage (rows past the last one read
+    # as zeros: 60 rows are 2 warps of 32 at one lane per row)
+    ("f32", 5, 4, 16, 64, [256, 128], {"loader": 2}),
+    ("f16", 5, 4, 16, 32, [96, 64], {"loader": 2, "tma_stage_windows": 3, "tma_stages": 3}),
+    ("f16", 4, 5, 5, 10, [10, 20, 40], {"loader": 2, "tma_stage_windows": 2}),
+    ("f32", 6, 3, 20, 40, [40, 60, 100], {"loader": 2, "tma_stages": 1, "warps_per_block": 2}),
+    ("f16", 5, 4, 10, 20, [20, 40], {"loader": 2, "window_F": 2}),
+    ("f32", 5, 6, 16, 64, [256, 128], {"loader": 2, "lanes_per_row": 4}),
+    ("f16", 6, 4, 16, 32, [96, 64], {"loader": 2, "lanes_per_row": 2, "max_registers": 64}),
+    ("f16", 5, 4, 32, 64, [128, 64], {"loader": 2, "lanes_per_row": 4, "tma_stages": 3}),
+    ("f32", 5, 4, 10, 20, [20, 40], {"loader": 2, "lanes_per_row": 2, "window_F": 2}),
     # statistics and flag words written 16 bytes at a time (falls back to plain
     # stores where T/M or the flag words per row are not multiples of 4)
     ("f16", 5, 4, 8, 32, [128, 64, 32], {"buffered_stores": 1, "lanes_per_row": 2}),
@@ -503,9 +514,13 @@ def test_tma_loader_bit_identical_to_direct_loads():
         a = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P).process(v)
         b = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P, loader=1, tma_stage_windows=2,
                       max_registers=64 if P > 1 else 0).process(v)
+        # tensor tiles: lanes_per_row <= 4 (a tile of at least 8 rows)
+        b2 = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P, loader=2, tma_stage_windows=2,
+                       max_registers=80 if P > 1 else 0).process(v) if P <= 4 else b
         torch.cuda.synchronize()
         for k in ("flags", "avg", "weight", "stats"):
             assert torch.equal(a[k], b[k]), (dtype, P, k)
+            assert torch.equal(a[k], b2[k]), (dtype, P, "tensor tiles", k)
         # a staged-loader context batches with direct-loader ones (the batch kernel
         # loads directly): same bits again
         c = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P, loader=1)
@@ -535,6 +550,8 @@ def test_buffered_stores_bit_identical_to_plain_stores():
             assert torch.equal(a[k], b[k]), (dtype, P, k)
     with pytest.raises(binding.RfiError):      # no buffered variant of the staged loader
         RfiStream(4, 4, 8, 64, thr8, "f32", loader=1, buffered_stores=1)
+    with pytest.raises(binding.RfiError):      # tensor tiles of 4 rows: not 128-B aligned
+        RfiStream(4, 4, 16, 64, thr8, "f32", loader=2, lanes_per_row=8)
     with pytest.raises(binding.RfiError):      # nor of the reduced register budgets
         RfiStream(4, 4, 8, 64, thr8, "f32", max_registers=64, buffered_stores=1)
 
@@ -696,15 +713,17 @@ def test_process_block_captures_in_a_cuda_graph():
     ref.close()
 
 
-def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
+@pytest.mark.parametrize("loader", [1, 2])
+def test_bounded_wait_reports_timeout_and_gpu_stays_usable(loader):
     """Failure detection without a GPU fault: with the injection option the staged
-    loader expects more bytes than it copies, so every stage wait gives up after about
-    1 ms; rfi_check reports RFI_ETIMEOUT, and the device keeps working."""
+    loader (row copies or tensor tiles) expects more bytes than it copies, so every
+    stage wait gives up after about 1 ms; rfi_check reports RFI_ETIMEOUT, and the
+    device keeps working."""
     M, K, T = 16, 64, 128
     thr = default_thresholds(M)
     d = synth.tiny_block(seed=32, stations=6, channels=4, T=T)["vis"]
     v = to_device_rows(d, "f32")
-    bad = RfiStream(6, 4, M, K, thr, "f32", loader=1, debug_inject_wait_timeout=1)
+    bad = RfiStream(6, 4, M, K, thr, "f32", loader=loader, debug_inject_wait_timeout=1)
     bad.process(v)
     with pytest.raises(RfiError) as ei:
         binding.rfi_check(bad.ctx)
@@ -712,7 +731,7 @@ def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
     with pytest.raises(RfiError):                                 # sticky until reset
         bad.process(v)
     binding.rfi_reset(bad.ctx)
-    good = RfiStream(6, 4, M, K, thr, "f32", loader=1)
+    good = RfiStream(6, 4, M, K, thr, "f32", loader=loader)
     out = good.process(v)
     binding.rfi_check(good.ctx)
     want = RfiStream(6, 4, M, K, thr, "f32",
