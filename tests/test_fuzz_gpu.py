@@ -29,7 +29,7 @@ def _draw(rng):
     opts["lanes_per_row"] = int(rng.choice(ps))
     roll = rng.random(6)
     if roll[0] < 0.25:
-        opts["loader"] = 1
+        opts["loader"] = 1 if roll[0] < 0.15 else 2      # row copies or tensor tiles
         opts["tma_stage_windows"] = int(rng.integers(1, 3))
         opts["tma_stages"] = int(rng.integers(2, 4))
         opts["warps_per_block"] = int(rng.choice([2, 4]))
