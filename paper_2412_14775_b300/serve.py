@@ -18,7 +18,9 @@ thresholds, open windows) stays on the device between blocks.  The loop
     block's flags, averages and weights (one contiguous range of its slot) back to
     pinned host memory (the per-window statistics stay on the device); batches
     admitted while others run overlap on the device;
-  * retires batches as their CUDA events complete, releasing their slots.
+  * retires batches as their CUDA events complete, releasing their slots; a stream's
+    next block may be admitted once the kernel of the batch holding its previous block
+    is done, while that batch's results are still being copied out.
 
 Block latency = completion of the batch's last copy (device clock) - arrival time
 (host clock), the clocks tied by an event recorded at start.  Everything computed runs
@@ -95,6 +97,7 @@ class _Stream:
         self.sources = sources                    # arriving blocks (host pinned or device)
         self.queue = collections.deque()          # (arrival_time, seq)
         self.busy = False
+        self.lat = []                             # latencies of this stream's blocks (s)
         self.done = 0
         R, F = self.st.R, self.st.F
         bits = self.st.bits_per_window
@@ -159,11 +162,14 @@ class ServingLoop:
     def __init__(self, stream_cfgs, M=16, K=256, T=256, thresholds=None, dtype="f16",
                  options=None, hbm_budget_bytes=8 << 30, max_batch=32, cuda_streams=3,
                  block_seconds=0.128, pool_blocks=2, seed=5, record_outputs=False,
-                 blocks=None, source="device", headroom_bytes=2 << 30, results_to_host=True):
+                 blocks=None, source="device", headroom_bytes=2 << 30, results_to_host=True,
+                 early_release=True):
         """source: "device" (blocks arrive in device memory, as from a GPU correlator,
         and are copied into the pool) or "host" (blocks arrive in pinned host memory and
         are copied to the device).  The block pool takes min(hbm_budget_bytes, free
-        device memory - headroom_bytes), measured once here."""
+        device memory - headroom_bytes), measured once here.  early_release: a stream's
+        next block may be admitted as soon as the kernel of the batch holding its previous
+        block is done (its state is final then), before that batch's result copies."""
         import torch
         from .thresholds import default_thresholds
         import synth
@@ -174,6 +180,7 @@ class ServingLoop:
         self.record = record_outputs
         self.source = source
         self.results_to_host = results_to_host
+        self.early_release = early_release
         if source not in ("device", "host"):
             raise ValueError("source is 'device' or 'host'")
         thr = thresholds or default_thresholds(M)
@@ -238,6 +245,10 @@ class ServingLoop:
                             ptr["flags"], [p if h else None for p, h in zip(ptr["avg"], has_out)],
                             [p if h else None for p, h in zip(ptr["weight"], has_out)],
                             ptr["stats"], stream=cs)
+        # the streams' state (carry, thresholds) is final once the kernel is done: their
+        # next blocks may be admitted while this batch's results are still being copied
+        ev_kernel = torch.cuda.Event()
+        ev_kernel.record(cs)
         if self.results_to_host:
             with torch.cuda.stream(cs):
                 for s, _, _, off, _ in items:
@@ -245,7 +256,7 @@ class ServingLoop:
                                      non_blocking=True)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(cs)
-        return ev
+        return ev_kernel, ev
 
     def run(self, duration, seed=0, arrivals=None):
         """Serve Poisson arrivals for `duration` seconds of wall time (then drain).
@@ -254,10 +265,11 @@ class ServingLoop:
         rng = np.random.default_rng(seed)
         arrivals = arrivals if arrivals is not None else self._schedule(duration, rng)
         ai = 0
-        inflight = []                 # (event, items, cuda_stream)
+        inflight = []                 # [kernel event, done event, items, cuda stream, freed]
         free_cs = list(self.cuda_streams)
         lat, samples, nbatches, batch_sizes, waits = [], 0, 0, [], 0
         h2d = d2h = 0
+        t_launch = t_retire = 0.0         # host seconds spent launching / retiring batches
         torch.cuda.synchronize()
         ref = torch.cuda.Event(enable_timing=True)
         ref.record()
@@ -270,12 +282,19 @@ class ServingLoop:
                 self.streams[si].queue.append((ta, k))
                 ai += 1
             # retire finished batches and release their slots
+            tr = time.perf_counter()
             still = []
-            for ev, items, cs in inflight:
+            for entry in inflight:
+                ev_k, ev, items, cs, freed = entry
+                if self.early_release and not freed and ev_k.query():
+                    for s, *_ in items:
+                        s.busy = False         # its next block may be admitted now
+                    entry[4] = True
                 if ev.query():
                     tdone = ref.elapsed_time(ev) * 1e-3
                     for s, ta, k, off, counts in items:
                         lat.append(tdone - ta)
+                        s.lat.append(tdone - ta)
                         samples += s.st.R * self.T
                         s.busy = False
                         s.done += 1
@@ -287,8 +306,9 @@ class ServingLoop:
                         self.pool.release(off, s.slot_bytes)
                     free_cs.append(cs)
                 else:
-                    still.append((ev, items, cs))
+                    still.append(entry)
             inflight = still
+            t_retire += time.perf_counter() - tr
             # admit: oldest head-of-queue first, while pool slots and batch slots allow
             if free_cs:
                 ready = sorted((s.queue[0][0], s.idx) for s in self.streams
@@ -307,7 +327,9 @@ class ServingLoop:
                     items.append((s, ta, k, off, s.next_counts()))
                 if items:
                     cs = free_cs.pop()
-                    inflight.append((self._launch(items, cs), items, cs))
+                    tl = time.perf_counter()
+                    inflight.append([*self._launch(items, cs), items, cs, False])
+                    t_launch += time.perf_counter() - tl
                     nbatches += 1
                     batch_sizes.append(len(items))
                     for s, *_ in items:
@@ -338,6 +360,10 @@ class ServingLoop:
             "source": self.source, "h2d_bytes": h2d, "d2h_bytes": d2h,
             "pool_gb": self.pool.nbytes / 1e9, "pool_peak_gb": self.pool.peak / 1e9,
             "free_gb_at_start": self.free_at_start / 1e9, "admission_waits": waits,
+            "host_launch_us_per_batch": 1e6 * t_launch / max(nbatches, 1),
+            "host_busy_frac": (t_launch + t_retire) / wall if wall > 0 else 0.0,
+            "per_stream_p99_s": [float(np.percentile(s.lat, 99)) if s.lat else None
+                                 for s in self.streams],
         }
 
     def close(self):
