@@ -590,8 +590,8 @@ def batched_extras(options, torch, steps=300, warmup=10):
 
 def serving_extras(seconds, options, torch):
     """The serving loop (binary16, M = 16, K = 256, blocks of 256 samples = 128 ms): the
-    32 mixed streams at 1-4x real time, the same at 4x and 6x that rate (4-16x and
-    6-24x real time per stream, 340 and 510 real-time streams offered, so batches
+    32 mixed streams at 1-4x real time, the same at 4x, 6x and 8x that rate (4-16x to
+    8-32x real time per stream, 340 to 680 real-time streams offered, so batches
     fill), the 62-station, 64-channel stream at 50x real time and backlogged, all with blocks arriving in device memory (a GPU correlator's output),
     and that stream fed from pinned host memory at 10x real time (the host link carries
     512 MB per block).  Every admitted block is copied into a slot of the device block
@@ -602,7 +602,7 @@ def serving_extras(seconds, options, torch):
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(0.5 * free, 32 << 30))
     cfgs = synth.serving_streams(seed=5, n=32)
-    for name, scale in (("mix32", 1.0), ("mix32_x4", 4.0), ("mix32_x6", 6.0)):
+    for name, scale in (("mix32", 1.0), ("mix32_x4", 4.0), ("mix32_x6", 6.0), ("mix32_x8", 8.0)):
         c = [dict(x, rho=x["rho"] * scale) for x in cfgs]
         loop = ServingLoop(c, M=16, K=256, T=256, dtype="f16", options=options,
                            hbm_budget_bytes=budget, max_batch=32, cuda_streams=3)
