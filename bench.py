@@ -592,7 +592,8 @@ def serving_extras(seconds, options, torch):
     """The serving loop (binary16, M = 16, K = 256, blocks of 256 samples = 128 ms): the
     32 mixed streams at 1-4x real time, the same at 4x, 6x and 8x that rate (4-16x to
     8-32x real time per stream, 340 to 680 real-time streams offered, so batches
-    fill), the 62-station, 64-channel stream at 50x real time and backlogged, all with blocks arriving in device memory (a GPU correlator's output),
+    fill; the 10x run reads each block where it arrived instead of copying it into the
+    pool), the 62-station, 64-channel stream at 50x real time and backlogged, all with blocks arriving in device memory (a GPU correlator's output),
     and that stream fed from pinned host memory at 10x real time (the host link carries
     512 MB per block).  Every admitted block is copied into a slot of the device block
     pool and its results are copied back to pinned host memory."""
@@ -602,10 +603,13 @@ def serving_extras(seconds, options, torch):
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(0.5 * free, 32 << 30))
     cfgs = synth.serving_streams(seed=5, n=32)
-    for name, scale in (("mix32", 1.0), ("mix32_x4", 4.0), ("mix32_x6", 6.0), ("mix32_x8", 8.0)):
+    for name, scale, copy_in in (("mix32", 1.0, True), ("mix32_x4", 4.0, True),
+                                 ("mix32_x6", 6.0, True), ("mix32_x8", 8.0, True),
+                                 ("mix32_x10_in_place", 10.0, False)):
         c = [dict(x, rho=x["rho"] * scale) for x in cfgs]
         loop = ServingLoop(c, M=16, K=256, T=256, dtype="f16", options=options,
-                           hbm_budget_bytes=budget, max_batch=32, cuda_streams=3)
+                           hbm_budget_bytes=budget, max_batch=32, cuda_streams=3,
+                           copy_in=copy_in)
         res[name] = dict(loop.run(seconds / 2, seed=11), streams=32, rho_scale=scale)
         loop.close()
         torch.cuda.empty_cache()

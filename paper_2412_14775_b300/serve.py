@@ -88,7 +88,7 @@ class DevicePool:
 
 
 class _Stream:
-    def __init__(self, idx, cfg, M, K, T, thr, dtype, options, sources):
+    def __init__(self, idx, cfg, M, K, T, thr, dtype, options, sources, copy_in=True):
         import torch
         self.idx = idx
         self.T = T
@@ -111,7 +111,7 @@ class _Stream:
         self.in_shape, self.in_dtype = tuple(src.shape), src.dtype
         # slot layout: input, then the outputs returned to the host (flags, averages,
         # weights: one contiguous range), then the statistics
-        self.parts = [("vis", src.numel() * src.element_size()),
+        self.parts = [("vis", src.numel() * src.element_size() if copy_in else 0),
                       ("flags", 4 * R * words_max), ("avg", 4 * R * n_out_max * 8),
                       ("weight", 4 * R * n_out_max), ("stats", 4 * 3 * (R // F) * n_win_max)]
         self.offsets = {}
@@ -163,13 +163,16 @@ class ServingLoop:
                  options=None, hbm_budget_bytes=8 << 30, max_batch=32, cuda_streams=3,
                  block_seconds=0.128, pool_blocks=2, seed=5, record_outputs=False,
                  blocks=None, source="device", headroom_bytes=2 << 30, results_to_host=True,
-                 early_release=True):
+                 early_release=True, copy_in=True):
         """source: "device" (blocks arrive in device memory, as from a GPU correlator,
         and are copied into the pool) or "host" (blocks arrive in pinned host memory and
         are copied to the device).  The block pool takes min(hbm_budget_bytes, free
         device memory - headroom_bytes), measured once here.  early_release: a stream's
         next block may be admitted as soon as the kernel of the batch holding its previous
-        block is done (its state is final then), before that batch's result copies."""
+        block is done (its state is final then), before that batch's result copies.
+        copy_in=False (device source only): the batch reads each block where it arrived
+        (the producer keeps it until the batch's kernel is done) and its slot holds the
+        outputs alone, so admission by free memory counts the outputs only."""
         import torch
         from .thresholds import default_thresholds
         import synth
@@ -183,6 +186,9 @@ class ServingLoop:
         self.early_release = early_release
         if source not in ("device", "host"):
             raise ValueError("source is 'device' or 'host'")
+        if not copy_in and source != "device":
+            raise ValueError("copy_in=False needs blocks in device memory")
+        self.copy_in = copy_in
         thr = thresholds or default_thresholds(M)
         opts = dict(options or {})
         self.streams = []
@@ -195,7 +201,7 @@ class ServingLoop:
                       for k in range(pool_blocks)]
             if source == "host":
                 bl = [b.cpu().pin_memory() for b in bl]
-            self.streams.append(_Stream(i, cfg, M, K, T, thr, dtype, opts, bl))
+            self.streams.append(_Stream(i, cfg, M, K, T, thr, dtype, opts, bl, copy_in))
         torch.cuda.synchronize()
         free, total = torch.cuda.mem_get_info()
         self.free_at_start = int(free)
@@ -233,13 +239,16 @@ class ServingLoop:
         on this path)."""
         torch = self.torch
         buf, base = self.pool.buf, self.pool.buf.data_ptr()
-        with torch.cuda.stream(cs):
-            for s, _, k, off, _ in items:
-                src = s.sources[k % len(s.sources)].reshape(-1)
-                n = s.parts[0][1]
-                buf[off:off + n].view(src.dtype).copy_(src, non_blocking=True)
+        if self.copy_in:
+            with torch.cuda.stream(cs):
+                for s, _, k, off, _ in items:
+                    src = s.sources[k % len(s.sources)].reshape(-1)
+                    n = s.parts[0][1]
+                    buf[off:off + n].view(src.dtype).copy_(src, non_blocking=True)
         ptr = {name: [base + off + s.offsets[name] for s, _, _, off, _ in items]
                for name in ("vis", "flags", "avg", "weight", "stats")}
+        if not self.copy_in:
+            ptr["vis"] = [s.sources[k % len(s.sources)].data_ptr() for s, _, k, _, _ in items]
         has_out = [c[0] > 0 for *_, c in items]
         B.rfi_process_batch([s.st.ctx for s, *_ in items], ptr["vis"], [self.T] * len(items),
                             ptr["flags"], [p if h else None for p, h in zip(ptr["avg"], has_out)],

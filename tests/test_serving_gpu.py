@@ -55,6 +55,37 @@ def test_serving_mix_equals_solo(options, T):
     loop.close()
 
 
+def test_serving_in_place_equals_solo():
+    """Blocks read where they arrived in device memory (no copy into the pool; slots
+    hold the outputs only): the same bits as the blocks processed alone."""
+    M, K, T = 16, 32, 48
+    cfgs = [dict(stations=n, channels=c, rho=r) for n, c, r in
+            ((5, 4, 3.0), (9, 8, 2.0), (7, 16, 4.0), (12, 4, 1.5))]
+    thr = default_thresholds(M)
+    blocks = [[synth.generate.device_block(c["stations"], c["channels"], T, seed=400 + 7 * i + k)
+               for k in range(3)] for i, c in enumerate(cfgs)]
+    loop = ServingLoop(cfgs, M=M, K=K, T=T, thresholds=thr, dtype="f16", block_seconds=0.01,
+                       max_batch=4, cuda_streams=3, record_outputs=True, blocks=blocks,
+                       hbm_budget_bytes=1 << 30, copy_in=False)
+    assert loop.streams[0].parts[0] == ("vis", 0)
+    stats = loop.run(0.5, seed=6)
+    assert stats["blocks"] > 100
+    opts = loop.streams[0].st.options
+    for i, cfg in enumerate(cfgs):
+        solo = RfiStream(cfg["stations"], cfg["channels"], M, K, thr, "f16",
+                         lanes_per_row=opts["lanes_per_row"],
+                         warps_per_block=opts["warps_per_block"])
+        for k, mixed in sorted(loop.outputs[i], key=lambda t: t[0]):
+            o = solo.process(blocks[i][k % 3].contiguous())
+            torch.cuda.synchronize()
+            for name in ("flags", "avg", "weight", "stats"):
+                assert np.array_equal(o[name].cpu().numpy(), mixed[name]), (i, k, name)
+        solo.close()
+    loop.close()
+    with pytest.raises(ValueError):           # host blocks must be copied to the device
+        ServingLoop(cfgs[:1], M=M, K=K, T=T, dtype="f16", source="host", copy_in=False)
+
+
 def test_serving_admission_respects_memory_budget():
     """With a block pool that holds one block at a time, batches hold a single block
     and every block is still served."""
