@@ -88,7 +88,8 @@ class DevicePool:
 
 
 class _Stream:
-    def __init__(self, idx, cfg, M, K, T, thr, dtype, options, sources, copy_in=True):
+    def __init__(self, idx, cfg, M, K, T, thr, dtype, options, sources, copy_in=True,
+                 n_host_buffers=1):
         import torch
         self.idx = idx
         self.T = T
@@ -121,7 +122,11 @@ class _Stream:
             o += DevicePool.rounded(n)
         self.slot_bytes = o
         self.ret_lo, self.ret_hi = self.offsets["flags"], self.offsets["stats"]
-        self.out_host = torch.empty(self.ret_hi - self.ret_lo, dtype=torch.uint8, pin_memory=True)
+        # pinned host buffers of the returned outputs, one per CUDA stream of the loop: a
+        # stream's blocks may be in several batches' result copies at once (a block is
+        # admitted once the previous one's kernel is done), block seq uses seq mod n
+        self.out_host = [torch.empty(self.ret_hi - self.ret_lo, dtype=torch.uint8,
+                                     pin_memory=True) for _ in range(max(1, n_host_buffers))]
 
         # contexts whose blocks always complete T/M windows: counts kept here, without a
         # call into the library per block
@@ -201,7 +206,8 @@ class ServingLoop:
                       for k in range(pool_blocks)]
             if source == "host":
                 bl = [b.cpu().pin_memory() for b in bl]
-            self.streams.append(_Stream(i, cfg, M, K, T, thr, dtype, opts, bl, copy_in))
+            self.streams.append(_Stream(i, cfg, M, K, T, thr, dtype, opts, bl, copy_in,
+                                        cuda_streams if early_release else 1))
         torch.cuda.synchronize()
         free, total = torch.cuda.mem_get_info()
         self.free_at_start = int(free)
@@ -260,9 +266,9 @@ class ServingLoop:
         ev_kernel.record(cs)
         if self.results_to_host:
             with torch.cuda.stream(cs):
-                for s, _, _, off, _ in items:
-                    s.out_host.copy_(self.pool.buf[off + s.ret_lo:off + s.ret_hi],
-                                     non_blocking=True)
+                for s, _, k, off, _ in items:
+                    dst = s.out_host[k % len(s.out_host)]
+                    dst.copy_(self.pool.buf[off + s.ret_lo:off + s.ret_hi], non_blocking=True)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(cs)
         return ev_kernel, ev
