@@ -62,7 +62,10 @@ typedef enum {
 /* Thresholds (Sections 2.1-2.3).  d: SK shape parameter; [s_low, s_high]: SK
  * acceptance interval; gamma: directional-statistic threshold; eps: the additive
  * constant of Tables 1 and 2 (added to S1^2 and to p).  Stored on the device as
- * float32 (the kernels compare in float32). */
+ * float32 (the kernels compare in float32).  No value may be NaN, d must be finite,
+ * eps finite and >= 0 and s_low <= s_high (else RFI_EINVAL).  Infinite bounds are
+ * allowed and switch a test off: s_low = -inf and s_high = +inf never flag by SK, and
+ * gamma >= 1 (r never exceeds 1) or +inf never by DS; gamma < 0 flags every window. */
 typedef struct {
     double d, s_low, s_high, gamma, eps;
 } rfi_thresholds;
