@@ -279,6 +279,8 @@ class ServingLoop:
         torch = self.torch
         rng = np.random.default_rng(seed)
         arrivals = arrivals if arrivals is not None else self._schedule(duration, rng)
+        for s in self.streams:
+            s.lat = []                # the statistics of this run only
         ai = 0
         inflight = []                 # [kernel event, done event, items, cuda stream, freed]
         free_cs = list(self.cuda_streams)
