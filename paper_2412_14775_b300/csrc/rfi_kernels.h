@@ -193,13 +193,14 @@ WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, true>}
 #define RFI_WP_CH(DT, SPU, P)                                                               \
     RFI_WP(DT, SPU, P, 1), RFI_WP(DT, SPU, P, 2), RFI_WP(DT, SPU, P, 4), RFI_WP(DT, SPU, P, 5)
-// straddling windows (P M <= 32; 2 lanes per row, the footprints' split)
+// straddling windows (P M <= 32; 2 or 4 lanes per row, the footprints' splits)
 #define RFI_WPS(DT, SPU, P, CH, PREC)                                                       \
     {DT, SPU, P, CH, PREC, 1, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH, PREC, true>,    \
      (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, PREC, true>}
 #define RFI_WPS_CH(DT, SPU, PREC)                                                           \
     RFI_WPS(DT, SPU, 2, 1, PREC), RFI_WPS(DT, SPU, 2, 2, PREC), RFI_WPS(DT, SPU, 2, 4, PREC), \
-        RFI_WPS(DT, SPU, 2, 5, PREC)
+        RFI_WPS(DT, SPU, 2, 5, PREC), RFI_WPS(DT, SPU, 4, 1, PREC),                         \
+        RFI_WPS(DT, SPU, 4, 2, PREC), RFI_WPS(DT, SPU, 4, 4, PREC), RFI_WPS(DT, SPU, 4, 5, PREC)
 // the 96-register budget for binary16 odd windows (one sample per 16-byte unit) with
 // the whole-round flag path, 2 lanes per row; batches run the 128-register kernel
 #define RFI_WPS3(DT, P, CH, PREC)                                                           \
