@@ -525,10 +525,12 @@ def test_tma_loader_bit_identical_to_direct_loads():
         # loads directly): same bits again
         c = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P, loader=1)
         e = RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P, max_registers=80 if P <= 8 else 0)
-        outs = [c.alloc_outputs(T), e.alloc_outputs(T)]
-        binding.rfi_process_batch([c.ctx, e.ctx], [v, v], [T, T], [o["flags"] for o in outs],
-                                  [o["avg"] for o in outs], [o["weight"] for o in outs],
-                                  [o["stats"] for o in outs])
+        bat = [c, e] + ([RfiStream(9, 11, M, K, thr, dtype, lanes_per_row=P, loader=2)]
+                        if P <= 4 else [])
+        outs = [x.alloc_outputs(T) for x in bat]
+        binding.rfi_process_batch([x.ctx for x in bat], [v] * len(bat), [T] * len(bat),
+                                  [o["flags"] for o in outs], [o["avg"] for o in outs],
+                                  [o["weight"] for o in outs], [o["stats"] for o in outs])
         torch.cuda.synchronize()
         for o in outs:
             for k in ("flags", "avg", "weight", "stats"):
