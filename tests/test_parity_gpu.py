@@ -402,8 +402,8 @@ def test_host_path_matches_device_path():
     for k in ("flags", "avg", "weight", "stats"):
         assert torch.equal(want[k].cpu(), got2[k]), k
     # both staged loaders in chunks of rows: the tensor-tile loader's map starts at the
-    # chunk's first row (180 rows in 3 chunks of 60: 2 warps of 32, the second part
-    # empty)
+    # chunk's first row (180 rows in 3 chunks of 60: 4 warps of 16 rows at 2 lanes per
+    # row, the last one partly empty)
     for loader in (1, 2):
         got3 = RfiStream(8, 5, M, K, thr, "f32", host_max_T=T, host_chunks=3,
                          loader=loader).process_host(hv)
