@@ -467,6 +467,37 @@ def test_edge_values():
         assert np.isfinite(g["avg"]).all() and np.isfinite(g["weight"]).all()
 
 
+def test_binary16_range_extremes():
+    """Binary16 input across its whole range: rows scaled from the smallest subnormal
+    (2^-24) to the largest finite value (65504), and a row whose xx + yy (131008)
+    exceeds binary16 but not float32.  The Stokes sums of two binary16 values are
+    formed in float32 (one rounding each), so statistics, flags and averages match the
+    FP64 oracle on the same binary16 values within the usual tolerances."""
+    M, K, T = 16, 32, 64
+    thr = default_thresholds(M)
+    S, C = 3, 4
+    R = S * (S + 1) // 2 * C
+    rng = np.random.default_rng(77)
+    scales = [2.0 ** -24, 2.0 ** -20, 2.0 ** -14, 2.0 ** -6, 1.0, 16.0, 256.0, 4096.0, 32768.0]
+    rows = np.empty((R, T, 4, 2), np.float32)
+    for r in range(R):
+        mag = rng.uniform(0.5, 1.0, (T, 4, 2)) * scales[r % len(scales)]
+        rows[r] = (mag * rng.choice([-1.0, 1.0], (T, 4, 2))).astype(np.float16)
+    rows[R - 1] = np.float16(65504.0)            # xx + yy = 131008: float32 only
+    rows[R - 2, :, :, 1] = 0.0
+    rows[R - 2, :, 0, 0] = np.float16(65504.0)   # xx = 65504 and yy = -65504 (I = 0)
+    rows[R - 2, :, 3, 0] = np.float16(-65504.0)
+    rows[R - 3, ::3] = np.float16(2.0 ** -24)    # subnormal samples among normal ones
+    rows[R - 3, 1::3] = np.float16(-(2.0 ** -24))
+    assert np.isfinite(rows).all() and np.abs(rows).max() == 65504.0
+    st = RfiStream(S, C, M, K, thr, "f16")
+    g = run_gpu(st, to_device_rows(rows, "f16"))
+    o = oracle.OracleStream(R, M, K, **thr).process(rows.astype(np.float16))
+    compare(g, o, thr, M, K)
+    assert np.isfinite(g["tau"]).all() and np.isfinite(g["avg"]).all()
+    st.close()
+
+
 def test_threshold_update():
     M, K, T = 16, 64, 128
     thr = default_thresholds(M)
