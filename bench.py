@@ -11,6 +11,7 @@ Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on 
 bounded sample of the same workload instead.
 """
 import argparse
+import collections
 import json
 import math
 import os
@@ -297,7 +298,7 @@ def footprint_extras(torch, cs, peak, steps=500, warmup=10, only=None):
                 fixed = {"window_F": F, **({"precision": 2} if prec else {})}
                 best, _ = autotune.tune(62, 64, M, K, thr, dtype, vis, fixed=fixed,
                                         cache_path=autotune.TUNED_PATH, write_cache=False)
-                opts = autotune.options_of(best)
+                opts = dict(autotune.options_of(best), **PIPELINED)
                 st = RfiStream(62, 64, M, K, thr, dtype, **opts)
                 out = st.alloc_outputs(T)
                 k, _, _, _ = time_kernel(st, vis, out, steps, warmup, torch, cs)
@@ -408,7 +409,7 @@ def fp16_extras(vis32, vis16, tuned, torch, cs, peak, dev, steps, warmup):
         b16 = algo_bytes(R, T, Mw, 256, 1, 16)
         entry = {}
         for mode, fixed in (("storage", {}), ("h2", {"precision": 2})):
-            o16opts = tuned(Mw, "f16", vis16, fixed)
+            o16opts = dict(tuned(Mw, "f16", vis16, fixed), **PIPELINED)
             s16 = RfiStream(62, 64, Mw, 256, thr, "f16", **o16opts)
             o16 = s16.alloc_outputs(T, device=dev)
             k16, _, _, _ = time_kernel(s16, vis16, o16, steps, warmup, torch, cs)
@@ -643,23 +644,37 @@ def serving_extras(seconds, options, torch):
     return res
 
 
+# The timed workloads are streams of blocks whose launches share no buffer with the
+# launches still in flight (each block closes its averaging bins, outputs go to a ring of
+# output sets), so their contexts let such launches start without waiting for the one
+# before (option independent_launches; the library checks every launch and orders the
+# others as before).
+PIPELINED = {"independent_launches": 1}
+N_OUT_SETS = 16
+
+
 def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler_index=None,
-                serial_steps=100, n_out_sets=4):
+                serial_steps=100, n_out_sets=N_OUT_SETS):
     """Warm up, then time `steps` back-to-back launches with CUDA events on the launching
     stream around the whole run; returns the mean launch period (device time of the
     flagging kernel in a stream of calls, launch overlap included), the run's total and
     the clock record.  Step i reads vis[i % len(vis)] (vis: one tensor or a list) and
     writes the (i % n_out_sets)-th of n_out_sets output sets, `out` and copies of it: a
     ring of output buffers, as a pipeline keeps them (one set reused every step would let
-    the outputs stay in L2 and never reach DRAM).  Then `serial_steps` launches with an
+    the outputs stay in L2 and never reach DRAM; a launch that writes the set of a launch
+    still possibly running is ordered after it, so the ring is 16 deep).  Then `serial_steps` launches with an
     event pair around each one (which keeps consecutive launches from overlapping): their
     mean duration, reported beside it."""
+    from paper_2412_14775_b300 import binding
     vis_l = list(vis) if isinstance(vis, (list, tuple)) else [vis]
     outs = [out] + [{k: torch.empty_like(x) for k, x in out.items()}
                     for _ in range(n_out_sets - 1)]
+    orders = collections.Counter()
 
-    def step(i):
+    def step(i, count=False):
         stream_obj.process(vis_l[i % len(vis_l)], out=outs[i % len(outs)], stream=cuda_stream)
+        if count:
+            orders[binding.rfi_last_launch(stream_obj.ctx)] += 1
 
     for i in range(warmup):
         step(i)
@@ -671,7 +686,7 @@ def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler
     t_all1 = torch.cuda.Event(enable_timing=True)
     t_all0.record(cuda_stream)
     for i in range(steps):
-        step(i)
+        step(i, count=True)
     t_all1.record(cuda_stream)
     torch.cuda.synchronize()
     if sampler:
@@ -690,6 +705,7 @@ def time_kernel(stream_obj, vis, out, steps, warmup, torch, cuda_stream, sampler
         for k in out:
             out[k].copy_(last[k])
     serial = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in ev) if ev else None
+    time_kernel.last_orders = dict(orders)     # how the timed launches were ordered
     return total / steps, total, serial, (sampler.summary() if sampler else None)
 
 
@@ -854,7 +870,8 @@ def main():
     vis_main = vis32 if main_dt == "f32" else vis32.half()
     if args.precision and main_dt != "f16":
         ap.error("--precision 2 needs --dtype f16")
-    opts = tuned(M, main_dt, vis_main, {"precision": 2} if args.precision else None)
+    opts = dict(tuned(M, main_dt, vis_main, {"precision": 2} if args.precision else None),
+                **PIPELINED)
     prof_key = main_dt + ("_h2" if args.precision else "")
     st = RfiStream(62, 64, M, K, thr, main_dt, **opts)
     out = st.alloc_outputs(T, device=dev)
@@ -862,10 +879,11 @@ def main():
 
     if ws > 1:
         dist.barrier()
-    # two input blocks in turn (each larger than L2) and a ring of four output sets
+    # two input blocks in turn (each larger than L2) and a ring of output sets
     kern, total, kern_serial, clocks = time_kernel(st, [vis_main, vis_main.clone()], out,
                                                    args.steps, args.warmup,
                                                    torch, cs, sampler_index=local)
+    time_kernel.last_orders_main = time_kernel.last_orders
     samples = R * T
     out_bytes = sum(x.numel() * x.element_size() for x in out.values())
     # every rank processes its own block (weak scaling): total samples of all ranks over
@@ -972,17 +990,18 @@ def main():
             "data": "synthetic",
             "config": dict(WORKLOAD, dtype="complex64" if main_dt == "f32" else "complex32 (binary16)",
                            l2=f"two input blocks of {R * T * sbytes / 1e9:.2f} GB (> 126 MB L2) in "
-                              f"turn, outputs into a ring of 4 sets ({4 * out_bytes / 1e6:.0f} MB), "
-                              "no flush",
+                              f"turn, outputs into a ring of {N_OUT_SETS} sets "
+                              f"({N_OUT_SETS * out_bytes / 1e6:.0f} MB), no flush",
                            options={k: st.options[k] for k in
                                     ("lanes_per_row", "warps_per_block", "prefetch_bytes",
-                                     "prefetch_groups")}),
+                                     "prefetch_groups", "independent_launches")}),
             "hbm_gbs": achieved * ws,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(prof_key),
                          "ncu_dram_gbs": profiled_dram_gbs(prof_key),
                          "peak_kind": peak_kind, "kernel_us": kern * 1e6,
                          "kernel_us_serialised": kern_serial * 1e6,
+                         "launch_orders": getattr(time_kernel, "last_orders_main", None),
                          "algorithmic_bytes_per_launch": bytes_launch},
             "frac_of_8tbs": achieved / 8000.0,
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,

@@ -190,7 +190,28 @@ typedef enum {
  *                  identical; back-to-back calls lose less time at each launch
  *                  boundary.  0 = 512 bytes (default), -1 = off, else a multiple of
  *                  128.  Launches recorded into a CUDA graph, the shared-memory loader
- *                  and batches keep plain stream order.
+ *                  and batches keep plain stream order.  The library orders every
+ *                  flagging launch against the flagging launches (of any context, and
+ *                  of rfi_process_block_noalloc) that may still run on the same stream:
+ *                  it waits as described only while each of those waited for the one
+ *                  before it, and is otherwise a plain launch (rfi_last_launch).
+ *   independent_launches  1 = a flagging launch that reads no byte that a flagging
+ *                  launch still possibly running on the stream writes, and writes no
+ *                  byte that one reads or writes (input, flags, statistics, averages,
+ *                  weights, and the context state it uses: the open bin's carry when a
+ *                  block starts or ends inside a bin, the open window's samples with
+ *                  partial_windows, the thresholds' state with adaptive, the pending
+ *                  hop with window_hop), does not wait for the kernel before it: its
+ *                  blocks start their work while the launches before it drain.  For a
+ *                  stream of blocks that each close their bins (K dividing T) written
+ *                  into a ring of output buffers, consecutive launches overlap fully.
+ *                  The caller promises that no kernel of its own that lets its
+ *                  successor start early (griddepcontrol.launch_dependents,
+ *                  cudaTriggerProgrammaticLaunchCompletion) writes a block's input or
+ *                  reads its outputs between two calls on the stream; plain kernels,
+ *                  copies and events in between need nothing.  Results are identical.
+ *                  At most 32 launches are kept in flight; the next is a plain launch.
+ *                  0 = off (default).
  *   window_hop     overlapping windows: a window of M samples starts every H =
  *                  window_hop samples (0 or M = no overlap, the paper's windows).
  *                  Only H = M/2 is built: every sample lies in two windows and is
@@ -246,6 +267,7 @@ typedef struct {
     int overlap_bytes;
     int window_hop;
     int lane_split;
+    int independent_launches;
 } rfi_options;
 
 /* Parameters of the online SK thresholds (option `adaptive`). */
@@ -285,6 +307,14 @@ int rfi_windows_for(const rfi_ctx *ctx, int T, int *n_win, long long *first_samp
 
 /* The launch shape the context uses (after automatic choice). */
 int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt);
+
+/* How the context's last single-stream flagging launch was ordered on its stream
+ * (options overlap_bytes and independent_launches; no counterpart in the paper, a
+ * diagnostic): *order = 2 independent (its blocks did not wait for the kernel before),
+ * 1 waiting (they waited for it before touching memory), 0 plain (ordered after all
+ * earlier work: overlap off, the staged loaders, or the launches in flight did not
+ * allow either), -1 none yet or recorded into a CUDA graph. */
+int rfi_last_launch(const rfi_ctx *ctx, int *order);
 
 /* Replace the thresholds (takes effect for work issued afterwards). */
 int rfi_set_thresholds(rfi_ctx *ctx, const rfi_thresholds *thr);

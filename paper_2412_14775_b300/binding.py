@@ -26,7 +26,7 @@ EXPORTED = ["rfi_create", "rfi_create_ex", "rfi_rows", "rfi_outputs_for", "rfi_g
             "rfi_batch_graph_destroy", "rfi_reset", "rfi_destroy", "rfi_status_str",
             "rfi_last_error", "rfi_process_block_noalloc", "rfi_check", "rfi_state_size",
             "rfi_get_state", "rfi_set_state", "rfi_windows_for", "rfi_set_adaptation",
-            "rfi_adaptive_state"]
+            "rfi_adaptive_state", "rfi_last_launch"]
 
 # Fixed size of the library's no-allocation scratch (RFI_NOALLOC_SCRATCH_BYTES).
 RFI_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -58,7 +58,8 @@ class rfi_options(ctypes.Structure):
                 ("tma_stages", ctypes.c_int), ("debug_inject_wait_timeout", ctypes.c_int),
                 ("buffered_stores", ctypes.c_int), ("partial_windows", ctypes.c_int),
                 ("adaptive", ctypes.c_int), ("overlap_bytes", ctypes.c_int),
-                ("window_hop", ctypes.c_int), ("lane_split", ctypes.c_int)]
+                ("window_hop", ctypes.c_int), ("lane_split", ctypes.c_int),
+                ("independent_launches", ctypes.c_int)]
 
 
 _lib = None
@@ -84,6 +85,7 @@ def load_library(path=None):
         "rfi_outputs_for": ([vp, ip, ctypes.POINTER(ip)], ip),
         "rfi_windows_for": ([vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_longlong)], ip),
         "rfi_get_options": ([vp, ctypes.POINTER(rfi_options)], ip),
+        "rfi_last_launch": ([vp, ctypes.POINTER(ip)], ip),
         "rfi_set_thresholds": ([vp, ctypes.POINTER(rfi_thresholds)], ip),
         "rfi_set_adaptation": ([vp, ctypes.POINTER(rfi_adaptation)], ip),
         "rfi_adaptive_state": ([vp, vp, ctypes.c_size_t, ip, vp], ip),
@@ -209,6 +211,18 @@ def rfi_get_options(ctx):
     o = rfi_options()
     _check(load_library().rfi_get_options(ctx, ctypes.byref(o)), "rfi_get_options")
     return {f: getattr(o, f) for f, _ in rfi_options._fields_}
+
+
+# How rfi_last_launch reports the order of a context's last flagging launch.
+LAUNCH_ORDER = {-1: "none", 0: "plain", 1: "waiting", 2: "independent"}
+
+
+def rfi_last_launch(ctx):
+    """Order of the context's last flagging launch on its stream: 'plain', 'waiting',
+    'independent' or 'none' (see rfi_last_launch in rfi.h)."""
+    o = ctypes.c_int()
+    _check(load_library().rfi_last_launch(ctx, ctypes.byref(o)), "rfi_last_launch")
+    return LAUNCH_ORDER[o.value]
 
 
 def rfi_set_thresholds(ctx, thresholds):

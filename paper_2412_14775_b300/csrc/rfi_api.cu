@@ -21,6 +21,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
@@ -174,6 +175,11 @@ struct rfi_ctx {
     rfi_adaptation adp;
     int pf_bytes, pf_groups;            // L2 prefetch group size and distance
     int ovl;                            // launch overlap: bytes per row requested early
+    int indep;                          // independent_launches: a launch that shares no
+                                        // buffer with the flagging launches that may still
+                                        // run on the stream does not wait for them
+    int last_launch;                    // how the last flagging launch was ordered (-1 none,
+                                        // 0 plain, 1 waiting, 2 independent)
     int sw, H;                          // overlapping windows: a window every H samples
     const void *sw_fn;                  // k_slide<...>
     float *sw_buf;                      // [R][1][8] totals, [R][P][1][8] averaging sums of
@@ -592,6 +598,121 @@ bool capturing(cudaStream_t st) {
     return cs != cudaStreamCaptureStatusNone;
 }
 
+// ---- launch ordering of the flagging kernels -----------------------------------------
+// k_block, k_wpar and k_slide execute griddepcontrol.launch_dependents on entry, so a
+// launch made after one of them with the programmatic-serialisation attribute may start
+// once all of its blocks have started, while it (and, by the same rule, launches before
+// it) still runs.  Per (device, stream) the host keeps the byte ranges that the flagging
+// launches since the last fully ordered one read and write ("in flight": those that may
+// still run when the next launch starts) and orders every new flagging launch:
+//   independent (2): it reads nothing that a launch in flight writes and writes nothing
+//       that one reads or writes, and the context allows it (independent_launches):
+//       launched with the attribute, its blocks start at once;
+//   waiting (1): otherwise, if every launch in flight waited for the one before it (so
+//       the completion of the last implies that of all): launched with the attribute,
+//       its blocks wait for the kernel before it (griddepcontrol.wait) first;
+//   plain (0): otherwise (or overlap off, or more than kMaxInFlight in flight): a plain
+//       launch, after everything before it on the stream.
+// Kernels that do not trigger early (the staged loaders, the batch and state-update
+// kernels, and graphs of them) are launched plain; after them nothing is in flight.
+// Work that other code puts on the stream between two calls is either a plain stream
+// operation (ordered after everything before it) or a kernel of the caller's; the
+// independent order assumes that no kernel of the caller's that triggers early writes
+// a block's input or reads its outputs between two calls (the option's contract).
+struct Span {
+    uintptr_t lo, hi;                   // [lo, hi)
+};
+struct Footprint {
+    int nr = 0, nw = 0;
+    Span r[6], w[10];
+    void read(const void *p, size_t bytes) { add(r, nr, 6, p, bytes); }
+    void write(const void *p, size_t bytes) { add(w, nw, 10, p, bytes); }
+    static void add(Span *s, int &n, int cap, const void *p, size_t bytes) {
+        if (!p || !bytes) return;
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(p);
+        if (n < cap) s[n++] = Span{lo, lo + bytes};
+        else s[cap - 1] = Span{0, ~uintptr_t(0)};   // cannot happen; stay conservative
+    }
+    static Footprint everything() {
+        Footprint f;
+        f.r[f.nr++] = Span{0, ~uintptr_t(0)};
+        f.w[f.nw++] = Span{0, ~uintptr_t(0)};
+        return f;
+    }
+};
+bool spans_meet(const Span *a, int na, const Span *b, int nb) {
+    for (int i = 0; i < na; ++i)
+        for (int k = 0; k < nb; ++k)
+            if (a[i].lo < b[k].hi && b[k].lo < a[i].hi) return true;
+    return false;
+}
+// x must wait for y: x reads what y writes, or writes what y reads or writes
+bool clashes(const Footprint &x, const Footprint &y) {
+    return spans_meet(x.r, x.nr, y.w, y.nw) || spans_meet(x.w, x.nw, y.r, y.nr) ||
+           spans_meet(x.w, x.nw, y.w, y.nw);
+}
+struct InFlight {
+    std::vector<Footprint> fp;
+    bool all_waited = true;
+};
+constexpr size_t kMaxInFlight = 32;
+std::mutex g_order_mu;
+std::map<std::pair<int, uintptr_t>, InFlight> g_order;
+
+InFlight &in_flight(int device, cudaStream_t st) {
+    return g_order[{device, reinterpret_cast<uintptr_t>(st)}];
+}
+
+// The buffers one flagging launch reads and writes (rows r0 .. r0 + a.R of the stream).
+Footprint footprint_of(const rfi_ctx *c, const StreamArgs &a) {
+    Footprint f;
+    const size_t R = (size_t)a.R, SB = (size_t)sample_bytes(c->dtype);
+    f.read(a.vis, R * (size_t)a.T * SB);
+    const size_t carry_bytes = R * (size_t)c->P * 9 * sizeof(float);
+    if (c->sw) {
+        // overlapping windows: the bin carry and the pending hop's state, both ways
+        f.read(a.carry, carry_bytes);
+        f.write(a.carry, carry_bytes);
+        f.read(a.sw_tot, R * 8 * sizeof(float));
+        f.write(a.sw_tot, R * 8 * sizeof(float));
+        f.read(a.sw_pend, R * (size_t)c->P * 8 * sizeof(float));
+        f.write(a.sw_pend, R * (size_t)c->P * 8 * sizeof(float));
+        f.read(a.sw_hist, R * sizeof(uint32_t));
+        f.write(a.sw_hist, R * sizeof(uint32_t));
+    } else {
+        // the open bin is read when the block starts inside one and written when it
+        // ends inside one
+        if (a.bin_pos0 != 0) f.read(a.carry, carry_bytes);
+        if ((a.bin_pos0 / a.M + a.nwin) % (a.K / a.M) != 0) f.write(a.carry, carry_bytes);
+    }
+    if (c->pw) {
+        f.read(a.hw, R * (size_t)a.M * SB);
+        f.write(a.hw, R * (size_t)a.M * SB);
+    }
+    const size_t G = R / (size_t)c->F;              // footprint rows of the launch
+    if (c->ad) f.read(a.adapt, G * 4 * sizeof(float));
+    f.write(a.flags, R * (size_t)a.Wpr * sizeof(uint32_t));
+    for (int k = 0; k < 3; ++k)
+        f.write(a.stats + k * a.stats_plane, G * (size_t)a.nwin * sizeof(float));
+    if (a.n_out > 0) {
+        f.write(a.avg, R * (size_t)a.n_out * 8 * sizeof(float));
+        f.write(a.weight, R * (size_t)a.n_out * sizeof(float));
+    }
+    return f;
+}
+
+// After a plain launch on `st` (ordered after everything before it): nothing earlier is
+// in flight; the launch itself is when its kernel triggers its successor early (then
+// with unknown buffers: everything).  No bookkeeping while the stream is captured.
+void note_plain_launch(int device, cudaStream_t st, bool triggers_early) {
+    if (capturing(st)) return;
+    std::lock_guard<std::mutex> lock(g_order_mu);
+    InFlight &fl = in_flight(device, st);
+    fl.fp.clear();
+    fl.all_waited = true;
+    if (triggers_early) fl.fp.push_back(Footprint::everything());
+}
+
 int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
     if (a.R <= 0) return RFI_OK;
     const int RW = 32 / c->P;
@@ -622,32 +743,64 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
         if (e == cudaSuccess)
             e = cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args2,
                                  c->tma_smem, st);
+        if (e == cudaSuccess) note_plain_launch(c->device, st, false);
+        c->last_launch = 0;
     } else if (c->loader == 1) {
         e = allow_smem(c->tma_fn, c->tma_smem);
         if (e == cudaSuccess)
             e = cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args,
                                  c->tma_smem, st);
-    } else if (c->ovl > 0 && !capturing(st)) {
-        // programmatic dependent launch: the blocks may start while the kernel before
-        // this one on the stream drains, and wait for it before touching anything but
-        // L2 (k_block)
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)blocks);
-        cfg.blockDim = dim3(32 * c->wpb);
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelExC(&cfg, fn, args);
+        if (e == cudaSuccess) note_plain_launch(c->device, st, false);
+        c->last_launch = 0;
     } else {
-        e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args, 0, st);
+        // a kernel that triggers its successor early: ordered against the flagging
+        // launches in flight on the stream (see above); the decision and the launch
+        // happen under one lock, so the bookkeeping follows the stream's order
+        const bool cap = capturing(st);
+        const Footprint fp = footprint_of(c, a);
+        std::lock_guard<std::mutex> lock(g_order_mu);
+        InFlight &fl = in_flight(c->device, st);
+        int order = 0;
+        if (!cap && c->ovl > 0 && fl.fp.size() < kMaxInFlight) {
+            bool clash = false;
+            for (const Footprint &x : fl.fp) clash = clash || clashes(fp, x);
+            if (c->indep && !clash) order = 2;
+            else if (fl.all_waited) order = 1;
+        }
+        StreamArgs b = a;
+        b.indep = order == 2;
+        void *bargs[] = {&b};
+        if (order > 0) {
+            // programmatic dependent launch: the blocks may start while the kernel before
+            // this one on the stream drains
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)blocks);
+            cfg.blockDim = dim3(32 * c->wpb);
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelExC(&cfg, fn, bargs);
+        } else {
+            e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(32 * c->wpb), bargs, 0, st);
+        }
+        if (e == cudaSuccess && !cap) {
+            if (order == 0) {
+                fl.fp.clear();
+                fl.all_waited = true;
+            }
+            if (order == 2) fl.all_waited = false;
+            fl.fp.push_back(fp);
+        }
+        c->last_launch = cap ? -1 : order;
     }
     if (e == cudaSuccess && c->ad && a.nwin > 0) {     // advance the online thresholds
         const long long G = a.R / c->F;
         e = cudaLaunchKernel(adapt_fn(), dim3((unsigned)((G + 255) / 256)), dim3(256), args, 0,
                              st);
+        if (e == cudaSuccess) note_plain_launch(c->device, st, false);
     }
     if (e != cudaSuccess) return set_cuda_error(c, e, "kernel launch");
     return RFI_OK;
@@ -748,6 +901,10 @@ void free_ctx(rfi_ctx *c) {
 
 int rfi_internal_fail(int status, const char *msg) { return fail(status, "%s", msg); }
 
+void rfi_internal_note_plain_launch(int device, void *stream, int triggers_early) {
+    note_plain_launch(device, static_cast<cudaStream_t>(stream), triggers_early != 0);
+}
+
 int rfi_internal_check_dev(const void *p, size_t bytes, size_t align, int device,
                            const char *what) {
     return check_dev(p, bytes, align, device, what);
@@ -805,7 +962,8 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
         o.tma_stage_windows > 64 || o.tma_stages < 0 || o.tma_stages > 8 ||
         o.debug_inject_wait_timeout < 0 || o.debug_inject_wait_timeout > 1 ||
         o.overlap_bytes < -1 || (o.overlap_bytes > 0 && o.overlap_bytes % 128 != 0) ||
-        o.lane_split < 0 || o.lane_split > 1)
+        o.lane_split < 0 || o.lane_split > 1 || o.independent_launches < 0 ||
+        o.independent_launches > 1)
         return fail(RFI_EINVAL, "bad options");
 
     rfi_ctx *c = new (std::nothrow) rfi_ctx();
@@ -884,6 +1042,8 @@ int rfi_create_ex(rfi_ctx **out, int stations, int channels, int window_M, int a
     c->pf_bytes = o.prefetch_bytes ? o.prefetch_bytes : 1024;
     c->pf_groups = o.prefetch_groups > 0 ? o.prefetch_groups : 0;
     c->ovl = o.overlap_bytes == 0 ? 512 : (o.overlap_bytes < 0 ? 0 : o.overlap_bytes);
+    c->indep = o.independent_launches;
+    c->last_launch = -1;
     c->H = hop;
     c->sw = hop != window_M;
     c->wp = o.lane_split == 1;
@@ -1033,6 +1193,14 @@ int rfi_get_options(const rfi_ctx *ctx, rfi_options *opt) {
     opt->overlap_bytes = ctx->ovl > 0 ? ctx->ovl : -1;
     opt->window_hop = ctx->sw ? ctx->H : 0;
     opt->lane_split = ctx->wp;
+    opt->independent_launches = ctx->indep;
+    return RFI_OK;
+}
+
+int rfi_last_launch(const rfi_ctx *ctx, int *order) {
+    if (!ctx || !is_live(ctx)) return fail(RFI_ESTATE, "not a live context");
+    if (!order) return fail(RFI_EINVAL, "null output");
+    *order = ctx->last_launch;
     return RFI_OK;
 }
 
@@ -1156,6 +1324,8 @@ int rfi_process_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const
     if (e == cudaSuccess && c0->ad)
         e = cudaLaunchKernel(adapt_batch_fn(), dim3(adapt_batch_grid(c0->device)), dim3(256),
                              args, 0, static_cast<cudaStream_t>(stream));
+    // the batch kernels do not trigger early: nothing before them is in flight after them
+    if (e == cudaSuccess) note_plain_launch(c0->device, static_cast<cudaStream_t>(stream), false);
     if (e != cudaSuccess) {
         for (int i = 0; i < n; ++i) ctxs[i]->status = RFI_ECUDA;
         return fail(RFI_ECUDA, "batch launch: %s", cudaGetErrorString(e));
@@ -1240,6 +1410,8 @@ int rfi_batch_graph_launch(rfi_batch_graph *g, const void *const *vis, uint32_t 
         e = cudaGraphExecKernelNodeSetParams(g->exec, g->adapt_node, &ka);
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess)
+        note_plain_launch(g->ctxs[0]->device, static_cast<cudaStream_t>(stream), false);
     if (e != cudaSuccess) {
         for (rfi_ctx *c : g->ctxs) c->status = RFI_ECUDA;
         return fail(RFI_ECUDA, "graph launch: %s", cudaGetErrorString(e));

@@ -70,8 +70,12 @@ struct StreamArgs {
     float k_sigma;          // thresholds mean -/+ k_sigma * sd once n >= n_warm
     float n_warm;
     // launch overlap: bytes at the start of every row requested into L2 before the
-    // kernel waits for the grid it depends on (0 = none)
+    // kernel waits for the grid it depends on (0 = none); indep = 1: the host found
+    // that nothing this launch reads is written, and nothing it writes is read or
+    // written, by the flagging launches that may still run on the stream, so it
+    // neither waits for the grid before it nor requests anything early
     int ovl_bytes;
+    int indep;
     // overlapping windows (rfi_sliding.cuh): a window of M samples every hop samples;
     // warm = min(hops of the stream before this launch, M/hop - 1); the carried totals
     // [R][8] and the lane's averaging sums [R][P][8] of the pending hop, and the last
@@ -975,9 +979,11 @@ __device__ __forceinline__ void process_group(const StreamArgs &a, long long gro
 // requests the first ovl_bytes of the warp's rows into L2 (a hint; L2 is where all of
 // the GPU's writes meet, so this is safe whatever that grid writes); then it waits for
 // that grid, after which its writes are visible.  For a launch without the attribute
-// the wait returns at once.
+// the wait returns at once.  A launch the host marked independent (a.indep) shares no
+// buffer with the launches that may still be running and starts its work at once.
 template <int DT, int P>
 __device__ __forceinline__ void overlap_prologue(const StreamArgs &a, long long group) {
+    if (a.indep) return;
     if (a.ovl_bytes > 0) {
         const int lane = threadIdx.x & 31;
         const int SB = DT == DT_F32 ? 32 : 16;

@@ -11,3 +11,8 @@ int rfi_internal_fail(int status, const char *msg);
 // recorded as the last error).
 int rfi_internal_check_dev(const void *p, size_t bytes, size_t align, int device,
                            const char *what);
+
+// Record a plain kernel launch on `stream` for the ordering of later flagging launches:
+// nothing launched before it is still running once it runs; a kernel that triggers its
+// successor early (triggers_early) counts as in flight with unknown buffers.
+void rfi_internal_note_plain_launch(int device, void *stream, int triggers_early);

@@ -247,5 +247,8 @@ extern "C" int rfi_process_block_noalloc(int stations, int channels, int window_
         snprintf(msg, sizeof msg, "kernel launch: %s", cudaGetErrorString(e));
         return rfi_internal_fail(RFI_ECUDA, msg);
     }
+    // the kernel lets the next launch on the stream start early: a flagging launch of a
+    // context after it is ordered as after any launch whose buffers it does not know
+    rfi_internal_note_plain_launch(device, stream, 1);
     return RFI_OK;
 }

@@ -109,3 +109,150 @@ def test_overlap_option_checks():
     assert st.options["overlap_bytes"] == 1024
     st.close()
     assert binding.rfi_options.overlap_bytes.offset > binding.rfi_options.adaptive.offset
+
+
+# ---- independent launches (option independent_launches) ------------------------------
+# A launch that shares no byte with the flagging launches that may still run on the
+# stream starts without waiting for the kernel before it.  The library decides per
+# launch (rfi_last_launch); these tests check both the decision and that every result
+# equals the same calls made one at a time with the overlap off.
+
+def _order(st):
+    return binding.rfi_last_launch(st.ctx)
+
+
+@pytest.mark.parametrize("dtype,opts", [("f32", {}), ("f16", {}),
+                                        ("f16", {"lane_split": 1, "lanes_per_row": 2}),
+                                        ("f32", {"window_F": 2})],
+                         ids=["f32", "f16", "lane_split", "footprint"])
+def test_independent_blocks_overlap_and_match(dtype, opts):
+    """Blocks that close their bins (K = T) into a ring of eight output sets: every call
+    runs independent of the calls still in flight, except one that writes the output
+    set of a call since the last plain launch (launch i + 8 writes what launch i wrote,
+    and launch i may in principle still run): that one runs in plain stream order.
+    The results are those of plain calls."""
+    M, K, T = 16, 64, 64
+    N, C = 9, 16
+    thr = default_thresholds(M * opts.get("window_F", 1))
+    blocks = _blocks(6, N, C, T, dtype, seed=81)
+    on = RfiStream(N, C, M, K, thr, dtype, independent_launches=1, **opts)
+    off = RfiStream(N, C, M, K, thr, dtype, overlap_bytes=-1, **opts)
+    assert on.options["independent_launches"] == 1 and off.options["independent_launches"] == 0
+    ref = []
+    for blk in blocks:
+        ref.append(off.process(blk))
+        torch.cuda.synchronize()
+    assert _order(off) == "plain"
+    ring = [on.alloc_outputs(T) for _ in range(8)]
+    orders = []
+    n = 3 * len(blocks)
+    for i in range(n):
+        on.process(blocks[i % len(blocks)], out=ring[i % 8])
+        orders.append(_order(on))
+        if i % 8 == 7 or i == n - 1:            # compare the ring before it is reused
+            torch.cuda.synchronize()
+            for j in range(i - i % 8, i + 1):
+                for k in ("flags", "avg", "weight", "stats"):
+                    assert torch.equal(ring[j % 8][k], ref[j % len(blocks)][k]), (j, k)
+    want = ["plain" if i > 0 and i % 8 == 0 else "independent" for i in range(n)]
+    assert orders == want, orders
+    on.close(); off.close()
+
+
+def test_independent_launches_wait_for_what_they_share():
+    """Shared output buffers and an open bin carried between calls make launches wait
+    (or run in plain stream order when an independent launch is still in flight); the
+    results are those of plain calls."""
+    M, T = 16, 48
+    N, C = 9, 16
+    thr = default_thresholds(M)
+    blocks = _blocks(6, N, C, T, "f32", seed=83)
+    # K = 32 does not divide T = 48: bins straddle calls, so the open bin's carry
+    # passes from call to call (written by one, read by the next)
+    on = RfiStream(N, C, M, 32, thr, "f32", independent_launches=1)
+    off = RfiStream(N, C, M, 32, thr, "f32", overlap_bytes=-1)
+    got, orders = [], []
+    for blk in blocks:
+        got.append(on.process(blk))
+        orders.append(_order(on))
+    torch.cuda.synchronize()
+    for g, blk in zip(got, blocks):
+        r = off.process(blk)
+        torch.cuda.synchronize()
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(g[k], r[k]), k
+    assert "independent" not in orders[1:], orders
+    on.close(); off.close()
+    # shared outputs: the second call writes what the first writes
+    M, K, T = 16, 64, 64
+    a, b = _blocks(2, N, C, T, "f32", seed=85)
+    st = RfiStream(N, C, M, K, thr, "f32", independent_launches=1)
+    ref = RfiStream(N, C, M, K, thr, "f32", overlap_bytes=-1)
+    rb = ref.process(b)
+    out = st.alloc_outputs(T)
+    for _ in range(10):
+        st.process(a, out=out)
+        st.process(b, out=out)
+        assert _order(st) in ("plain", "waiting")
+    torch.cuda.synchronize()
+    for k in ("flags", "avg", "weight", "stats"):
+        assert torch.equal(out[k], rb[k]), k
+    st.close(); ref.close()
+
+
+def test_independent_launches_across_contexts_and_the_no_alloc_path():
+    """Two contexts on one stream writing the same output buffers are ordered; a
+    launch after rfi_process_block_noalloc (whose buffers the library does not track)
+    waits for it; at most 32 launches stay in flight."""
+    M, K, T = 16, 64, 64
+    N, C = 9, 16
+    thr = default_thresholds(M)
+    a, b = _blocks(2, N, C, T, "f32", seed=87)
+    s1 = RfiStream(N, C, M, K, thr, "f32", independent_launches=1)
+    s2 = RfiStream(N, C, M, K, thr, "f32", independent_launches=1, lanes_per_row=2)
+    ref = RfiStream(N, C, M, K, thr, "f32", lanes_per_row=2, overlap_bytes=-1)
+    rb = ref.process(b)
+    out = s1.alloc_outputs(T)
+    for _ in range(5):
+        s1.process(a, out=out)
+        s2.process(b, out=out)                  # the same outputs, another context
+        assert _order(s2) in ("plain", "waiting")
+    torch.cuda.synchronize()
+    for k in ("flags", "avg", "weight", "stats"):
+        assert torch.equal(out[k], rb[k]), k
+    # after the no-allocation entry point: waiting, never independent
+    o2 = s1.alloc_outputs(T)
+    binding.rfi_process_block_noalloc(N, C, M, K, thr, binding.RFI_C64, 0, a, T,
+                                      o2["flags"], o2["avg"], o2["weight"], o2["stats"])
+    s2.process(b)
+    assert _order(s2) == "waiting"
+    # a plain launch empties the list of launches in flight; then 31 independent
+    # launches fill it to 32 and the next runs in plain stream order (references from a
+    # context of s1's shape with the overlap off)
+    ref1 = RfiStream(N, C, M, K, thr, "f32", overlap_bytes=-1)
+    rb = ref1.process(b)
+    ra = ref1.process(a)
+    assert _order(ref1) == "plain"
+    ring = [s1.alloc_outputs(T) for _ in range(40)]
+    orders = []
+    for i in range(70):
+        s1.process(a if i % 2 else b, out=ring[i % 40])
+        orders.append(_order(s1))
+    torch.cuda.synchronize()
+    want = ["plain" if i in (31, 63) else "independent" for i in range(70)]
+    assert orders == want, orders
+    for i in (0, 31, 32, 63, 69):
+        exp = ra if i % 2 else rb
+        for k in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(ring[i % 40][k], exp[k]), (i, k)
+    s1.close(); s2.close(); ref.close(); ref1.close()
+
+
+def test_independent_launches_option_checks():
+    thr = default_thresholds(16)
+    for bad in (2, -1):
+        with pytest.raises(RfiError):
+            RfiStream(3, 4, 16, 32, thr, "f32", independent_launches=bad)
+    st = RfiStream(3, 4, 16, 32, thr, "f32")
+    assert st.options["independent_launches"] == 0 and _order(st) == "none"
+    st.close()
