@@ -1,6 +1,7 @@
 """The debug-bounds build (every global access of the kernels checked against the
 extent its launch declares; a violation is skipped and reported by rfi_check) runs the
-GPU parity, batching, partial-window, online-threshold and random-combination tests.
+GPU parity, batching, partial-window, online-threshold, launch-overlap (including
+independent launches) and random-combination tests.
 They must pass unchanged: the checks alter no result, and no kernel touches memory
 outside its buffers on any of those shapes.
 
@@ -28,7 +29,7 @@ def test_parity_suite_under_debug_bounds_build():
            "tests/test_sliding_gpu.py", "tests/test_overlap_gpu.py", "tests/test_wpar_gpu.py",
            "-k", "shapes or partial or batch or host or tma or buffered or footprints or "
                  "checkpoint or degenerate or online or warm_up or edge or random or "
-                 "sliding or overlap or window_parallel"]
+                 "sliding or overlap or independent or window_parallel"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1500)
     tail = (r.stdout + r.stderr)[-3000:]
     assert r.returncode == 0, tail

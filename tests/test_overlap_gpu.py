@@ -156,7 +156,8 @@ def test_independent_blocks_overlap_and_match(dtype, opts):
                     assert torch.equal(ring[j % 8][k], ref[j % len(blocks)][k]), (j, k)
     want = ["plain" if i > 0 and i % 8 == 0 else "independent" for i in range(n)]
     assert orders == want, orders
-    on.close(); off.close()
+    binding.rfi_check(on.ctx)                    # no device error (and, in the checked
+    on.close(); off.close()                      # build, no access outside a buffer)
 
 
 def test_independent_launches_wait_for_what_they_share():
@@ -182,6 +183,7 @@ def test_independent_launches_wait_for_what_they_share():
         for k in ("flags", "avg", "weight", "stats"):
             assert torch.equal(g[k], r[k]), k
     assert "independent" not in orders[1:], orders
+    binding.rfi_check(on.ctx)
     on.close(); off.close()
     # shared outputs: the second call writes what the first writes
     M, K, T = 16, 64, 64
@@ -197,6 +199,7 @@ def test_independent_launches_wait_for_what_they_share():
     torch.cuda.synchronize()
     for k in ("flags", "avg", "weight", "stats"):
         assert torch.equal(out[k], rb[k]), k
+    binding.rfi_check(st.ctx)
     st.close(); ref.close()
 
 
@@ -245,6 +248,8 @@ def test_independent_launches_across_contexts_and_the_no_alloc_path():
         exp = ra if i % 2 else rb
         for k in ("flags", "avg", "weight", "stats"):
             assert torch.equal(ring[i % 40][k], exp[k]), (i, k)
+    binding.rfi_check(s1.ctx)
+    binding.rfi_check(s2.ctx)
     s1.close(); s2.close(); ref.close(); ref1.close()
 
 
