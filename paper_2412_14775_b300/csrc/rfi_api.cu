@@ -17,6 +17,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -615,6 +616,10 @@ bool capturing(cudaStream_t st) {
 //       launch, after everything before it on the stream.
 // Kernels that do not trigger early (the staged loaders, the batch and state-update
 // kernels, and graphs of them) are launched plain; after them nothing is in flight.
+// rfi_process_block_noalloc may not allocate, so it does not touch the lists: it counts
+// its launches (an epoch, under the same lock as its launch), and a flagging launch that
+// finds the count changed since its stream's list was last brought up to date treats
+// the stream as holding a launch in flight with unknown buffers.
 // Work that other code puts on the stream between two calls is either a plain stream
 // operation (ordered after everything before it) or a kernel of the caller's; the
 // independent order assumes that no kernel of the caller's that triggers early writes
@@ -654,10 +659,12 @@ bool clashes(const Footprint &x, const Footprint &y) {
 struct InFlight {
     std::vector<Footprint> fp;
     bool all_waited = true;
+    unsigned long long noalloc_seen = 0;   // no-allocation launches accounted for
 };
 constexpr size_t kMaxInFlight = 32;
 std::mutex g_order_mu;
 std::map<std::pair<int, uintptr_t>, InFlight> g_order;
+std::atomic<unsigned long long> g_noalloc_launches{0};
 
 InFlight &in_flight(int device, cudaStream_t st) {
     return g_order[{device, reinterpret_cast<uintptr_t>(st)}];
@@ -701,16 +708,22 @@ Footprint footprint_of(const rfi_ctx *c, const StreamArgs &a) {
     return f;
 }
 
-// After a plain launch on `st` (ordered after everything before it): nothing earlier is
-// in flight; the launch itself is when its kernel triggers its successor early (then
-// with unknown buffers: everything).  No bookkeeping while the stream is captured.
-void note_plain_launch(int device, cudaStream_t st, bool triggers_early) {
-    if (capturing(st)) return;
+// A plain launch of a kernel that does not trigger its successor early, made under the
+// ordering lock: once it runs nothing launched before it is still running, and the
+// launch after it waits for its completion, so the stream's list is emptied (the
+// no-allocation count is left alone: a launch of rfi_process_block_noalloc between the
+// list's last update and this one stays accounted for).  No bookkeeping while the
+// stream is captured.
+template <class Launch>
+cudaError_t launch_plain(int device, cudaStream_t st, Launch &&launch) {
     std::lock_guard<std::mutex> lock(g_order_mu);
-    InFlight &fl = in_flight(device, st);
-    fl.fp.clear();
-    fl.all_waited = true;
-    if (triggers_early) fl.fp.push_back(Footprint::everything());
+    const cudaError_t e = launch();
+    if (e == cudaSuccess && !capturing(st)) {
+        InFlight &fl = in_flight(device, st);
+        fl.fp.clear();
+        fl.all_waited = true;
+    }
+    return e;
 }
 
 int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
@@ -741,16 +754,18 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
         void *args2[] = {const_cast<StreamArgs *>(&a), &tmap};
         e = allow_smem(c->tma_fn, c->tma_smem);
         if (e == cudaSuccess)
-            e = cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args2,
-                                 c->tma_smem, st);
-        if (e == cudaSuccess) note_plain_launch(c->device, st, false);
+            e = launch_plain(c->device, st, [&] {
+                return cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb),
+                                        args2, c->tma_smem, st);
+            });
         c->last_launch = 0;
     } else if (c->loader == 1) {
         e = allow_smem(c->tma_fn, c->tma_smem);
         if (e == cudaSuccess)
-            e = cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb), args,
-                                 c->tma_smem, st);
-        if (e == cudaSuccess) note_plain_launch(c->device, st, false);
+            e = launch_plain(c->device, st, [&] {
+                return cudaLaunchKernel(c->tma_fn, dim3((unsigned)blocks), dim3(32 * c->wpb),
+                                        args, c->tma_smem, st);
+            });
         c->last_launch = 0;
     } else {
         // a kernel that triggers its successor early: ordered against the flagging
@@ -760,6 +775,13 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
         const Footprint fp = footprint_of(c, a);
         std::lock_guard<std::mutex> lock(g_order_mu);
         InFlight &fl = in_flight(c->device, st);
+        const unsigned long long na = g_noalloc_launches.load();
+        if (!cap && fl.noalloc_seen != na) {
+            // a no-allocation launch (on this stream or another) since the list's last
+            // update: it may still run here, with unknown buffers
+            fl.fp.push_back(Footprint::everything());
+            fl.noalloc_seen = na;
+        }
         int order = 0;
         if (!cap && c->ovl > 0 && fl.fp.size() < kMaxInFlight) {
             bool clash = false;
@@ -798,9 +820,10 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
     }
     if (e == cudaSuccess && c->ad && a.nwin > 0) {     // advance the online thresholds
         const long long G = a.R / c->F;
-        e = cudaLaunchKernel(adapt_fn(), dim3((unsigned)((G + 255) / 256)), dim3(256), args, 0,
-                             st);
-        if (e == cudaSuccess) note_plain_launch(c->device, st, false);
+        e = launch_plain(c->device, st, [&] {
+            return cudaLaunchKernel(adapt_fn(), dim3((unsigned)((G + 255) / 256)), dim3(256),
+                                    args, 0, st);
+        });
     }
     if (e != cudaSuccess) return set_cuda_error(c, e, "kernel launch");
     return RFI_OK;
@@ -901,9 +924,12 @@ void free_ctx(rfi_ctx *c) {
 
 int rfi_internal_fail(int status, const char *msg) { return fail(status, "%s", msg); }
 
-void rfi_internal_note_plain_launch(int device, void *stream, int triggers_early) {
-    note_plain_launch(device, static_cast<cudaStream_t>(stream), triggers_early != 0);
+void rfi_internal_noalloc_launch_begin() {
+    g_order_mu.lock();
+    g_noalloc_launches.fetch_add(1);
 }
+
+void rfi_internal_noalloc_launch_end() { g_order_mu.unlock(); }
 
 int rfi_internal_check_dev(const void *p, size_t bytes, size_t align, int device,
                            const char *what) {
@@ -1319,13 +1345,16 @@ int rfi_process_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const
     rfi_ctx *c0 = ctxs[0];
     const int grid = persistent_grid(c0->batch_fn, c0->wpb, c0->device);
     void *args[] = {b};
-    cudaError_t e = cudaLaunchKernel(c0->batch_fn, dim3(grid), dim3(32 * c0->wpb), args, 0,
-                                     static_cast<cudaStream_t>(stream));
-    if (e == cudaSuccess && c0->ad)
-        e = cudaLaunchKernel(adapt_batch_fn(), dim3(adapt_batch_grid(c0->device)), dim3(256),
-                             args, 0, static_cast<cudaStream_t>(stream));
     // the batch kernels do not trigger early: nothing before them is in flight after them
-    if (e == cudaSuccess) note_plain_launch(c0->device, static_cast<cudaStream_t>(stream), false);
+    const cudaStream_t bst = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_plain(c0->device, bst, [&] {
+        cudaError_t r = cudaLaunchKernel(c0->batch_fn, dim3(grid), dim3(32 * c0->wpb), args, 0,
+                                         bst);
+        if (r == cudaSuccess && c0->ad)
+            r = cudaLaunchKernel(adapt_batch_fn(), dim3(adapt_batch_grid(c0->device)),
+                                 dim3(256), args, 0, bst);
+        return r;
+    });
     if (e != cudaSuccess) {
         for (int i = 0; i < n; ++i) ctxs[i]->status = RFI_ECUDA;
         return fail(RFI_ECUDA, "batch launch: %s", cudaGetErrorString(e));
@@ -1409,9 +1438,10 @@ int rfi_batch_graph_launch(rfi_batch_graph *g, const void *const *vis, uint32_t 
         ka.blockDim = dim3(256);
         e = cudaGraphExecKernelNodeSetParams(g->exec, g->adapt_node, &ka);
     }
-    if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
     if (e == cudaSuccess)
-        note_plain_launch(g->ctxs[0]->device, static_cast<cudaStream_t>(stream), false);
+        e = launch_plain(g->ctxs[0]->device, static_cast<cudaStream_t>(stream), [&] {
+            return cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
+        });
     if (e != cudaSuccess) {
         for (rfi_ctx *c : g->ctxs) c->status = RFI_ECUDA;
         return fail(RFI_ECUDA, "graph launch: %s", cudaGetErrorString(e));

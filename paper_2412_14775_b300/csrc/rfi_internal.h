@@ -12,7 +12,9 @@ int rfi_internal_fail(int status, const char *msg);
 int rfi_internal_check_dev(const void *p, size_t bytes, size_t align, int device,
                            const char *what);
 
-// Record a plain kernel launch on `stream` for the ordering of later flagging launches:
-// nothing launched before it is still running once it runs; a kernel that triggers its
-// successor early (triggers_early) counts as in flight with unknown buffers.
-void rfi_internal_note_plain_launch(int device, void *stream, int triggers_early);
+// Bracket the kernel launch of rfi_process_block_noalloc (whose kernel lets the launch
+// after it start early): begin takes the lock under which flagging launches are
+// ordered and counts the launch, end releases it.  Neither allocates; a later flagging
+// launch of a context treats its stream as holding a launch with unknown buffers.
+void rfi_internal_noalloc_launch_begin();
+void rfi_internal_noalloc_launch_end();

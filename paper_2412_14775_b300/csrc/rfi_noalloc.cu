@@ -241,14 +241,16 @@ extern "C" int rfi_process_block_noalloc(int stations, int channels, int window_
     const long long groups = (R + 31) / 32;
     const long long blocks = (groups + wpb - 1) / wpb;
     void *args[] = {&a};
+    // the kernel lets the next launch on the stream start early: counted, so that a
+    // flagging launch of a context after it is ordered as after a launch whose buffers
+    // it does not know
+    rfi_internal_noalloc_launch_begin();
     e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(32 * wpb), args, 0,
                          static_cast<cudaStream_t>(stream));
+    rfi_internal_noalloc_launch_end();
     if (e != cudaSuccess) {
         snprintf(msg, sizeof msg, "kernel launch: %s", cudaGetErrorString(e));
         return rfi_internal_fail(RFI_ECUDA, msg);
     }
-    // the kernel lets the next launch on the stream start early: a flagging launch of a
-    // context after it is ordered as after any launch whose buffers it does not know
-    rfi_internal_note_plain_launch(device, stream, 1);
     return RFI_OK;
 }
