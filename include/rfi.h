@@ -406,6 +406,11 @@ int rfi_batch_graph_destroy(rfi_batch_graph *g);
  *     that continues an open bin (n_seen % K != 0) reads the carry left by the
  *     previous call, so such blocks of one stream must follow each other with no
  *     call for another stream in between.  Calls that overlap on the GPU race.
+ *   - Its kernel lets the launch after it start early; the call counts its launch
+ *     (without allocating) under the lock that orders the library's flagging launches,
+ *     so that the next flagging launch of a context, on any stream, waits for the
+ *     launch before it (or runs in plain stream order) rather than starting
+ *     independently (option independent_launches).
  *   - Calls no cudaMalloc, cudaFree or other allocating routine. */
 #define RFI_NOALLOC_SCRATCH_BYTES (4u << 20)
 int rfi_process_block_noalloc(int stations, int channels, int window_M, int avg_K,
