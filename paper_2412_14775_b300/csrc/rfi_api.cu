@@ -304,11 +304,13 @@ int choose_shape(rfi_ctx *c, int P_req) {
         c->ch = largest_chunk(c->S);
         if (c->mixed && c->F != 1)
             return fail(RFI_EINVAL, "precision = 1 supports time-only windows");
-        // windows that straddle flag words, P of them within one word: the instances
-        // with the whole-round flag path (measured 3-5 % faster there, slower elsewhere)
-        const bool straddle = 32 % c->M != 0 && c->M % 32 != 0 && P * c->M <= 32;
+        // a round's P windows within 32 flag bits: the instances with the whole-round
+        // flag path (measured 3-5 % faster for windows that straddle flag words, 2 % for
+        // binary16 M = 8 with 4 lanes, where a round fills one word; the same bits)
+        const bool whole_round = P * c->M <= 32;
         const WpInstance *wi =
-            straddle && c->prec != 1 ? find_wp(dt, spu_w, P, c->ch, c->prec, 1, c->lb) : nullptr;
+            whole_round && c->prec != 1 ? find_wp(dt, spu_w, P, c->ch, c->prec, 1, c->lb)
+                                        : nullptr;
         if (!wi) wi = find_wp(dt, spu_w, P, c->ch, c->prec, 0, c->lb);
         c->inst = nullptr;
         if (!wi && c->lb != 0)

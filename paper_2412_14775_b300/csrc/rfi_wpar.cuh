@@ -25,9 +25,10 @@ namespace rfi {
 // summed sample by sample in one lane, in the tables' order, so statistics and flags
 // are those of the one-lane-per-row mixed kernel bit for bit (time-only windows).
 // PREC 2: binary16 Stokes arithmetic (accumulate_h2), as in process_group.
-// FS: windows that straddle flag words (M neither divides 32 nor is a multiple of it)
-// with P M <= 32: a whole round's flag bits are placed with one shift (the host picks
-// these instances for such windows only; the code costs the other shapes 2-3 %).
+// FS: a round's P windows span at most 32 flag bits (P M <= 32): a whole round's flag
+// bits are placed with one shift, across a word boundary where windows straddle flag
+// words (the host picks these instances for such shapes only; compiled into every
+// kernel, the code cost the other shapes 2-3 %).
 template <int DT, int SPU, int P, int CH, int PREC = 0, bool FS = false>
 __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long group) {
     constexpr bool MIXED = PREC == 1, H2 = PREC == 2;
