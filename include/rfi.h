@@ -211,7 +211,8 @@ typedef enum {
  *                  reads its outputs between two calls on the stream; plain kernels,
  *                  copies and events in between need nothing.  Results are identical.
  *                  At most 32 launches are kept in flight; the next is a plain launch.
- *                  0 = off (default).
+ *                  rfi_destroy, rfi_reset and rfi_set_state synchronise the device and
+ *                  forget the launches made until then.  0 = off (default).
  *   window_hop     overlapping windows: a window of M samples starts every H =
  *                  window_hop samples (0 or M = no overlap, the paper's windows).
  *                  Only H = M/2 is built: every sample lies in two windows and is

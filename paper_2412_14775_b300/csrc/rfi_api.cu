@@ -728,6 +728,27 @@ cudaError_t launch_plain(int device, cudaStream_t st, Launch &&launch) {
     return e;
 }
 
+// Synchronise the current device under the ordering lock, then empty its streams'
+// lists: every launch made so far has completed, and no flagging launch can be made
+// between the synchronisation and the clearing.  For the entry points that synchronise
+// anyway (destroy, reset, restoring a saved state).
+cudaError_t sync_device_and_forget() {
+    std::lock_guard<std::mutex> lock(g_order_mu);
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) {
+        const unsigned long long na = g_noalloc_launches.load();
+        for (auto &kv : g_order) {
+            if (kv.first.first != device) continue;
+            kv.second.fp.clear();
+            kv.second.all_waited = true;
+            kv.second.noalloc_seen = na;
+        }
+    }
+    return e;
+}
+
 int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
     if (a.R <= 0) return RFI_OK;
     const int RW = 32 / c->P;
@@ -901,6 +922,9 @@ int build_batch(rfi_ctx *const *ctxs, int n, const void *const *vis, const int *
 void free_ctx(rfi_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    // the frees below synchronise the device as well; done first, explicitly, so the
+    // launch-ordering lists of the device can be emptied
+    if (sync_device_and_forget() != cudaSuccess) cudaGetLastError();
     if (c->carry) cudaFree(c->carry);
     if (c->hw) cudaFree(c->hw);
     if (c->adapt) cudaFree(c->adapt);
@@ -1549,7 +1573,7 @@ int rfi_set_state(rfi_ctx *ctx, const void *buf, size_t bytes) {
                                 "adaptive %d, hop %d)",
                     h.R, h.P, h.M, h.K, h.F, h.pw, h.ad, h.hop);
     if ((rc = check_thresholds(&h.thr))) return rc;
-    cudaError_t e = cudaDeviceSynchronize();
+    cudaError_t e = sync_device_and_forget();
     const char *src = static_cast<const char *>(buf) + sizeof h;
     if (e == cudaSuccess)
         e = cudaMemcpy(ctx->carry, src, carry_bytes(ctx), cudaMemcpyHostToDevice);
@@ -1601,7 +1625,7 @@ int rfi_reset(rfi_ctx *ctx) {
     if (!ctx || !is_live(ctx) || ctx->magic != CTX_MAGIC)
         return fail(RFI_ESTATE, "not a live context");
     cudaSetDevice(ctx->device);
-    cudaError_t e = cudaDeviceSynchronize();
+    cudaError_t e = sync_device_and_forget();
     if (e == cudaSuccess)
         e = cudaMemset(ctx->carry, 0, sizeof(float) * 9 * (size_t)ctx->P * ctx->R);
     if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 4 * sizeof(unsigned long long));
