@@ -187,6 +187,8 @@ struct rfi_ctx {
                                         // the pending segment, [R] window flag history
     int wp;                             // window-parallel lanes (lane_split = 1)
     const void *wp_fn;                  // k_wpar<...>
+    const void *wp_fn_whole;            // the same without the partial-round flag path (for
+                                        // launches whose rounds are all whole), or null
     const Instance *inst;
     const void *batch_fn;               // persistent kernel of rfi_process_batch
     long long n_seen;
@@ -320,6 +322,9 @@ int choose_shape(rfi_ctx *c, int P_req) {
         if (!wi) return fail(RFI_EUNSUPPORTED, "no window-parallel kernel for this shape");
         c->wp_fn = wi->fn;
         c->batch_fn = wi->batch_fn;
+        const WpInstance *ww =
+            wi->fs == 1 ? find_wp(dt, spu_w, P, c->ch, c->prec, 2, c->lb) : nullptr;
+        c->wp_fn_whole = ww ? ww->fn : nullptr;
         return RFI_OK;
     }
     // the run of samples the lanes of a row split: a window, or a hop of overlapping ones
@@ -755,7 +760,12 @@ int launch_block(rfi_ctx *c, const StreamArgs &a, cudaStream_t st) {
     const long long groups = (a.R + RW - 1) / RW;
     const long long blocks = (groups + c->wpb - 1) / c->wpb;
     void *args[] = {const_cast<StreamArgs *>(&a)};
-    const void *fn = c->sw ? c->sw_fn : (c->wp ? c->wp_fn : (c->inst ? c->inst->block_fn : nullptr));
+    // window-parallel lanes: a launch whose first window is lane 0's and whose window
+    // count is a multiple of the lanes has whole rounds only
+    const bool whole = c->wp && c->wp_fn_whole && a.wphase == 0 && a.nwin % c->P == 0;
+    const void *fn = c->sw ? c->sw_fn
+                           : (c->wp ? (whole ? c->wp_fn_whole : c->wp_fn)
+                                    : (c->inst ? c->inst->block_fn : nullptr));
     cudaError_t e;
     if (c->loader == 2) {
         // the launch's rows as a 2-D tensor of 8-byte elements; one tile = the pitch of

@@ -64,7 +64,8 @@ SwTable sw_instances_f16();   // rfi_inst_sw_f16.cu
 // Window-parallel lanes (rfi_wpar.cuh): the P lanes of a row take whole windows in turn.
 struct WpInstance {
     int dt, spu, P, ch, mixed;
-    int fs;                 // 1: the whole-round flag-bit path of straddling windows
+    int fs;                 // 1: the whole-round flag-bit path (P M <= 32); 2: the same
+                            // for launches whose rounds are all whole
     int lb;                 // register budget (0: 128, 3: 96); batches take the 128 kernel
     const void *fn;         // k_wpar<...>
     const void *batch_fn;   // k_batch_wp<...>
@@ -209,6 +210,13 @@ WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
 #define RFI_WPS3_CH(DT, PREC)                                                               \
     RFI_WPS3(DT, 2, 1, PREC), RFI_WPS3(DT, 2, 2, PREC), RFI_WPS3(DT, 2, 4, PREC),            \
         RFI_WPS3(DT, 2, 5, PREC)
+// the same for launches whose rounds are all whole (no per-window flag path compiled in)
+#define RFI_WPW3(DT, P, CH, PREC)                                                           \
+    {DT, 1, P, CH, PREC, 2, 3, (const void *)&rfi::k_wpar<DT, 1, P, CH, PREC, 2, 3>,        \
+     (const void *)&rfi::k_batch_wp<DT, 1, P, CH, PREC, 1>}
+#define RFI_WPW3_CH(DT, PREC)                                                               \
+    RFI_WPW3(DT, 2, 1, PREC), RFI_WPW3(DT, 2, 2, PREC), RFI_WPW3(DT, 2, 4, PREC),            \
+        RFI_WPW3(DT, 2, 5, PREC)
 #define RFI_WPM_CH(DT, SPU, P)                                                              \
     RFI_WPM(DT, SPU, P, 1), RFI_WPM(DT, SPU, P, 2), RFI_WPM(DT, SPU, P, 4),                  \
         RFI_WPM(DT, SPU, P, 5)

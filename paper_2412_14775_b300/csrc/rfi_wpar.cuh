@@ -28,8 +28,11 @@ namespace rfi {
 // FS: a round's P windows span at most 32 flag bits (P M <= 32): a whole round's flag
 // bits are placed with one shift, across a word boundary where windows straddle flag
 // words (the host picks these instances for such shapes only; compiled into every
-// kernel, the code cost the other shapes 2-3 %).
-template <int DT, int SPU, int P, int CH, int PREC = 0, bool FS = false>
+// kernel, the code cost the other shapes 2-3 %).  FS = 2: every round of the launch is
+// whole (the host takes these instances for a launch whose first window is lane 0's and
+// whose window count is a multiple of P), so the per-window path of partial rounds is
+// not compiled in (measured 2 % of the binary16 5 x 4 footprint kernel).
+template <int DT, int SPU, int P, int CH, int PREC = 0, int FS = 0>
 __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long group) {
     constexpr bool MIXED = PREC == 1, H2 = PREC == 2;
     static_assert(P >= 2, "one lane per row is the plain kernel");
@@ -193,8 +196,8 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
                 }
             }
         };
-        if constexpr (FS) {
-            if (k * P - s >= 0 && k * P - s + P <= a.nwin) {
+        if constexpr (FS != 0) {
+            if (FS == 2 || (k * P - s >= 0 && k * P - s + P <= a.nwin)) {
                 // a whole round of windows: its P M <= 32 bits, spread from the P
                 // flags, straddle at most one word boundary
                 uint32_t m = 0;
@@ -210,7 +213,7 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
                         fl_row[lo >> 5] = fword;
                     fword = (uint32_t)(m64 >> 32);
                 }
-            } else {
+            } else if constexpr (FS == 1) {
                 flag_each();
             }
         } else {
@@ -290,7 +293,7 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
 
 // LB: the register budget (Bounds in rfi_device.cuh): 0 = 128 registers, 3 = 96 (20
 // resident warps per SM; built for the binary16 odd windows, which fit it unspilled).
-template <int DT, int SPU, int P, int CH, int PREC = 0, bool FS = false, int LB = 0>
+template <int DT, int SPU, int P, int CH, int PREC = 0, int FS = 0, int LB = 0>
 __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
     k_wpar(const __grid_constant__ StreamArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks)
 }
 
 // The persistent batch over window-parallel contexts (same task loop as k_batch).
-template <int DT, int SPU, int P, int CH, int PREC = 0, bool FS = false>
+template <int DT, int SPU, int P, int CH, int PREC = 0, int FS = 0>
 __global__ void __launch_bounds__(512, 1) k_batch_wp(const __grid_constant__ BatchArgs b) {
     run_batch_tasks(b, [](const StreamArgs &a, long long group) {
         process_group_wp<DT, SPU, P, CH, PREC, FS>(a, group);
