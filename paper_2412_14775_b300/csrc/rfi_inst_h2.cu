@@ -21,7 +21,7 @@ static const WpInstance wp_table[] = {
     RFI_WPH_CH(DT_F16, 2, 2), RFI_WPH_CH(DT_F16, 2, 4), RFI_WPH_CH(DT_F16, 2, 8),
     RFI_WPH_CH(DT_F16, 1, 2), RFI_WPH_CH(DT_F16, 1, 4), RFI_WPH_CH(DT_F16, 1, 8),
     RFI_WPS_CH(DT_F16, 2, 2), RFI_WPS_CH(DT_F16, 1, 2), RFI_WPS3_CH(DT_F16, 2),
-    RFI_WPW3_CH(DT_F16, 2),
+    RFI_WPW3_CH(DT_F16, 2), RFI_WPW(DT_F16, 2, 4, 4, 2),
 };
 
 InstanceTable instances_f16_h2() { return {k_table, (int)(sizeof(k_table) / sizeof(k_table[0]))}; }

@@ -10,7 +10,8 @@ static const WpInstance k_table[] = {
     RFI_WP_CH(DT_F16, 1, 2), RFI_WP_CH(DT_F16, 1, 4), RFI_WP_CH(DT_F16, 1, 8),
     RFI_WPM_CH(DT_F16, 2, 2), RFI_WPM_CH(DT_F16, 2, 4), RFI_WPM_CH(DT_F16, 1, 2),
     RFI_WPM_CH(DT_F16, 1, 4), RFI_WPS_CH(DT_F16, 2, 0), RFI_WPS_CH(DT_F16, 1, 0),
-    RFI_WPS3_CH(DT_F16, 0), RFI_WPW3_CH(DT_F16, 0),
+    RFI_WPS3_CH(DT_F16, 0), RFI_WPW3_CH(DT_F16, 0), RFI_WPW(DT_F16, 2, 4, 4, 0),
+    RFI_WPW(DT_F16, 2, 2, 4, 0),
 };
 
 WpTable wp_instances_f16() { return {k_table, (int)(sizeof(k_table) / sizeof(k_table[0]))}; }

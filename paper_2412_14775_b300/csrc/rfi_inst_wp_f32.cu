@@ -9,6 +9,7 @@ namespace rfi {
 static const WpInstance k_table[] = {
     RFI_WP_CH(DT_F32, 1, 2), RFI_WP_CH(DT_F32, 1, 4), RFI_WP_CH(DT_F32, 1, 8),
     RFI_WPM_CH(DT_F32, 1, 2), RFI_WPM_CH(DT_F32, 1, 4), RFI_WPS_CH(DT_F32, 1, 0),
+    RFI_WPW(DT_F32, 1, 2, 5, 0), RFI_WPW(DT_F32, 1, 4, 5, 0),
 };
 
 WpTable wp_instances_f32() { return {k_table, (int)(sizeof(k_table) / sizeof(k_table[0]))}; }

@@ -214,6 +214,11 @@ WpTable wp_instances_f16_h2();  // binary16 Stokes arithmetic (rfi_inst_h2.cu)
 #define RFI_WPW3(DT, P, CH, PREC)                                                           \
     {DT, 1, P, CH, PREC, 2, 3, (const void *)&rfi::k_wpar<DT, 1, P, CH, PREC, 2, 3>,        \
      (const void *)&rfi::k_batch_wp<DT, 1, P, CH, PREC, 1>}
+// whole rounds only, the 128-register budget (binary16 M = 8 with 4 lanes, complex64
+// 5 x 4 footprints with 2 or 4 lanes)
+#define RFI_WPW(DT, SPU, P, CH, PREC)                                                       \
+    {DT, SPU, P, CH, PREC, 2, 0, (const void *)&rfi::k_wpar<DT, SPU, P, CH, PREC, 2, 0>,    \
+     (const void *)&rfi::k_batch_wp<DT, SPU, P, CH, PREC, 1>}
 #define RFI_WPW3_CH(DT, PREC)                                                               \
     RFI_WPW3(DT, 2, 1, PREC), RFI_WPW3(DT, 2, 2, PREC), RFI_WPW3(DT, 2, 4, PREC),            \
         RFI_WPW3(DT, 2, 5, PREC)
