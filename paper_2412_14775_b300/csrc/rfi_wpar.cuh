@@ -27,11 +27,11 @@ namespace rfi {
 // PREC 2: binary16 Stokes arithmetic (accumulate_h2), as in process_group.
 // FS: a round's P windows span at most 32 flag bits (P M <= 32): a whole round's flag
 // bits are placed with one shift, across a word boundary where windows straddle flag
-// words (the host picks these instances for such shapes only; compiled into every
+// words, and a round at an end of the block keeps only the bits of its windows inside
+// the block (the host picks these instances for such shapes only; compiled into every
 // kernel, the code cost the other shapes 2-3 %).  FS = 2: every round of the launch is
 // whole (the host takes these instances for a launch whose first window is lane 0's and
-// whose window count is a multiple of P), so the per-window path of partial rounds is
-// not compiled in (measured 2 % of the binary16 5 x 4 footprint kernel).
+// whose window count is a multiple of P), so the clamps at the block's ends are left out.
 template <int DT, int SPU, int P, int CH, int PREC = 0, int FS = 0>
 __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long group) {
     constexpr bool MIXED = PREC == 1, H2 = PREC == 2;
@@ -197,24 +197,32 @@ __device__ __forceinline__ void process_group_wp(const StreamArgs &a, long long 
             }
         };
         if constexpr (FS != 0) {
-            if (FS == 2 || (k * P - s >= 0 && k * P - s + P <= a.nwin)) {
-                // a whole round of windows: its P M <= 32 bits, spread from the P
-                // flags, straddle at most one word boundary
-                uint32_t m = 0;
+            // a round's P windows, P M <= 32 bits spread from the P flags, placed with one
+            // shift (they straddle at most one word boundary).  A round at either end of
+            // the block keeps only its windows inside the block: before window 0 the
+            // bits are shifted out, after the block's last sample the word is left open
+            // for the store after the loop (FS = 2: every round is whole)
+            uint32_t m = 0;
 #pragma unroll
-                for (int e = 0; e < P; ++e)
-                    if ((rowbits >> e) & 1u) m |= wmask << (e * a.M);
-                const int lo = (k * P - s) * a.M;
-                const int b0 = lo & 31;
-                const unsigned long long m64 = (unsigned long long)m << b0;
-                fword |= (uint32_t)m64;
-                if (b0 + P * a.M >= 32) {
-                    if (lead && rfi_in(fl_row + (lo >> 5), 4, a.flags, flags_ext, a.err))
-                        fl_row[lo >> 5] = fword;
-                    fword = (uint32_t)(m64 >> 32);
+            for (int e = 0; e < P; ++e)
+                if ((rowbits >> e) & 1u) m |= wmask << (e * a.M);
+            int lo = (k * P - s) * a.M;
+            int span = P * a.M;
+            if constexpr (FS == 1) {
+                if (lo < 0) {
+                    m >>= -lo;
+                    span += lo;
+                    lo = 0;
                 }
-            } else if constexpr (FS == 1) {
-                flag_each();
+                span = min(span, nbits - lo);
+            }
+            const int b0 = lo & 31;
+            const unsigned long long m64 = (unsigned long long)m << b0;
+            fword |= (uint32_t)m64;
+            if (b0 + span >= 32) {
+                if (lead && rfi_in(fl_row + (lo >> 5), 4, a.flags, flags_ext, a.err))
+                    fl_row[lo >> 5] = fword;
+                fword = (uint32_t)(m64 >> 32);
             }
         } else {
             flag_each();
