@@ -261,3 +261,64 @@ def test_independent_launches_option_checks():
     st = RfiStream(3, 4, 16, 32, thr, "f32")
     assert st.options["independent_launches"] == 0 and _order(st) == "none"
     st.close()
+
+
+def test_independent_launches_random_sequences():
+    """A seeded random sequence of calls of three contexts on one stream (one carries its
+    open bin from call to call, one is binary16 with window-parallel lanes), each call
+    into one of a few output sets that later calls, of the same or another context of
+    the same shape, may write again: the sets' final contents and every context's saved
+    state equal those of the same sequence with the overlap off."""
+    rng = np.random.default_rng(91)
+    N, C = 7, 8
+    specs = [dict(M=16, K=64, T=64, dtype="f32", opts={}),
+             dict(M=16, K=32, T=48, dtype="f32", opts={"lanes_per_row": 2}),
+             dict(M=8, K=64, T=64, dtype="f16", opts={"lane_split": 1, "lanes_per_row": 4})]
+    on, off, inputs, sets_on, sets_off = [], [], [], [], []
+    for i, sp in enumerate(specs):
+        thr = default_thresholds(sp["M"])
+        on.append(RfiStream(N, C, sp["M"], sp["K"], thr, sp["dtype"], independent_launches=1,
+                            **sp["opts"]))
+        off.append(RfiStream(N, C, sp["M"], sp["K"], thr, sp["dtype"], overlap_bytes=-1,
+                             **sp["opts"]))
+        inputs.append(_blocks(3, N, C, sp["T"], sp["dtype"], seed=93 + i))
+    # three output sets per context, taken at random by its calls; context 1's output
+    # sizes depend on the stream position (its bins straddle calls), so its calls take
+    # fresh outputs
+    for i, sp in enumerate(specs):
+        if i == 1:
+            sets_on.append(None); sets_off.append(None)
+        else:
+            sets_on.append([on[i].alloc_outputs(sp["T"]) for _ in range(3)])
+            sets_off.append([off[i].alloc_outputs(sp["T"]) for _ in range(3)])
+    # the sequence runs back to back with independent launches, then again with the
+    # overlap off (so that no plain launch of the reference breaks the first run's chains)
+    seq = [(int(rng.integers(3)), int(rng.integers(3)), int(rng.integers(3))) for _ in range(60)]
+    fresh_on, fresh_off, orders = [], [], []
+    for i, blk, k in seq:
+        if i == 1:
+            fresh_on.append(on[1].process(inputs[1][blk]))
+        else:
+            on[i].process(inputs[i][blk], out=sets_on[i][k])
+        orders.append(_order(on[i]))
+    for i, blk, k in seq:
+        if i == 1:
+            fresh_off.append(off[1].process(inputs[1][blk]))
+        else:
+            off[i].process(inputs[i][blk], out=sets_off[i][k])
+    torch.cuda.synchronize()
+    for i in (0, 2):
+        for a, b in zip(sets_on[i], sets_off[i]):
+            for name in ("flags", "avg", "weight", "stats"):
+                assert torch.equal(a[name], b[name]), (i, name)
+    for a, b in zip(fresh_on, fresh_off):
+        for name in ("flags", "avg", "weight", "stats"):
+            assert torch.equal(a[name], b[name]), name
+    for s_on, s_off in zip(on, off):
+        a, b = binding.rfi_get_state(s_on.ctx), binding.rfi_get_state(s_off.ctx)
+        n = 36 * s_on.options["lanes_per_row"] * s_on.R      # the open bins' carry
+        assert len(a) == len(b) and a[-n:] == b[-n:]
+        binding.rfi_check(s_on.ctx)
+    assert "independent" in orders and ("waiting" in orders or "plain" in orders), orders
+    for s in on + off:
+        s.close()
